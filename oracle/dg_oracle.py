@@ -1,0 +1,442 @@
+"""FP64 CPU oracle for the symmetric weighted interior-penalty DG operator.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
+CPU-baseline leg may import this module.  The CUDA library and its Python
+binding never call it, and it shares no code with them.
+
+What it computes (Exa-Dune paper, Section 4.1, the SWIPDG bilinear form b_h;
+Section 3.3, matrix-free application of that operator; Section 2.4, the PCG
+algorithm), for -div(K grad u) = f on the unit cube with u = 0 on the boundary:
+
+  a(u, v) = sum_cells  sum_q h^3 w_q K_q  grad u . grad v
+          + sum_faces  sum_p h^2 w_p gamma_F [ -{d_n u}[v] - {d_n v}[u] + (sigma/h)[u][v] ]
+
+on N^3 cubes of side h = 1/N with the tensor-product orthonormal Legendre basis
+L_i(t) = sqrt(2i+1) P_i(2t-1) of degree k per direction, n = k+1 Gauss points
+per direction, sigma = 2(k+1)^2, and:
+  * interior faces: n points from the lower-index cell (-) to the upper one (+),
+    [w] = w- - w+, {w} = (w- + w+)/2;
+  * boundary faces: outward n, [w] = w, {w} = w (one-sided);
+  * per-cell face coefficient Kbar_c = exp(sum_q w_q log K_{c,q}) (Gauss-weighted
+    geometric mean); gamma_F = 2 Kbar- Kbar+ / (Kbar- + Kbar+) on interior faces
+    (weighted averages of the SWIPDG method with per-face-constant K) and
+    gamma_F = Kbar_c on boundary faces.
+Consistency terms carry a MINUS sign (standard symmetric interior penalty; the
+printed plus sign yields an inconsistent scheme, see the convergence pins).
+
+Every basis function and gradient is evaluated at every 3D quadrature point
+from full 3D tables: there is no sum-factorisation here.  Dense matrix products
+(numpy / BLAS) are used as plain library steps.
+
+Parity status: every public function is pinned by tests/test_oracle_pins.py
+(closed-form one-cell matrices, the Kronecker-sum identity, symmetry,
+positive definiteness and the continuum eigenvalue, consistency on harmonic
+polynomials, L2 convergence rates, Euler homogeneity and finite differences of
+the gradient, CG against a direct solve).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from numpy.polynomial import legendre as npleg
+import scipy.sparse as sp
+
+
+# ----------------------------------------------------------------------------
+# 1D ingredients: Gauss points on [0,1] and the orthonormal Legendre basis.
+# ----------------------------------------------------------------------------
+
+def gauss_points(n: int):
+    """n-point Gauss-Legendre rule mapped to [0, 1]; weights sum to 1."""
+    t, w = npleg.leggauss(n)
+    return 0.5 * (t + 1.0), 0.5 * w
+
+
+def legendre(i: int, t):
+    """L_i(t) = sqrt(2i+1) P_i(2t - 1), orthonormal on [0, 1]."""
+    c = np.zeros(i + 1)
+    c[i] = 1.0
+    return math.sqrt(2 * i + 1) * npleg.legval(2.0 * np.asarray(t, float) - 1.0, c)
+
+
+def legendre_deriv(i: int, t):
+    """d/dt L_i(t) = 2 sqrt(2i+1) P_i'(2t - 1)."""
+    c = np.zeros(i + 1)
+    c[i] = 1.0
+    return 2.0 * math.sqrt(2 * i + 1) * npleg.legval(
+        2.0 * np.asarray(t, float) - 1.0, npleg.legder(c))
+
+
+# ----------------------------------------------------------------------------
+# The discretisation: full 3D tables and face tables.
+# ----------------------------------------------------------------------------
+
+class SIPG:
+    """SIPG discretisation of -div(K grad u) on N^3 cubes, Q_k Legendre basis.
+
+    Index conventions: cell c = cx + N(cy + N cz); mode m = i + n(j + n l);
+    volume point q = a + n(b + n e).  Vectors are arrays of shape (N^3, n^3)
+    or their flattening.
+    """
+
+    def __init__(self, n_cells: int, degree: int, sigma: float | None = None):
+        if n_cells < 1 or degree < 1:
+            raise ValueError("need n_cells >= 1 and degree >= 1")
+        self.N = n_cells
+        self.k = degree
+        self.n = n = degree + 1
+        self.n3 = n ** 3
+        self.h = 1.0 / n_cells
+        self.sigma = 2.0 * (degree + 1) ** 2 if sigma is None else float(sigma)
+        self.xi, self.w = gauss_points(n)
+
+        # 1D values at the Gauss points and at the two ends of [0, 1]
+        L = np.array([[legendre(i, t) for i in range(n)] for t in self.xi])       # [a, i]
+        dL = np.array([[legendre_deriv(i, t) for i in range(n)] for t in self.xi])
+        ends = {s: (np.array([legendre(i, float(s)) for i in range(n)]),
+                    np.array([legendre_deriv(i, float(s)) for i in range(n)])) for s in (0, 1)}
+
+        # Full 3D tables over (q, m): value and reference gradient (d/dxi).
+        idx = np.arange(n)
+        qa, qb, qe = np.meshgrid(idx, idx, idx, indexing="ij")   # a,b,e
+        ma, mb, me = qa, qb, qe
+        # flatten with first index fastest: q = a + n(b + n e)
+        def flat(A):
+            return A.transpose(2, 1, 0).reshape(-1)
+        a_, b_, e_ = flat(qa), flat(qb), flat(qe)
+        i_, j_, l_ = flat(ma), flat(mb), flat(me)
+        self.phi = L[a_][:, i_] * L[b_][:, j_] * L[e_][:, l_]                  # (q, m)
+        self.grad = np.stack([dL[a_][:, i_] * L[b_][:, j_] * L[e_][:, l_],
+                              L[a_][:, i_] * dL[b_][:, j_] * L[e_][:, l_],
+                              L[a_][:, i_] * L[b_][:, j_] * dL[e_][:, l_]], axis=-1)  # (q, m, 3)
+        self.wq = self.w[a_] * self.w[b_] * self.w[e_]                           # (q,)
+
+        # Face tables for each axis d and face side s (xi_d = s): value and
+        # reference derivative along axis d at the n^2 face points p = s1 + n s2,
+        # (s1, s2) = Gauss indices along the two other axes in increasing order.
+        self.face_val = {}
+        self.face_der = {}
+        self.face_w = {}
+        P1, P2 = np.meshgrid(idx, idx, indexing="ij")
+        p1 = P1.T.reshape(-1)
+        p2 = P2.T.reshape(-1)
+        for d in range(3):
+            t1, t2 = [ax for ax in range(3) if ax != d]
+            self.face_w[d] = self.w[p1] * self.w[p2]
+            for s in (0, 1):
+                Ls, dLs = ends[s]
+                val = np.empty((n * n, self.n3))
+                der = np.empty((n * n, self.n3))
+                for m in range(self.n3):
+                    mi = (m % n, (m // n) % n, m // (n * n))
+                    # factor along the normal axis d, Gauss factors along t1, t2
+                    tang = L[p1, mi[t1]] * L[p2, mi[t2]]
+                    val[:, m] = Ls[mi[d]] * tang
+                    der[:, m] = dLs[mi[d]] * tang
+                self.face_val[(d, s)] = val
+                self.face_der[(d, s)] = der
+
+    # -- geometry helpers ------------------------------------------------------
+    def cell_coords(self, c):
+        N = self.N
+        c = np.asarray(c)
+        return c % N, (c // N) % N, c // (N * N)
+
+    def stride(self, d: int) -> int:
+        return self.N ** d
+
+    @property
+    def n_cells_total(self) -> int:
+        return self.N ** 3
+
+    @property
+    def n_dofs(self) -> int:
+        return self.N ** 3 * self.n3
+
+    # -- coefficient -----------------------------------------------------------
+    def kbar(self, K):
+        """Per-cell face coefficient Kbar_c = exp(sum_q w_q log K_{c,q})."""
+        K = np.asarray(K, float).reshape(self.n_cells_total, self.n3)
+        return np.exp(np.log(K) @ self.wq)
+
+    def face_gamma(self, Kbar, c, d, upper: bool):
+        """gamma on face (c, d, side): harmonic mean with the neighbour across an
+        interior face, Kbar_c on a boundary face.  Returns (gamma, interior mask,
+        neighbour index)."""
+        c = np.asarray(c)
+        coord = self.cell_coords(c)[d]
+        if upper:
+            interior = coord < self.N - 1
+            nb = np.where(interior, c + self.stride(d), c)
+        else:
+            interior = coord > 0
+            nb = np.where(interior, c - self.stride(d), c)
+        km, kp = Kbar[c], Kbar[nb]
+        gamma = np.where(interior, 2.0 * km * kp / (km + kp), km)
+        return gamma, interior, nb
+
+    # -- matrix-free application (mode E) -------------------------------------
+    def apply(self, K, x, cells=None, chunk: int = 16384):
+        """y = A(K) x on the requested cells (all cells by default).
+
+        Element-by-element with the full 3D tables; each face contribution is
+        evaluated from the face form with the requested cell as the test side.
+        Cells are processed in chunks only to bound memory; every cell's result
+        is computed by the same formula.  Returns an array of shape
+        (len(cells), n^3) (flattened when cells=None).
+        """
+        Nc, n3 = self.n_cells_total, self.n3
+        K = np.asarray(K, float).reshape(Nc, n3)
+        x = np.asarray(x, float).reshape(Nc, n3)
+        full = cells is None
+        cells = np.arange(Nc) if full else np.asarray(cells, dtype=np.int64)
+        Kbar = self.kbar(K)
+        y = np.empty((len(cells), n3))
+        for s in range(0, len(cells), chunk):
+            y[s:s + chunk] = self._apply_cells(K, Kbar, x, cells[s:s + chunk])
+        return y.reshape(-1) if full else y
+
+    def _apply_cells(self, K, Kbar, x, cells):
+        n3, h, sigma = self.n3, self.h, self.sigma
+        # volume: sum_q h w_q K grad^u . grad^phi  (the 1/h^2 of the physical
+        # gradients and the h^3 of the volume element leave one factor h)
+        Gm = self.grad.transpose(1, 0, 2).reshape(n3, n3 * 3)   # [m, (q, d)]
+        gu = (x[cells] @ Gm).reshape(len(cells), n3, 3)         # grad^u at q
+        kt = h * self.wq[None, :] * K[cells]
+        y = (gu * kt[:, :, None]).reshape(len(cells), n3 * 3) @ Gm.T
+
+        for d in range(3):
+            wf = h * self.face_w[d]          # h^2 w_p from the face element times 1/h
+            V0, V1 = self.face_val[(d, 0)], self.face_val[(d, 1)]
+            D0, D1 = self.face_der[(d, 0)], self.face_der[(d, 1)]
+            for upper in (True, False):
+                gamma, interior, nb = self.face_gamma(Kbar, cells, d, upper)
+                W = gamma[:, None] * wf[None, :]
+                xc, xn = x[cells], x[nb]
+                if upper:    # this cell is the (-) side; its neighbour the (+) side
+                    um, gm = xc @ V1.T, xc @ D1.T
+                    up, gp = xn @ V0.T, xn @ D0.T
+                    # interior: [phi] = phi-, {d phi} = d phi- / 2
+                    Jphi, Aphi = V1, 0.5 * D1
+                    # boundary (outward n = +e_d): [u] = u, {d_n u} = d u
+                    jump_b, dn_b, Jphi_b, Aphi_b = um, gm, V1, D1
+                else:        # this cell is the (+) side
+                    um, gm = xn @ V1.T, xn @ D1.T
+                    up, gp = xc @ V0.T, xc @ D0.T
+                    # interior: [phi] = -phi+, {d phi} = d phi+ / 2
+                    Jphi, Aphi = -V0, 0.5 * D0
+                    # boundary (outward n = -e_d): [u] = u, {d_n u} = -d u
+                    jump_b, dn_b, Jphi_b, Aphi_b = up, -gp, V0, -D0
+                jump = um - up
+                avg = 0.5 * (gm + gp)
+                # -{d_n u}[phi] - {d_n phi}[u] + sigma [u][phi], weighted by W
+                y_int = (W * (-avg + sigma * jump)) @ Jphi - (W * jump) @ Aphi
+                y_bnd = (W * (-dn_b + sigma * jump_b)) @ Jphi_b - (W * jump_b) @ Aphi_b
+                y += np.where(interior[:, None], y_int, y_bnd)
+        return y
+
+    # -- assembled matrix (mode A) ---------------------------------------------
+    def assemble(self, K) -> sp.csr_matrix:
+        """Assemble A(K) as a CSR matrix from the same volume and face forms."""
+        Nc, n3, h, sigma = self.n_cells_total, self.n3, self.h, self.sigma
+        K = np.asarray(K, float).reshape(Nc, n3)
+        rows, cols, vals = [], [], []
+        loc = np.arange(n3)
+        R, C = np.meshgrid(loc, loc, indexing="ij")
+
+        def add_block(tc, sc, B):
+            rows.append((tc * n3 + R).reshape(-1))
+            cols.append((sc * n3 + C).reshape(-1))
+            vals.append(B.reshape(-1))
+
+        kt = h * self.wq[None, :] * K
+        G = self.grad
+        for c in range(Nc):
+            B = np.einsum("qmd,q,qnd->mn", G, kt[c], G)
+            add_block(c, c, B)
+
+        Kbar = self.kbar(K)
+        for d in range(3):
+            wf = h * self.face_w[d]
+            V0, V1 = self.face_val[(d, 0)], self.face_val[(d, 1)]
+            D0, D1 = self.face_der[(d, 0)], self.face_der[(d, 1)]
+            # [w] and {d_n w} as linear maps of each side's coefficients
+            side = {"m": (V1, 0.5 * D1), "p": (-V0, 0.5 * D0)}
+            for c in range(Nc):
+                coord = self.cell_coords(c)[d]
+                if coord < self.N - 1:
+                    cp = c + self.stride(d)
+                    km, kp = Kbar[c], Kbar[cp]
+                    W = 2.0 * km * kp / (km + kp) * wf
+                    for tname, tc in (("m", c), ("p", cp)):
+                        Jt, At = side[tname]
+                        for sname, sc in (("m", c), ("p", cp)):
+                            Js, As = side[sname]
+                            B = Jt.T @ (W[:, None] * (-As + sigma * Js)) - At.T @ (W[:, None] * Js)
+                            add_block(tc, sc, B)
+                if coord == self.N - 1:       # upper boundary face, outward +e_d
+                    W = Kbar[c] * wf
+                    Jt, At = V1, D1
+                    add_block(c, c, Jt.T @ (W[:, None] * (-At + sigma * Jt)) - At.T @ (W[:, None] * Jt))
+                if coord == 0:                # lower boundary face, outward -e_d
+                    W = Kbar[c] * wf
+                    Jt, At = V0, -D0
+                    add_block(c, c, Jt.T @ (W[:, None] * (-At + sigma * Jt)) - At.T @ (W[:, None] * Jt))
+        A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(Nc * n3, Nc * n3))
+        return A.tocsr()
+
+    # -- coefficient gradient ---------------------------------------------------
+    def face_form_unit(self, u, v):
+        """b_F^{gamma=1}(u, v) for every face side: array (Nc, 6) in the order
+        (x-, x+, y-, y+, z-, z+); an interior face appears in both of its cells."""
+        Nc, n3, h, sigma = self.n_cells_total, self.n3, self.h, self.sigma
+        u = np.asarray(u, float).reshape(Nc, n3)
+        v = np.asarray(v, float).reshape(Nc, n3)
+        out = np.zeros((Nc, 6))
+        cells = np.arange(Nc)
+        for d in range(3):
+            wf = h * self.face_w[d]
+            V0, V1 = self.face_val[(d, 0)], self.face_val[(d, 1)]
+            D0, D1 = self.face_der[(d, 0)], self.face_der[(d, 1)]
+            for upper in (False, True):
+                coord = self.cell_coords(cells)[d]
+                if upper:
+                    interior = coord < self.N - 1
+                    nb = np.where(interior, cells + self.stride(d), cells)
+                    mcell, pcell = cells, nb
+                else:
+                    interior = coord > 0
+                    nb = np.where(interior, cells - self.stride(d), cells)
+                    mcell, pcell = nb, cells
+
+                def traces(z):
+                    zm, dzm = z[mcell] @ V1.T, z[mcell] @ D1.T
+                    zp, dzp = z[pcell] @ V0.T, z[pcell] @ D0.T
+                    jump, avg = zm - zp, 0.5 * (dzm + dzp)
+                    if upper:
+                        jb, db = zm, dzm
+                    else:
+                        jb, db = zp, -dzp
+                    I = interior[:, None]
+                    return np.where(I, jump, jb), np.where(I, avg, db)
+
+                ju, au = traces(u)
+                jv, av = traces(v)
+                out[:, 2 * d + int(upper)] = ((-au * jv - av * ju + sigma * ju * jv) * wf[None, :]).sum(1)
+        return out
+
+    def coeff_grad(self, K, u, v):
+        """g[c, q] = d(v^T A(K) u) / d log K_{c,q}.
+
+        Volume: h w_q K_{c,q} grad^u(q) . grad^v(q).  Faces: gamma_F depends on
+        K only through Kbar of its cells; d gamma/d log Kbar_c equals
+        gamma * Kbar_other / (Kbar_c + Kbar_other) on an interior face and gamma
+        on a boundary face, and d log Kbar_c / d log K_{c,q} = w_q.
+        """
+        Nc, n3, h = self.n_cells_total, self.n3, self.h
+        K = np.asarray(K, float).reshape(Nc, n3)
+        u = np.asarray(u, float).reshape(Nc, n3)
+        v = np.asarray(v, float).reshape(Nc, n3)
+        Gm = self.grad.transpose(1, 0, 2).reshape(n3, n3 * 3)
+        gu = (u @ Gm).reshape(Nc, n3, 3)
+        gv = (v @ Gm).reshape(Nc, n3, 3)
+        g = h * self.wq[None, :] * K * (gu * gv).sum(-1)
+
+        Kbar = self.kbar(K)
+        bf = self.face_form_unit(u, v)
+        cells = np.arange(Nc)
+        dface = np.zeros(Nc)
+        for d in range(3):
+            for upper in (False, True):
+                gamma, interior, nb = self.face_gamma(Kbar, cells, d, upper)
+                dgam = np.where(interior, gamma * Kbar[nb] / (Kbar + Kbar[nb]), gamma)
+                dface += dgam * bf[:, 2 * d + int(upper)]
+        return g + dface[:, None] * self.wq[None, :]
+
+    # -- right-hand side and errors --------------------------------------------
+    def load_vector(self, f, nq: int | None = None):
+        """b_{c,m} = int_T f phi_m by an nq-point Gauss rule per direction
+        (default nq = n)."""
+        nq = self.n if nq is None else nq
+        tq, wq1 = gauss_points(nq)
+        n, N, h = self.n, self.N, self.h
+        Lq = np.array([[legendre(i, t) for i in range(n)] for t in tq])         # [a, i]
+        c = np.arange(N ** 3)
+        cx, cy, cz = self.cell_coords(c)
+        X = (cx[:, None] + tq[None, :]) * h
+        Y = (cy[:, None] + tq[None, :]) * h
+        Z = (cz[:, None] + tq[None, :]) * h
+        F = f(X[:, :, None, None], Y[:, None, :, None], Z[:, None, None, :])   # (c, a, b, e)
+        Fw = F * (wq1[:, None, None] * wq1[None, :, None] * wq1[None, None, :])
+        # b[c, i, j, l] = h^3 sum_abe Fw L_i(a) L_j(b) L_l(e)
+        b = h ** 3 * np.einsum("cabe,ai,bj,el->clji", Fw, Lq, Lq, Lq)
+        return b.reshape(-1)
+
+    def l2_error(self, x, u, nq: int | None = None):
+        """||u_h - u||_{L2(Omega)} with an nq-point Gauss rule per direction
+        (default k + 3)."""
+        nq = self.k + 3 if nq is None else nq
+        tq, wq1 = gauss_points(nq)
+        n, N, h = self.n, self.N, self.h
+        Lq = np.array([[legendre(i, t) for i in range(n)] for t in tq])
+        x = np.asarray(x, float).reshape(N ** 3, n, n, n)                      # [c, l, j, i]
+        uh = np.einsum("clji,ai,bj,el->cabe", x, Lq, Lq, Lq)
+        c = np.arange(N ** 3)
+        cx, cy, cz = self.cell_coords(c)
+        X = (cx[:, None] + tq[None, :]) * h
+        Y = (cy[:, None] + tq[None, :]) * h
+        Z = (cz[:, None] + tq[None, :]) * h
+        U = u(X[:, :, None, None], Y[:, None, :, None], Z[:, None, None, :])
+        W = wq1[:, None, None] * wq1[None, :, None] * wq1[None, None, :]
+        return math.sqrt(h ** 3 * float(((uh - U) ** 2 * W[None]).sum()))
+
+    def project(self, p, nq: int | None = None):
+        """L2 projection onto the DG space: coefficients x_{c,m} = b_{c,m} / h^3
+        (the mass matrix is h^3 I for the orthonormal basis)."""
+        return self.load_vector(p, nq) / self.h ** 3
+
+
+# ----------------------------------------------------------------------------
+# Conjugate gradients (Section 2.4, Algorithm PCG, with M = I).
+# ----------------------------------------------------------------------------
+
+def cg(apply, b, x0=None, rtol=1e-10, maxit=100000, max_restarts=5):
+    """Unpreconditioned CG following the PCG algorithm of Section 2.4 (M = I).
+
+    Stops when the recursively updated ||r|| <= rtol ||b||; then recomputes
+    b - A x and restarts from x while that true residual is still above rtol.
+    Returns (x, total iterations, true relative residual, residual history).
+    """
+    b = np.asarray(b, float)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, float)
+    nb = float(np.linalg.norm(b))
+    if nb == 0.0:
+        return np.zeros_like(b), 0, 0.0, []
+    it = 0
+    hist = []
+    for _ in range(max_restarts + 1):
+        r = b - apply(x)
+        p = r.copy()                       # p_1 = M r_0
+        rho = float(r @ p)                 # rho_1 = <p_1, r_0>
+        while it < maxit:
+            q = apply(p)                   # q_i = A p_i
+            alpha = float(p @ q)           # alpha_i = <p_i, q_i>
+            if not alpha > 0.0:
+                raise FloatingPointError("CG breakdown: <p, Ap> <= 0")
+            x = x + (rho / alpha) * p
+            r = r - (rho / alpha) * q
+            it += 1
+            z = r                          # z_{i+1} = M r_i
+            rnorm = float(np.linalg.norm(r))
+            hist.append(rnorm / nb)
+            if rnorm <= rtol * nb:
+                break
+            rho_new = float(z @ r)
+            p = (rho_new / rho) * p + z
+            rho = rho_new
+        true_rel = float(np.linalg.norm(b - apply(x))) / nb
+        if true_rel <= rtol or it >= maxit:
+            return x, it, true_rel, hist
+    return x, it, true_rel, hist

@@ -1,0 +1,423 @@
+"""Pins of the FP64 oracle against mathematics, not against itself.
+
+Each test checks a fact fixed independently of the oracle's code path:
+closed-form 1D Legendre data, the Kronecker-sum structure of the K = 1
+operator, symmetry, positive definiteness and the continuum eigenvalue,
+consistency on harmonic polynomials, L2 convergence rates, Euler homogeneity
+of the coefficient gradient, finite differences, and CG against a direct solve.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import SIPG, cg, gauss_points, legendre, legendre_deriv
+from paper_1911_01492_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# 1D ingredients
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 9])
+def test_gauss_rule_exact_to_degree_2n_minus_1(n):
+    t, w = gauss_points(n)
+    assert abs(w.sum() - 1.0) < 1e-15
+    for p in range(2 * n):
+        assert abs((w * t ** p).sum() - 1.0 / (p + 1)) < 1e-14
+    # and not beyond: t^(2n) is integrated inexactly
+    assert abs((w * t ** (2 * n)).sum() - 1.0 / (2 * n + 1)) > 1e-13
+
+
+@pytest.mark.parametrize("i", range(8))
+def test_legendre_end_values_closed_form(i):
+    a = math.sqrt(2 * i + 1)
+    assert abs(legendre(i, 1.0) - a) < 1e-13
+    assert abs(legendre(i, 0.0) - (-1) ** i * a) < 1e-13
+    assert abs(legendre_deriv(i, 1.0) - a * i * (i + 1)) < 1e-11
+    assert abs(legendre_deriv(i, 0.0) - (-1) ** (i + 1) * a * i * (i + 1)) < 1e-11
+
+
+def test_legendre_orthonormal_and_stiffness_closed_form():
+    t, w = gauss_points(12)
+    for i in range(8):
+        for j in range(8):
+            m = (w * legendre(i, t) * legendre(j, t)).sum()
+            assert abs(m - (i == j)) < 1e-13
+            s = (w * legendre_deriv(i, t) * legendre_deriv(j, t)).sum()
+            mm = min(i, j)
+            ref = 2 * math.sqrt(2 * i + 1) * math.sqrt(2 * j + 1) * mm * (mm + 1) if (i + j) % 2 == 0 else 0.0
+            assert abs(s - ref) < 1e-10 * max(1.0, abs(ref))
+
+
+# --------------------------------------------------------------------------
+# P1: the one-cell matrix in closed form
+# --------------------------------------------------------------------------
+
+def closed_form_T(k):
+    n = k + 1
+    sigma = 2.0 * n * n
+    a = np.array([math.sqrt(2 * i + 1) for i in range(n)])
+    d = a * np.array([i * (i + 1) for i in range(n)])
+    T = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            S = 2 * a[i] * a[j] * min(i, j) * (min(i, j) + 1) if (i + j) % 2 == 0 else 0.0
+            T[i, j] = S + (1 + (-1) ** (i + j)) * (sigma * a[i] * a[j] - a[i] * d[j] - a[j] * d[i])
+    return T
+
+
+def kron_sum(T):
+    n = T.shape[0]
+    I = np.eye(n)
+    # m = i + n(j + n l): i is the fastest index
+    return np.kron(I, np.kron(I, T)) + np.kron(I, np.kron(T, I)) + np.kron(T, np.kron(I, I))
+
+
+def read_golden_T():
+    out = {}
+    cur = None
+    for line in open(os.path.join(GOLDEN, "one_cell_T.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("k="):
+            cur = int(line[2:])
+            out[cur] = {"rows": []}
+        elif "=" in line:
+            key, val = line.split("=")
+            out[cur][key] = float(val)
+        else:
+            out[cur]["rows"].append([eval(e, {"sqrt": math.sqrt}) for e in line.split(",")])
+    return out
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_one_cell_matrix_is_closed_form_kronecker_sum(k):
+    D = SIPG(1, k)
+    A = D.assemble(np.ones(D.n_dofs)).toarray()
+    ref = kron_sum(closed_form_T(k))
+    assert np.abs(A - ref).max() <= 1e-12 * np.abs(ref).max()
+    # the matrix-free form gives the same columns
+    for col in (0, 1, D.n3 - 1):
+        e = np.zeros(D.n_dofs)
+        e[col] = 1.0
+        y = D.apply(np.ones(D.n_dofs), e)
+        assert np.abs(y - ref[:, col]).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_one_cell_golden_values():
+    g = read_golden_T()
+    for k, rec in g.items():
+        T = np.array(rec["rows"])
+        assert np.abs(T - closed_form_T(k)).max() < 1e-12 * np.abs(T).max()
+        D = SIPG(1, k)
+        A = D.assemble(np.ones(D.n_dofs)).toarray()
+        ev = np.linalg.eigvalsh(A)
+        assert abs(A[0, 0] - rec["A00"]) < 1e-12 * rec["A00"]
+        assert abs(ev[-1] - rec["lmax"]) < 1e-8 * rec["lmax"]
+        if "lmin" in rec:
+            assert abs(ev[0] - rec["lmin"]) < 1e-7
+
+
+# --------------------------------------------------------------------------
+# P2: K = 1 operator is h^2 times a Kronecker sum of the 1D SIPG matrix
+# --------------------------------------------------------------------------
+
+def sipg_1d(N, k):
+    """1D SIPG matrix on N cells of [0,1] from closed-form trace data."""
+    n = k + 1
+    h = 1.0 / N
+    sigma = 2.0 * n * n
+    a1 = np.array([math.sqrt(2 * i + 1) for i in range(n)])   # L_i(1)
+    d1 = a1 * np.array([i * (i + 1) for i in range(n)])       # L_i'(1)
+    a0 = a1 * np.array([(-1) ** i for i in range(n)])          # L_i(0)
+    d0 = -d1 * np.array([(-1) ** i for i in range(n)])         # L_i'(0)
+    S = np.array([[2 * a1[i] * a1[j] * min(i, j) * (min(i, j) + 1) if (i + j) % 2 == 0 else 0.0
+                   for j in range(n)] for i in range(n)])
+    A = np.zeros((N * n, N * n))
+    for e in range(N):
+        A[e * n:(e + 1) * n, e * n:(e + 1) * n] += S / h
+    # interior points: [w] = w_e(1) - w_{e+1}(0), {w'} = (w_e'(1) + w_{e+1}'(0)) / (2h)
+    for e in range(N - 1):
+        J = np.zeros(N * n)
+        G = np.zeros(N * n)
+        J[e * n:(e + 1) * n] = a1
+        J[(e + 1) * n:(e + 2) * n] = -a0
+        G[e * n:(e + 1) * n] = 0.5 * d1 / h
+        G[(e + 1) * n:(e + 2) * n] = 0.5 * d0 / h
+        A += -np.outer(J, G) - np.outer(G, J) + sigma / h * np.outer(J, J)
+    # boundary points with outward normals
+    for (e, val, der) in ((N - 1, a1, d1 / h), (0, a0, -d0 / h)):
+        J = np.zeros(N * n)
+        G = np.zeros(N * n)
+        J[e * n:(e + 1) * n] = val
+        G[e * n:(e + 1) * n] = der
+        A += -np.outer(J, G) - np.outer(G, J) + sigma / h * np.outer(J, J)
+    return A
+
+
+@pytest.mark.parametrize("N,k", [(2, 1), (2, 2), (3, 2), (3, 1), (2, 3)])
+def test_unit_coefficient_operator_is_kronecker_sum(N, k):
+    n = k + 1
+    h = 1.0 / N
+    A1 = sipg_1d(N, k)
+    I = np.eye(N * n)
+    A3 = h * h * (np.kron(I, np.kron(I, A1)) + np.kron(I, np.kron(A1, I)) + np.kron(A1, np.kron(I, I)))
+    D = SIPG(N, k)
+    A = D.assemble(np.ones(D.n_dofs)).toarray()
+    # oracle index (cz, cy, cx, l, j, i) -> tensor index (Z, Y, X), X = cx n + i
+    g = np.arange(D.n_dofs)
+    m, c = g % D.n3, g // D.n3
+    i, j, l = m % n, (m // n) % n, m // (n * n)
+    cx, cy, cz = c % N, (c // N) % N, c // (N * N)
+    M = N * n
+    t = (cx * n + i) + M * ((cy * n + j) + M * (cz * n + l))
+    assert np.abs(A - A3[np.ix_(t, t)]).max() <= 1e-12 * np.abs(A3).max()
+
+
+# --------------------------------------------------------------------------
+# P3 / P4: symmetry and positive definiteness
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,k", [(3, 2), (2, 3), (2, 4)])
+def test_symmetry_matrix_free(N, k):
+    D = SIPG(N, k)
+    K = inputs.lognormal_coefficient(N, k, seed=7)
+    x = inputs.uniform_vector(N, k, 8)
+    y = inputs.uniform_vector(N, k, 9)
+    lhs = x @ D.apply(K, y)
+    rhs = y @ D.apply(K, x)
+    assert abs(lhs - rhs) <= 1e-13 * (np.abs(x) @ np.abs(D.assemble(K)) @ np.abs(y))
+
+
+@pytest.mark.parametrize("N,k,seed", [(2, 2, 2), (2, 3, 5), (3, 2, 4), (2, 4, 4)])
+def test_positive_definite_under_lognormal_coefficient(N, k, seed):
+    D = SIPG(N, k)
+    K = inputs.lognormal_coefficient(N, k, seed=seed)
+    A = D.assemble(K).toarray()
+    assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+    np.linalg.cholesky(A)                  # raises if not SPD
+    assert np.linalg.eigvalsh(A)[0] > 0
+
+
+def test_smallest_eigenvalue_approaches_continuum():
+    # lambda_min(M^-1 A) -> 3 pi^2 for -Laplace on the unit cube, M = h^3 I
+    D = SIPG(8, 2)
+    A = D.assemble(np.ones(D.n_dofs))
+    lam = spla.eigsh(A.tocsc(), k=1, sigma=0.0, which="LM", return_eigenvectors=False)[0]
+    lam /= D.h ** 3
+    assert abs(lam - 3 * math.pi ** 2) < 2e-3 * 3 * math.pi ** 2
+
+
+# --------------------------------------------------------------------------
+# P5: consistency on harmonic polynomials
+# --------------------------------------------------------------------------
+
+HARMONIC = [
+    lambda x, y, z: 1.0 + 0 * x,
+    lambda x, y, z: x + 0 * y,
+    lambda x, y, z: z - 2 * y + 0 * x,
+    lambda x, y, z: x * y + 0 * z,
+    lambda x, y, z: x * x - y * y + 0 * z,
+    lambda x, y, z: x * y * z,
+    lambda x, y, z: x * x - z * z + 3 * x * y,
+]
+
+
+def interior_cells(D):
+    c = np.arange(D.n_cells_total)
+    cx, cy, cz = D.cell_coords(c)
+    N = D.N
+    return c[(cx > 0) & (cx < N - 1) & (cy > 0) & (cy < N - 1) & (cz > 0) & (cz < N - 1)]
+
+
+@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("pi", range(len(HARMONIC)))
+def test_consistency_on_harmonic_polynomials(k, pi):
+    p = HARMONIC[pi]
+    D = SIPG(4, k)
+    Kc = 2.5
+    K = np.full(D.n_dofs, Kc)
+    x = D.project(p)
+    y = D.apply(K, x).reshape(D.n_cells_total, D.n3)
+    inner = interior_cells(D)
+    scale = np.abs(D.assemble(K)).max() * np.abs(x).max()
+    assert np.abs(y[inner]).max() <= 1e-12 * scale
+    # and the boundary-adjacent cells see the Dirichlet condition
+    if pi == 0:
+        assert np.abs(y).max() > 1e-3 * scale
+
+
+def test_constants_in_kernel_for_any_coefficient():
+    D = SIPG(4, 2)
+    K = inputs.lognormal_coefficient(4, 2, seed=3)
+    x = D.project(lambda x, y, z: 1.0 + 0 * x)
+    y = D.apply(K, x).reshape(D.n_cells_total, D.n3)
+    inner = interior_cells(D)
+    assert np.abs(y[inner]).max() <= 1e-12 * np.abs(y).max()
+
+
+def test_consistency_separates_the_printed_plus_sign():
+    """With the consistency terms' sign flipped, a linear function is no longer
+    in the kernel on interior cells (the reason for the minus-sign reading).
+
+    A(sigma) = Vol + C + sigma P is affine in sigma, so the consistency part is
+    C = A(0) - Vol and the flipped operator is A - 2 C."""
+    D = SIPG(4, 2)
+    K = np.ones(D.n_dofs)
+    x = D.project(lambda x, y, z: x + 0 * y)
+    A = D.assemble(K)
+    A0 = SIPG(4, 2, sigma=0.0).assemble(K)
+    G = D.grad
+    vol = sp.kron(sp.identity(D.n_cells_total), np.einsum("qmd,q,qnd->mn", G, D.h * D.wq, G))
+    A_plus = A - 2 * (A0 - vol)
+    inner = interior_cells(D)
+    y_minus = (A @ x).reshape(-1, D.n3)[inner]
+    y_plus = (A_plus @ x).reshape(-1, D.n3)[inner]
+    assert np.abs(y_minus).max() < 1e-12 * np.abs(A @ x).max()
+    assert np.abs(y_plus).max() > 1e-2 * np.abs(A @ x).max()
+
+
+# --------------------------------------------------------------------------
+# P6: L2 convergence O(h^(k+1))
+# --------------------------------------------------------------------------
+
+def u_exact(x, y, z):
+    return np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+
+
+def f_exact(x, y, z):
+    return 3 * np.pi ** 2 * u_exact(x, y, z)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("k,Ns", [(1, (4, 8)), (2, (4, 8)), (3, (2, 4))])
+def test_l2_convergence_rate(k, Ns):
+    errs = []
+    for N in Ns:
+        D = SIPG(N, k)
+        A = D.assemble(np.ones(D.n_dofs)).tocsc()
+        b = D.load_vector(f_exact, nq=k + 4)
+        x = spla.spsolve(A, b)
+        errs.append(D.l2_error(x, u_exact))
+    rate = math.log(errs[0] / errs[1]) / math.log(Ns[1] / Ns[0])
+    assert abs(rate - (k + 1)) < 0.25, (errs, rate)
+
+
+# --------------------------------------------------------------------------
+# P7 / P8: coefficient gradient
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,k", [(2, 2), (3, 1), (2, 3)])
+def test_gradient_euler_homogeneity_and_symmetry(N, k):
+    D = SIPG(N, k)
+    K = inputs.lognormal_coefficient(N, k, seed=11)
+    u = inputs.uniform_vector(N, k, 12)
+    v = inputs.uniform_vector(N, k, 13)
+    g = D.coeff_grad(K, u, v)
+    total = v @ D.apply(K, u)
+    assert abs(g.sum() - total) <= 1e-12 * np.abs(g).sum()
+    g2 = D.coeff_grad(K, v, u)
+    assert np.abs(g - g2).max() <= 1e-12 * np.abs(g).max()
+
+
+@pytest.mark.parametrize("N,k", [(2, 2), (3, 1)])
+def test_gradient_matches_central_differences(N, k):
+    D = SIPG(N, k)
+    K = inputs.lognormal_coefficient(N, k, seed=21)
+    u = inputs.uniform_vector(N, k, 22)
+    v = inputs.uniform_vector(N, k, 23)
+    g = D.coeff_grad(K, u, v).reshape(-1)
+    rng = np.random.default_rng(24)
+    eps = 1e-5
+    for idx in rng.choice(D.n_dofs, 12, replace=False):
+        Kp = K.copy()
+        Km = K.copy()
+        Kp[idx] *= math.exp(eps)
+        Km[idx] *= math.exp(-eps)
+        fd = (v @ D.apply(Kp, u) - v @ D.apply(Km, u)) / (2 * eps)
+        assert abs(fd - g[idx]) <= 1e-7 * max(1.0, np.abs(g).max())
+    # directional derivative along a random direction
+    dlog = rng.standard_normal(D.n_dofs)
+    fd = (v @ D.apply(K * np.exp(eps * dlog), u) - v @ D.apply(K * np.exp(-eps * dlog), u)) / (2 * eps)
+    assert abs(fd - g @ dlog) <= 1e-7 * np.abs(g).sum()
+
+
+# --------------------------------------------------------------------------
+# The matrix-free and assembled forms, sampled cells, load vectors
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,k", [(3, 2), (2, 4), (4, 1)])
+def test_matrix_free_equals_assembled_and_sampled(N, k):
+    D = SIPG(N, k)
+    K = inputs.lognormal_coefficient(N, k, seed=31)
+    x = inputs.uniform_vector(N, k, 32)
+    y = D.apply(K, x)
+    yA = D.assemble(K) @ x
+    assert np.abs(y - yA).max() <= 1e-13 * np.abs(yA).max()
+    cells = np.array([0, D.n_cells_total - 1, D.n_cells_total // 2])
+    ys = D.apply(K, x, cells=cells)
+    # same formula per cell; BLAS may block the products differently by row count
+    assert np.abs(ys - y.reshape(-1, D.n3)[cells]).max() <= 1e-14 * np.abs(y).max()
+
+
+def test_constant_load_vector_matches_quadrature():
+    D = SIPG(3, 3)
+    b = D.load_vector(lambda x, y, z: 1.0 + 0 * x)
+    assert np.abs(b - inputs.constant_load_vector(3, 3)).max() < 1e-16
+
+
+# --------------------------------------------------------------------------
+# CG (Section 2.4, PCG with M = I)
+# --------------------------------------------------------------------------
+
+def test_cg_matches_direct_solve():
+    D = SIPG(2, 2)
+    K = inputs.lognormal_coefficient(2, 2, seed=41)
+    A = D.assemble(K).toarray()
+    b = inputs.uniform_vector(2, 2, 42)
+    x, it, rel, hist = cg(lambda z: A @ z, b, rtol=1e-12)
+    xd = np.linalg.solve(A, b)
+    assert rel <= 1e-12
+    assert np.abs(x - xd).max() <= 1e-12 * np.linalg.cond(A) * np.abs(xd).max()
+    # CG terminates in at most n steps in exact arithmetic; allow rounding slack
+    assert it <= 2 * len(b)
+    assert hist[-1] <= 1e-12
+
+
+def test_cg_zero_rhs_and_breakdown():
+    x, it, rel, _ = cg(lambda z: z, np.zeros(5))
+    assert it == 0 and np.all(x == 0)
+    with pytest.raises(FloatingPointError):
+        cg(lambda z: -z, np.ones(5))
+
+
+# --------------------------------------------------------------------------
+# Face weights: on piecewise constants SWIPDG is two-point-flux finite volumes
+# (Section 3.4), whose transmissibility is the series conductance of the two
+# half cells -- i.e. the harmonic mean of the cell coefficients.
+# --------------------------------------------------------------------------
+
+def test_constant_modes_couple_with_two_point_flux_transmissibility():
+    N, k = 3, 2
+    D = SIPG(N, k)
+    rng = np.random.default_rng(5)
+    Kc = np.exp(rng.standard_normal(D.n_cells_total))
+    K = np.repeat(Kc, D.n3)                   # constant inside every cell
+    A = D.assemble(K)
+    h = D.h
+    for c in range(D.n_cells_total):
+        for d in range(3):
+            if D.cell_coords(c)[d] < N - 1:
+                c2 = c + D.stride(d)
+                # two half cells of length h/2 in series, face area h^2
+                T = h * h / (0.5 * h / Kc[c] + 0.5 * h / Kc[c2])
+                assert abs(A[c * D.n3, c2 * D.n3] + D.sigma * T) <= 1e-12 * D.sigma * T
+    # and the per-cell face coefficient of a cell-constant K is that constant
+    assert np.abs(D.kbar(K) - Kc).max() <= 1e-14 * Kc.max()
