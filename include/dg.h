@@ -1,0 +1,150 @@
+/*
+ * dg.h -- C ABI of the GB300 matrix-free SIPG-DG library.
+ *
+ * Operator: the symmetric weighted interior-penalty DG form of the Exa-Dune
+ * paper, Section 4.1 (bilinear form b_h with face coupling terms), for
+ * -div(K grad u) = f on the unit cube, u = 0 on the boundary, discretised on
+ * n_cells^3 axis-aligned cubes of side h = 1/n_cells with the tensor-product
+ * orthonormal Legendre basis L_i(t) = sqrt(2i+1) P_i(2t-1) of degree k in each
+ * direction (Section 3.3: matrix-free application by sum factorisation).
+ * Readings of the paper used here: consistency terms with a minus sign;
+ * penalty sigma/h with sigma = 2(k+1)^2; per-cell face coefficient
+ * Kbar_c = exp(sum_q w_q log K_{c,q}); face weight gamma_F = harmonic mean of
+ * the two cells' Kbar on interior faces, Kbar_c on boundary faces.
+ *
+ * Layouts (all vectors are dense, unpadded, contiguous):
+ *   cell      c = cx + N*(cy + N*cz),                    N = n_cells
+ *   DOF       m = i + n*(j + n*l)  (x-mode i fastest),   n = k + 1
+ *   vector    v[c*n^3 + m]          (a cell's DOFs are contiguous)
+ *   quad pt   q = a + n*(b + n*e)  (x-point a fastest), n Gauss points per direction
+ *   K, g      K[c*n^3 + q]
+ *
+ * Conventions.  Every function returns DG_OK (0) or a DG_ERR_* code and, on
+ * error, sets a thread-local message readable with dg_last_error().  Device
+ * pointers are raw CUDA device addresses owned by the caller; the library owns
+ * only the opaque mesh handle and the device workspaces it allocates.  `stream`
+ * is a cudaStream_t passed as void* (NULL = the legacy default stream); work is
+ * enqueued on it asynchronously unless a function says it blocks.  Calls that
+ * share a mesh must not run concurrently on different streams: they share the
+ * mesh's workspaces.
+ */
+#ifndef DG_GB300_H
+#define DG_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DG_OK = 0,
+  DG_ERR_INVALID_ARG = 1,   /* bad pointer, size, mode, aliasing, or invalid K  */
+  DG_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has details) */
+  DG_ERR_NOT_CONVERGED = 3, /* CG reached maxit before the tolerance            */
+  DG_ERR_BREAKDOWN = 4,     /* CG saw <p, Ap> <= 0 or a non-finite scalar        */
+  DG_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up                */
+  DG_ERR_OOM = 6            /* a device allocation failed                        */
+};
+
+enum { DG_FP64 = 0, DG_FP32 = 1 };            /* operator precision            */
+enum { DG_CG_FP64 = 0, DG_CG_MIXED_IR = 1, DG_CG_MIXED_IR_RESTART = 2 };  /* dg_cg_solve modes */
+
+typedef struct dg_mesh dg_mesh;
+
+/* Per-solve statistics (written by the solvers). */
+typedef struct {
+  int iterations;          /* CG iterations (inner iterations for MIXED_IR)         */
+  int outer_iterations;    /* refinement steps (MIXED_IR), restarts (FP64)          */
+  double rel_residual;     /* ||b - A x||_2 / ||b||_2 recomputed in FP64 at the end */
+  double rel_residual_rec; /* last recursively updated residual norm / ||b||        */
+  double seconds;          /* wall time of the solve on the host                    */
+  int status;              /* DG_OK or the error code the solve returned            */
+} dg_cg_stats;
+
+/* Last error message of the calling thread ("" if none).  The pointer stays
+ * valid until the next failing call on this thread. */
+const char* dg_last_error(void);
+
+/* Create a mesh of n_cells^3 cubes of the unit cube with Q_degree elements,
+ * 1 <= n_cells <= 1024, 1 <= degree <= 8, on the current CUDA device.
+ * Allocates the device workspaces (coefficient data, traces).  K is unset
+ * until dg_set_coefficient.  Errors: INVALID_ARG, OOM, CUDA. */
+int dg_create_mesh(int n_cells, int degree, dg_mesh** out);
+
+/* Free the mesh and its workspaces (NULL is accepted). Synchronises the device. */
+int dg_destroy_mesh(dg_mesh* mesh);
+
+/* Sizes: DOFs (= n_cells^3 (degree+1)^3), cells, n = degree+1, sigma. Any
+ * output pointer may be NULL. */
+int dg_mesh_info(const dg_mesh* mesh, long long* n_dofs, long long* n_cells_total,
+                 int* n_points_1d, double* sigma);
+
+/* Set the diffusion coefficient K (device pointer, FP64, layout K[c*n^3 + q],
+ * values at the volume Gauss points).  Derives the weighted volume factors
+ * h w_q K (FP64 and FP32 copies), Kbar per cell and gamma per face side.
+ * Blocks until done: K <= 0 or non-finite anywhere returns INVALID_ARG and
+ * leaves the mesh without a coefficient. */
+int dg_set_coefficient(dg_mesh* mesh, const double* K, void* stream);
+
+/* y = A(K) x (Section 3.3 matrix-free application of the Section 4.1 form).
+ * x, y: device pointers to n_dofs values of type double (prec = DG_FP64) or
+ * float (prec = DG_FP32); y is overwritten; x == y returns INVALID_ARG
+ * (overlapping ranges are not detected).  The FP32 operator computes and
+ * accumulates in FP32 from FP32-rounded tables and coefficients. */
+int dg_apply(const dg_mesh* mesh, const void* x, void* y, int prec, void* stream);
+
+/* xbar = A(K)^T ybar.  The SIPG form is symmetric (a(u,v) = a(v,u)), so the
+ * transposed data flow (test functions <-> trial functions) is the same
+ * sequence of contractions; arguments as dg_apply. */
+int dg_apply_adjoint(const dg_mesh* mesh, const void* ybar, void* xbar, int prec, void* stream);
+
+/* Same as dg_apply but x and y are HOST buffers (pinned or pageable): copies x
+ * to the device, applies, copies y back.  Blocks until y is written. */
+int dg_apply_host(const dg_mesh* mesh, const void* x_host, void* y_host, int prec, void* stream);
+
+/* g[c*n^3 + q] = d(v^T A(K) u) / d log K_{c,q}  (FP64 device pointers, g
+ * overwritten).  Volume part h w_q K_q grad u . grad v at the point; face part
+ * w_q * sum over the cell's faces of d gamma_F / d log Kbar_c times the face
+ * form with gamma = 1.  g must not alias u or v. */
+int dg_coeff_grad(const dg_mesh* mesh, const double* u, const double* v, double* g, void* stream);
+
+/* Solve A(K) x = b by CG (Section 2.4, PCG with M = I).  b, x: FP64 device
+ * pointers; x holds the initial guess on entry and the solution on exit.
+ * mode DG_CG_FP64: FP64 operator and vectors.
+ * mode DG_CG_MIXED_IR: mixed-precision CG with iterative refinement of the
+ *   residual: the CG recurrence runs on the FP32 operator with FP32 vectors and
+ *   FP64-accurate inner products; each time its residual has dropped by 10x
+ *   the FP32 correction is added to x in FP64 and r = b - A x is recomputed
+ *   with the FP64 operator and replaces the FP32 residual (the search
+ *   direction is kept).
+ * mode DG_CG_MIXED_IR_RESTART: classical iterative refinement: FP64 outer
+ *   residual and update, each correction solved from zero by FP32 CG to a 10x
+ *   residual reduction.
+ * Stops when ||b - A x|| <= rtol ||b|| recomputed in FP64.  Blocking.
+ * Returns NOT_CONVERGED at maxit (x holds the last iterate), BREAKDOWN on
+ * <p, Ap> <= 0 or non-finite scalars.  st may be NULL. */
+int dg_cg_solve(const dg_mesh* mesh, const double* b, double* x, double rtol, int maxit,
+                int mode, dg_cg_stats* st, void* stream);
+
+/* Solve count independent systems A_s x_s = b_s (meshes may differ in size and
+ * degree; FP64) with CG run in lock-step: every iteration of all unfinished
+ * samples is one persistent launch, and the iteration loop is captured in a
+ * CUDA graph.  b[s], x[s]: device pointers (arrays of count pointers on the
+ * host).  st: count entries (may be NULL).  Returns the first non-OK sample
+ * status, or OK.  Blocking. */
+int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, const double* const* b,
+                        double* const* x, double rtol, int maxit, dg_cg_stats* st, void* stream);
+
+/* Kernel timing for measurement tools (no paper counterpart).  While enabled,
+ * each dg_apply / dg_apply_adjoint / dg_apply_host on this mesh records CUDA
+ * events on its stream before pass 1 (traces), between the passes and after
+ * pass 2 (cell kernel), for at most max_applies applications.  dg_timing_read
+ * waits for those events, returns the number of recorded applications and the
+ * summed durations of each pass in milliseconds, and disables timing.
+ * Errors: INVALID_ARG (NULL mesh, max_applies < 1 or > 65536), OOM, CUDA. */
+int dg_timing_enable(dg_mesh* mesh, int max_applies);
+int dg_timing_read(dg_mesh* mesh, int* n_applies, double* ms_pass1, double* ms_pass2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_GB300_H */

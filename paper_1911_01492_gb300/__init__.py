@@ -1,1 +1,271 @@
-"""GB300-native matrix-free SIPG-DG operator and CG solvers (placeholder)."""
+"""GB300-native matrix-free SIPG-DG operator and CG solvers.
+
+Thin ctypes binding over the C ABI declared in include/dg.h (libdg_gb300.so,
+built in-tree by `paper_1911_01492_gb300.build`).  The binding only marshals
+arguments: every step of the operator and the solvers runs in the library's
+CUDA kernels.  PyTorch provides device memory and the current stream.  If the
+library is missing or fails to load, every call raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libdg_gb300.so")
+
+DG_OK = 0
+DG_ERR_INVALID_ARG = 1
+DG_ERR_CUDA = 2
+DG_ERR_NOT_CONVERGED = 3
+DG_ERR_BREAKDOWN = 4
+DG_ERR_TIMEOUT = 5
+DG_ERR_OOM = 6
+DG_FP64 = 0
+DG_FP32 = 1
+DG_CG_FP64 = 0
+DG_CG_MIXED_IR = 1
+DG_CG_MIXED_IR_RESTART = 2
+
+ERROR_NAMES = {
+    DG_ERR_INVALID_ARG: "DG_ERR_INVALID_ARG",
+    DG_ERR_CUDA: "DG_ERR_CUDA",
+    DG_ERR_NOT_CONVERGED: "DG_ERR_NOT_CONVERGED",
+    DG_ERR_BREAKDOWN: "DG_ERR_BREAKDOWN",
+    DG_ERR_TIMEOUT: "DG_ERR_TIMEOUT",
+    DG_ERR_OOM: "DG_ERR_OOM",
+}
+
+# every symbol include/dg.h declares, with its ctypes signature
+_VP = ctypes.c_void_p
+_SIGS = {
+    "dg_last_error": (ctypes.c_char_p, []),
+    "dg_create_mesh": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)]),
+    "dg_destroy_mesh": (ctypes.c_int, [_VP]),
+    "dg_mesh_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_double)]),
+    "dg_set_coefficient": (ctypes.c_int, [_VP, _VP, _VP]),
+    "dg_apply": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+    "dg_apply_adjoint": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+    "dg_apply_host": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+    "dg_coeff_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "dg_cg_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                   _VP, _VP]),
+    "dg_cg_solve_batched": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int,
+                                           ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                           ctypes.c_double, ctypes.c_int, _VP, _VP]),
+    "dg_timing_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "dg_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+class DGError(RuntimeError):
+    """A library call returned a DG_ERR_* code."""
+
+    def __init__(self, code: int, func: str, msg: str):
+        self.code = code
+        super().__init__(f"{func}: {ERROR_NAMES.get(code, code)}: {msg}")
+
+
+class CGStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int),
+                ("outer_iterations", ctypes.c_int),
+                ("rel_residual", ctypes.c_double),
+                ("rel_residual_rec", ctypes.c_double),
+                ("seconds", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libdg_gb300.so (once) and declare its signatures.  Raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"{path} is missing: build it with `python -m paper_1911_01492_gb300.build` "
+                "(the CUDA library is required; there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int, func: str):
+    if rc != DG_OK:
+        raise DGError(rc, func, library().dg_last_error().decode())
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, dtype, numel: int, name: str, device: bool = True):
+    import torch
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if device and not t.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor")
+    if not device and t.is_cuda:
+        raise TypeError(f"{name}: expected a host tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: tensor must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """n_cells^3 cubes of the unit cube with Q_degree elements on the current GPU."""
+
+    def __init__(self, n_cells: int, degree: int):
+        import torch
+        torch.cuda.init()
+        lib = library()
+        h = ctypes.c_void_p()
+        _check(lib.dg_create_mesh(int(n_cells), int(degree), ctypes.byref(h)), "dg_create_mesh")
+        self._h = h
+        self.n_cells = int(n_cells)
+        self.degree = int(degree)
+        nd, nc, n1, sg = (ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int(),
+                          ctypes.c_double())
+        _check(lib.dg_mesh_info(h, ctypes.byref(nd), ctypes.byref(nc), ctypes.byref(n1),
+                                ctypes.byref(sg)), "dg_mesh_info")
+        self.n_dofs = nd.value
+        self.n_cells_total = nc.value
+        self.n = n1.value
+        self.sigma = sg.value
+        self._coef_key = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(library().dg_destroy_mesh(self._h), "dg_destroy_mesh")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- coefficient --------------------------------------------------------
+    def set_coefficient(self, K, stream=None):
+        """K: CUDA float64 tensor of n_dofs values at the volume Gauss points."""
+        _check(library().dg_set_coefficient(self._h, _ptr(K, _f64(), self.n_dofs, "K"),
+                                            _stream(stream)), "dg_set_coefficient")
+        self._coef_key = (K.data_ptr(), K._version)
+
+    # -- operator --------------------------------------------------------------
+    def apply(self, x, y=None, stream=None, adjoint: bool = False):
+        """y = A x (or A^T x) in the precision of x (float64 or float32)."""
+        import torch
+        prec = _prec(x.dtype)
+        if y is None:
+            y = torch.empty_like(x)
+        xp = _ptr(x, x.dtype, self.n_dofs, "x")
+        yp = _ptr(y, x.dtype, self.n_dofs, "y")
+        fn = library().dg_apply_adjoint if adjoint else library().dg_apply
+        _check(fn(self._h, xp, yp, prec, _stream(stream)),
+               "dg_apply_adjoint" if adjoint else "dg_apply")
+        return y
+
+    def apply_adjoint(self, ybar, xbar=None, stream=None):
+        return self.apply(ybar, xbar, stream, adjoint=True)
+
+    def apply_host(self, x, y=None, stream=None):
+        """y = A x for host tensors (pinned or pageable); blocks until y is written."""
+        import torch
+        prec = _prec(x.dtype)
+        if y is None:
+            y = torch.empty_like(x)
+        _check(library().dg_apply_host(self._h, _ptr(x, x.dtype, self.n_dofs, "x", device=False),
+                                       _ptr(y, x.dtype, self.n_dofs, "y", device=False), prec,
+                                       _stream(stream)), "dg_apply_host")
+        return y
+
+    def coeff_grad(self, u, v, g=None, stream=None):
+        """g = d(v^T A(K) u) / d log K at the volume Gauss points (float64)."""
+        import torch
+        if g is None:
+            g = torch.empty_like(u)
+        _check(library().dg_coeff_grad(self._h, _ptr(u, _f64(), self.n_dofs, "u"),
+                                       _ptr(v, _f64(), self.n_dofs, "v"),
+                                       _ptr(g, _f64(), self.n_dofs, "g"), _stream(stream)),
+               "dg_coeff_grad")
+        return g
+
+    # -- measurement -------------------------------------------------------------
+    def timing_enable(self, max_applies: int):
+        """Record CUDA events around both passes of the next max_applies applies."""
+        _check(library().dg_timing_enable(self._h, int(max_applies)), "dg_timing_enable")
+
+    def timing_read(self):
+        """(applications recorded, summed pass-1 ms, summed pass-2 ms); disables timing."""
+        n, a, b = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        _check(library().dg_timing_read(self._h, ctypes.byref(n), ctypes.byref(a),
+                                        ctypes.byref(b)), "dg_timing_read")
+        return n.value, a.value, b.value
+
+    # -- solvers ---------------------------------------------------------------
+    def cg_solve(self, b, x=None, rtol: float = 1e-10, maxit: int = 100000,
+                 mode: int = DG_CG_FP64, stream=None, raise_on_error: bool = True):
+        """Solve A x = b (blocking).  Returns (x, stats dict)."""
+        import torch
+        if x is None:
+            x = torch.zeros_like(b)
+        st = CGStats()
+        rc = library().dg_cg_solve(self._h, _ptr(b, _f64(), self.n_dofs, "b"),
+                                   _ptr(x, _f64(), self.n_dofs, "x"), float(rtol), int(maxit),
+                                   int(mode), ctypes.byref(st), _stream(stream))
+        if raise_on_error:
+            _check(rc, "dg_cg_solve")
+        return x, st.as_dict()
+
+
+def cg_solve_batched(meshes, bs, xs, rtol: float = 1e-8, maxit: int = 100000, stream=None,
+                     raise_on_error: bool = True):
+    """Solve meshes[s] x[s] = b[s] for all s in one lock-step batched solve."""
+    count = len(meshes)
+    if not (len(bs) == len(xs) == count):
+        raise ValueError("meshes, bs and xs must have the same length")
+    H = (ctypes.c_void_p * count)(*[m.handle for m in meshes])
+    B = (ctypes.c_void_p * count)(*[_ptr(b, _f64(), m.n_dofs, "b") for b, m in zip(bs, meshes)])
+    X = (ctypes.c_void_p * count)(*[_ptr(x, _f64(), m.n_dofs, "x") for x, m in zip(xs, meshes)])
+    st = (CGStats * count)()
+    rc = library().dg_cg_solve_batched(H, count, B, X, float(rtol), int(maxit),
+                                       ctypes.cast(st, ctypes.c_void_p), _stream(stream))
+    if raise_on_error:
+        _check(rc, "dg_cg_solve_batched")
+    return [s.as_dict() for s in st]
+
+
+def _f64():
+    import torch
+    return torch.float64
+
+
+def _prec(dtype):
+    import torch
+    if dtype == torch.float64:
+        return DG_FP64
+    if dtype == torch.float32:
+        return DG_FP32
+    raise TypeError(f"unsupported dtype {dtype}: use float64 or float32")

@@ -1,0 +1,25 @@
+// FP64 instantiation of the two-pass operator application.
+#include "dg_apply_impl.cuh"
+
+int dg_launch_apply_f64(const dg_mesh* m, const double* x, double* y, const int* skip,
+                        cudaStream_t s) {
+  cudaError_t e = dgk::dispatch_n<double, dgk::ApplyF>(m->n, m, x, y, m->U64, m->X64, m->TR64,
+                                                       (const double*)m->kt64,
+                                                       (const double*)m->gh64, m->ncells, m->N,
+                                                       skip, &m->tab64, s);
+  if (e != cudaSuccess) return dg_cuda_fail(e, "apply (fp64) launch");
+  return DG_OK;
+}
+
+int dg_launch_trace_f64(const dg_mesh* m, const double* x, double* U, double* X, double* TR,
+                        cudaStream_t s) {
+  cudaError_t e = dgk::dispatch_n<double, dgk::TraceF>(m->n, x, U, X, TR, m->ncells, &m->tab64, s);
+  if (e != cudaSuccess) return dg_cuda_fail(e, "trace (fp64) launch");
+  return DG_OK;
+}
+
+int dg_prepare_apply_f64(int n) {
+  cudaError_t e = dgk::dispatch_n<double, dgk::PrepareF>(n);
+  if (e != cudaSuccess) return dg_cuda_fail(e, "apply (fp64) kernel attributes");
+  return DG_OK;
+}

@@ -1,0 +1,596 @@
+// Conjugate gradients on the device (Section 2.4, the PCG algorithm with M = I):
+//   q = A p,  alpha = rho / <p, q>,  x += alpha p,  r -= alpha q,
+//   rho' = <r, r>  (the convergence norm, merged into the update as in
+//   Section 2.4's merged reduction),  p = r + (rho'/rho) p.
+// Scalars live on the device (DGCGState); every kernel checks `done` first, so
+// a CUDA graph of a fixed number of iterations can be replayed until the host
+// sees convergence without overshooting.  Reductions are deterministic: a fixed
+// grid writes per-block partial sums and the last block to finish adds them in
+// a fixed order.
+//
+// Inner products of FP32 vectors are accumulated to FP64 accuracy without the
+// FP64 pipe: each product a*b is split exactly into p + e (p = fl(a*b),
+// e = fma(a, b, -p)), the pairs are summed in compensated float-float
+// arithmetic (Knuth's TwoSum), and only each block's partial sum is converted
+// to FP64.
+//
+// Mixed precision (DG_CG_MIXED_IR): the CG recurrence runs on the FP32 operator
+// with FP32 vectors; x and the true residual are kept in FP64.  When the FP32
+// residual has dropped below delta times its value at the last refinement (or
+// below the tolerance), the FP32 correction d is added to x in FP64, r = b - A x
+// is recomputed with the FP64 operator, and r replaces the FP32 residual; the
+// search direction p is kept, so the Krylov recurrence is not restarted.  The
+// refinement kernels are in every captured iteration and skip themselves unless
+// the update kernel requested a refinement.
+//
+// DG_CG_MIXED_IR_RESTART: classical refinement, each correction solved from
+// zero by FP32 CG to a fixed residual reduction, then x += ||r|| d in FP64.
+#include <chrono>
+#include <cmath>
+
+#include "dg_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// s + t = a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = a + b;
+  const float bb = s - a;
+  t = (a - (s - bb)) + (b - bb);
+}
+
+// Accumulators: FP64 for FP64 data, compensated float-float for FP32 data.
+struct AccD {
+  double s = 0.0;
+  __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+  __device__ double block_total();  // valid in thread 0
+};
+struct AccF {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);  // a*b = p + e exactly
+    float s, t;
+    two_sum(hi, p, s, t);
+    hi = s;
+    lo += t + e;
+  }
+  __device__ double block_total();
+};
+template <typename T> struct AccOf;
+template <> struct AccOf<double> { using type = AccD; };
+template <> struct AccOf<float> { using type = AccF; };
+
+__device__ double AccD::block_total() {
+  __shared__ double sw[DG_RED_THREADS / 32];
+  double v = warp_sum(s);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sw[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) r = warp_sum((l < DG_RED_THREADS / 32) ? sw[l] : 0.0);
+  return r;
+}
+
+__device__ double AccF::block_total() {
+  __shared__ float sh[DG_RED_THREADS / 32], sl[DG_RED_THREADS / 32];
+  float h = hi, lw = lo;
+  for (int off = 16; off > 0; off >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, off);
+    const float ol = __shfl_xor_sync(0xffffffffu, lw, off);
+    float s, t;
+    two_sum(h, oh, s, t);
+    h = s;
+    lw = lw + ol + t;
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+    sh[w] = h;
+    sl[w] = lw;
+  }
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    double v = (l < DG_RED_THREADS / 32) ? (double)sh[l] + (double)sl[l] : 0.0;
+    r = warp_sum(v);
+  }
+  return r;
+}
+
+// Publish this block's partial sums; returns true in the last block to finish,
+// whose thread 0 then holds the totals in tot[0..K-1] (fixed-order sums).
+template <int K, typename A>
+__device__ bool last_block_sums(A (&part)[K], double* partials, unsigned int* ticket,
+                                double (&tot)[K]) {
+  __shared__ bool is_last;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = part[k].block_total();
+    if (threadIdx.x == 0) partials[k * DG_RED_BLOCKS + blockIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    AccD a;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      a.s += ((volatile double*)partials)[k * DG_RED_BLOCKS + b];
+    tot[k] = a.block_total();
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+#define GRID_STRIDE(i, n)                                                         \
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (n); \
+       i += (long long)gridDim.x * blockDim.x)
+
+// r = b - q, p = r; rho = <r,r>, bnorm2 = <b,b>; tol2 = rtol^2 bnorm2.
+template <typename T>
+__global__ void __launch_bounds__(DG_RED_THREADS)
+k_init(const T* __restrict__ b, const T* __restrict__ q, T* __restrict__ r, T* __restrict__ p,
+       long long n, double rtol, double* partials, DGCGState* st) {
+  typename AccOf<T>::type acc[2];
+  GRID_STRIDE(i, n) {
+    const T ri = b[i] - q[i];
+    r[i] = ri;
+    p[i] = ri;
+    acc[0].add_prod(ri, ri);
+    acc[1].add_prod(b[i], b[i]);
+  }
+  double tot[2];
+  if (last_block_sums<2>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
+    st->rho = tot[0];
+    st->bnorm2 = tot[1];
+    st->tol2 = rtol * rtol * tot[1];
+    st->breakdown = !(finite(tot[0]) && finite(tot[1]));
+    st->done = st->breakdown || tot[0] <= st->tol2 || st->iters >= st->maxit;
+    st->ru_skip = 1;
+  }
+}
+
+// pq = <p, q>, alpha = rho / pq.
+template <typename T>
+__global__ void __launch_bounds__(DG_RED_THREADS)
+k_dot_pq(const T* __restrict__ p, const T* __restrict__ q, long long n, double* partials,
+         DGCGState* st) {
+  if (st->done) return;
+  typename AccOf<T>::type acc[1];
+  GRID_STRIDE(i, n) acc[0].add_prod(p[i], q[i]);
+  double tot[1];
+  if (last_block_sums<1>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
+    st->pq = tot[0];
+    if (!(tot[0] > 0.0) || !finite(tot[0])) {
+      st->breakdown = 1;
+      st->done = 1;
+      st->ru_skip = 1;
+    } else {
+      st->alpha = st->rho / tot[0];
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q, rho' = <r, r>.
+// MIXED = false: convergence test on rho', beta, rho = rho'.
+// MIXED = true: request an FP64 refinement (ru_skip = 0) when rho' has dropped
+// below delta2 * rmax2 or below tol2, or at the iteration cap; rho' is kept in
+// rho_new for the direction update.
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(DG_RED_THREADS)
+k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+            const T* __restrict__ q, long long n, double* partials, DGCGState* st) {
+  if (st->done) return;
+  const T a = (T)st->alpha;
+  typename AccOf<T>::type acc[1];
+  GRID_STRIDE(i, n) {
+    x[i] = fma(a, p[i], x[i]);
+    const T ri = fma(-a, q[i], r[i]);
+    r[i] = ri;
+    acc[0].add_prod(ri, ri);
+  }
+  double tot[1];
+  if (last_block_sums<1>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
+    const double rr = tot[0];
+    st->iters += 1;
+    if (!finite(rr)) {
+      st->breakdown = 1;
+      st->done = 1;
+      st->ru_skip = 1;
+    } else if (!MIXED) {
+      st->beta = rr / st->rho;
+      st->rho = rr;
+      if (rr <= st->tol2 || st->iters >= st->maxit) st->done = 1;
+    } else {
+      st->rho_new = rr;
+      st->ru_skip = !(rr <= st->delta2 * st->rmax2 || rr <= st->tol2 || st->iters >= st->maxit);
+    }
+  }
+}
+
+// p = r + beta p.  MIXED: beta = rho_new / rho (rho is committed afterwards by
+// k_commit_rho, so every block reads the same pair).
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(DG_RED_THREADS)
+k_update_p(T* __restrict__ p, const T* __restrict__ r, long long n, const DGCGState* st) {
+  if (st->done) return;
+  const double beta = MIXED ? st->rho_new / st->rho : st->beta;
+  const T be = (T)beta;
+  GRID_STRIDE(i, n) p[i] = fma(be, p[i], r[i]);
+}
+
+// mixed mode: rho = rho_new after the direction update
+__global__ void k_commit_rho(DGCGState* st) {
+  if (st->done) return;
+  st->rho = st->rho_new;
+}
+
+// refinement step 1 (mixed): x64 += d32, d32 = 0.
+__global__ void __launch_bounds__(DG_RED_THREADS)
+k_refine_x(double* __restrict__ x, float* __restrict__ d, long long n, const DGCGState* st) {
+  if (st->ru_skip) return;
+  GRID_STRIDE(i, n) {
+    x[i] += (double)d[i];
+    d[i] = 0.0f;
+  }
+}
+
+// refinement step 2 (mixed), after q = A64 x: r64 = b - q, r32 = (float) r64,
+// rho_new = rmax2 = ||r64||^2; converged when <= tol2; cap on iterations.
+__global__ void __launch_bounds__(DG_RED_THREADS)
+k_refine_r(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
+           float* __restrict__ r32, long long n, double* partials, DGCGState* st) {
+  if (st->ru_skip) return;
+  AccD acc[1];
+  GRID_STRIDE(i, n) {
+    const double ri = b[i] - q[i];
+    r[i] = ri;
+    r32[i] = (float)ri;
+    acc[0].add_prod(ri, ri);
+  }
+  double tot[1];
+  if (last_block_sums<1>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
+    const double rr = tot[0];
+    st->n_refine += 1;
+    st->rho_new = rr;
+    st->rmax2 = rr;
+    st->ru_skip = 1;
+    if (!finite(rr)) {
+      st->breakdown = 1;
+      st->done = 1;
+    } else if (rr <= st->tol2 || st->iters >= st->maxit) {
+      st->done = 1;
+    }
+  }
+}
+
+// r = b - q; res2 = <r, r>, b2 = <b, b> (no other state change).
+__global__ void __launch_bounds__(DG_RED_THREADS)
+k_residual(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
+           long long n, double* partials, DGCGState* st) {
+  AccD acc[2];
+  GRID_STRIDE(i, n) {
+    const double ri = b[i] - q[i];
+    r[i] = ri;
+    acc[0].add_prod(ri, ri);
+    acc[1].add_prod(b[i], b[i]);
+  }
+  double tot[2];
+  if (last_block_sums<2>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
+    st->res2 = tot[0];
+    st->b2 = tot[1];
+  }
+}
+
+// r32 = (float)(r64 * inv), d32 = 0
+__global__ void k_scale_to_f32(const double* __restrict__ r, float* __restrict__ r32,
+                               float* __restrict__ d32, long long n, double inv) {
+  GRID_STRIDE(i, n) {
+    r32[i] = (float)(r[i] * inv);
+    d32[i] = 0.0f;
+  }
+}
+
+// x += scale * d32  (FP64 update)
+__global__ void k_axpy_f32_into_f64(double* __restrict__ x, const float* __restrict__ d,
+                                    long long n, double scale) {
+  GRID_STRIDE(i, n) x[i] = fma(scale, (double)d[i], x[i]);
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+#define RED_LAUNCH DG_RED_BLOCKS, DG_RED_THREADS, 0, s
+
+// One iteration of plain CG on FP64 or FP32 vectors.
+template <typename T>
+int launch_iteration(dg_mesh* m, T* x, T* r, T* p, T* q, cudaStream_t s) {
+  int rc = (sizeof(T) == 8)
+               ? dg_launch_apply_f64(m, (const double*)p, (double*)q, &m->state->done, s)
+               : dg_launch_apply_f32(m, (const float*)p, (float*)q, &m->state->done, s);
+  if (rc) return rc;
+  const long long n = m->ndofs;
+  k_dot_pq<T><<<RED_LAUNCH>>>(p, q, n, m->partials, m->state);
+  k_update_xr<T, false><<<RED_LAUNCH>>>(x, r, p, q, n, m->partials, m->state);
+  k_update_p<T, false><<<RED_LAUNCH>>>(p, r, n, m->state);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+// One iteration of mixed CG with the conditional FP64 refinement.
+int launch_iteration_mixed(dg_mesh* m, const double* b, double* x, cudaStream_t s) {
+  const long long n = m->ndofs;
+  int rc = dg_launch_apply_f32(m, m->p32, m->q32, &m->state->done, s);
+  if (rc) return rc;
+  k_dot_pq<float><<<RED_LAUNCH>>>(m->p32, m->q32, n, m->partials, m->state);
+  k_update_xr<float, true><<<RED_LAUNCH>>>(m->d32, m->r32, m->p32, m->q32, n, m->partials,
+                                           m->state);
+  k_refine_x<<<RED_LAUNCH>>>(x, m->d32, n, m->state);
+  rc = dg_launch_apply_f64(m, x, m->q64, &m->state->ru_skip, s);
+  if (rc) return rc;
+  k_refine_r<<<RED_LAUNCH>>>(b, m->q64, m->r64, m->r32, n, m->partials, m->state);
+  k_update_p<float, true><<<RED_LAUNCH>>>(m->p32, m->r32, n, m->state);
+  k_commit_rho<<<1, 1, 0, s>>>(m->state);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+// Capture `chunk` iterations into a graph and replay it until `done`.
+template <typename F>
+int run_graph(dg_mesh* m, cudaStream_t s, int chunk, F&& one_iteration) {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  DG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int rc = DG_OK;
+  for (int i = 0; i < chunk && rc == DG_OK; ++i) rc = one_iteration();
+  cudaError_t ec = cudaStreamEndCapture(s, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  DG_CUDA(ec);
+  ec = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  DG_CUDA(ec);
+  for (;;) {
+    ec = cudaGraphLaunch(exec, s);
+    if (ec == cudaSuccess)
+      ec = cudaMemcpyAsync(m->state_host, m->state, sizeof(DGCGState), cudaMemcpyDeviceToHost, s);
+    if (ec == cudaSuccess) ec = cudaStreamSynchronize(s);
+    if (ec != cudaSuccess) {
+      cudaGraphExecDestroy(exec);
+      return dg_cuda_fail(ec, "CG iteration graph");
+    }
+    if (m->state_host->done) break;
+  }
+  cudaGraphExecDestroy(exec);
+  return DG_OK;
+}
+
+int set_state(dg_mesh* m, int maxit, int iters, cudaStream_t s) {
+  DGCGState h = {};
+  h.maxit = maxit;
+  h.iters = iters;
+  h.ru_skip = 1;
+  *m->state_host = h;
+  DG_CUDA(cudaMemcpyAsync(m->state, m->state_host, sizeof(DGCGState), cudaMemcpyHostToDevice, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
+// ||b - A x||^2 and ||b||^2 in FP64 (r64 gets the residual).
+int true_residual(dg_mesh* m, const double* b, const double* x, cudaStream_t s, double* res2,
+                  double* b2) {
+  int rc = dg_launch_apply_f64(m, x, m->q64, nullptr, s);
+  if (rc) return rc;
+  k_residual<<<RED_LAUNCH>>>(b, m->q64, m->r64, m->ndofs, m->partials, m->state);
+  DG_CUDA(cudaGetLastError());
+  DG_CUDA(cudaMemcpyAsync(m->state_host, m->state, sizeof(DGCGState), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  *res2 = m->state_host->res2;
+  *b2 = m->state_host->b2;
+  return DG_OK;
+}
+
+int chunk_for(const dg_mesh* m) { return m->ndofs < (1LL << 22) ? 32 : 8; }
+
+int zero_solution(dg_mesh* m, double* x, dg_cg_stats* st, cudaStream_t s) {
+  DG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)m->ndofs, s));
+  if (st) st->rel_residual = st->rel_residual_rec = 0.0;
+  return DG_OK;
+}
+
+int cg_fp64(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_cg_stats* st,
+            cudaStream_t s) {
+  const int max_restarts = 5;
+  int iters = 0, restarts = 0;
+  double res2 = 0, b2 = 0;
+  int rc = true_residual(m, b, x, s, &res2, &b2);
+  if (rc) return rc;
+  if (b2 == 0.0) return zero_solution(m, x, st, s);  // A x = 0 has the solution x = 0
+  for (;;) {
+    rc = set_state(m, maxit, iters, s);
+    if (rc) return rc;
+    rc = dg_launch_apply_f64(m, x, m->q64, nullptr, s);
+    if (rc) return rc;
+    k_init<double><<<RED_LAUNCH>>>(b, m->q64, m->r64, m->p64, m->ndofs, rtol, m->partials,
+                                   m->state);
+    DG_CUDA(cudaGetLastError());
+    rc = run_graph(m, s, chunk_for(m), [&] {
+      return launch_iteration<double>(m, x, m->r64, m->p64, m->q64, s);
+    });
+    if (rc) return rc;
+    const DGCGState hs = *m->state_host;
+    iters = hs.iters;
+    if (st) st->rel_residual_rec = hs.bnorm2 > 0 ? std::sqrt(hs.rho / hs.bnorm2) : 0.0;
+    rc = true_residual(m, b, x, s, &res2, &b2);
+    if (rc) return rc;
+    const double rel = std::sqrt(res2 / b2);
+    if (st) {
+      st->iterations = iters;
+      st->outer_iterations = restarts;
+      st->rel_residual = rel;
+    }
+    if (hs.breakdown)
+      return dg_fail(DG_ERR_BREAKDOWN, "dg_cg_solve: breakdown (<p,Ap> <= 0 or non-finite) at "
+                                       "iteration %d", iters);
+    if (rel <= rtol) return DG_OK;
+    if (iters >= maxit || restarts >= max_restarts)
+      return dg_fail(DG_ERR_NOT_CONVERGED,
+                     "dg_cg_solve: relative residual %.3e > rtol %.3e after %d iterations", rel,
+                     rtol, iters);
+    ++restarts;  // recursive residual drifted from the true one: restart from x
+  }
+}
+
+// FP32 CG recurrence with FP64 residual refinement (search direction kept).
+int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_cg_stats* st,
+             cudaStream_t s) {
+  const double delta = 0.1;
+  const long long n = m->ndofs;
+  double res2 = 0, b2 = 0;
+  int rc = true_residual(m, b, x, s, &res2, &b2);
+  if (rc) return rc;
+  if (b2 == 0.0) return zero_solution(m, x, st, s);
+  rc = set_state(m, maxit, 0, s);
+  if (rc) return rc;
+  // q32 = (float) r64 is the right-hand side of k_init and d32 = 0 the initial
+  // correction, so r32 = p32 = (float) r64.
+  const unsigned vblocks = (unsigned)(m->sm_count * 8);
+  k_scale_to_f32<<<vblocks, 256, 0, s>>>(m->r64, m->q32, m->d32, n, 1.0);
+  k_init<float><<<RED_LAUNCH>>>(m->q32, m->d32, m->r32, m->p32, n, rtol, m->partials,
+                                m->state);
+  DG_CUDA(cudaGetLastError());
+  // FP64 tolerance and reference norm from the FP64 residual
+  DG_CUDA(cudaMemcpyAsync(m->state_host, m->state, sizeof(DGCGState), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  {
+    DGCGState h = *m->state_host;
+    h.bnorm2 = b2;
+    h.tol2 = rtol * rtol * b2;
+    h.rmax2 = res2;
+    h.delta2 = delta * delta;
+    h.done = h.breakdown || res2 <= h.tol2;
+    h.ru_skip = 1;
+    *m->state_host = h;
+    DG_CUDA(cudaMemcpyAsync(m->state, m->state_host, sizeof(DGCGState), cudaMemcpyHostToDevice,
+                            s));
+  }
+  rc = run_graph(m, s, chunk_for(m), [&] { return launch_iteration_mixed(m, b, x, s); });
+  if (rc) return rc;
+  const DGCGState hs = *m->state_host;
+  rc = true_residual(m, b, x, s, &res2, &b2);
+  if (rc) return rc;
+  const double rel = std::sqrt(res2 / b2);
+  if (st) {
+    st->iterations = hs.iters;
+    st->outer_iterations = hs.n_refine;
+    st->rel_residual = rel;
+    st->rel_residual_rec = std::sqrt(hs.rho_new / b2);
+  }
+  if (hs.breakdown)
+    return dg_fail(DG_ERR_BREAKDOWN, "dg_cg_solve(mixed): breakdown at iteration %d", hs.iters);
+  if (rel <= rtol) return DG_OK;
+  return dg_fail(DG_ERR_NOT_CONVERGED,
+                 "dg_cg_solve(mixed): relative residual %.3e > rtol %.3e after %d iterations "
+                 "(%d refinements)", rel, rtol, hs.iters, hs.n_refine);
+}
+
+// Classical refinement: restart an FP32 CG from zero for every correction.
+int cg_mixed_restart(dg_mesh* m, const double* b, double* x, double rtol, int maxit,
+                     dg_cg_stats* st, cudaStream_t s) {
+  const int max_outer = 60;
+  const double inner_tol = 0.1;  // relative reduction per refinement step
+  const long long n = m->ndofs;
+  const unsigned vblocks = (unsigned)(m->sm_count * 8);
+  int inner_total = 0;
+  double res2 = 0, b2 = 0;
+  for (int outer = 0;; ++outer) {
+    int rc = true_residual(m, b, x, s, &res2, &b2);
+    if (rc) return rc;
+    if (b2 == 0.0) return zero_solution(m, x, st, s);
+    const double rn = std::sqrt(res2);
+    const double rel = rn / std::sqrt(b2);
+    if (st) {
+      st->iterations = inner_total;
+      st->outer_iterations = outer;
+      st->rel_residual = rel;
+      st->rel_residual_rec = rel;
+    }
+    if (!std::isfinite(rel))
+      return dg_fail(DG_ERR_BREAKDOWN, "dg_cg_solve(mixed restart): non-finite residual");
+    if (rel <= rtol) return DG_OK;
+    if (outer >= max_outer || inner_total >= maxit)
+      return dg_fail(DG_ERR_NOT_CONVERGED,
+                     "dg_cg_solve(mixed restart): relative residual %.3e > rtol %.3e after %d "
+                     "outer / %d inner iterations", rel, rtol, outer, inner_total);
+    k_scale_to_f32<<<vblocks, 256, 0, s>>>(m->r64, m->q32, m->d32, n, 1.0 / rn);
+    DG_CUDA(cudaGetLastError());
+    rc = set_state(m, maxit - inner_total, 0, s);
+    if (rc) return rc;
+    k_init<float><<<RED_LAUNCH>>>(m->q32, m->d32, m->r32, m->p32, n, inner_tol, m->partials,
+                                  m->state);
+    DG_CUDA(cudaGetLastError());
+    rc = run_graph(m, s, chunk_for(m), [&] {
+      return launch_iteration<float>(m, m->d32, m->r32, m->p32, m->q32, s);
+    });
+    if (rc) return rc;
+    const DGCGState hs = *m->state_host;
+    inner_total += hs.iters;
+    if (hs.breakdown && hs.iters == 0)
+      return dg_fail(DG_ERR_BREAKDOWN, "dg_cg_solve(mixed restart): inner CG breakdown");
+    k_axpy_f32_into_f64<<<vblocks, 256, 0, s>>>(x, m->d32, n, rn);
+    DG_CUDA(cudaGetLastError());
+  }
+}
+
+}  // namespace
+
+extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double rtol, int maxit,
+                           int mode, dg_cg_stats* st, void* stream) {
+  if (mc == nullptr) return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: mesh is NULL");
+  if (!mc->has_coef) return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: coefficient not set");
+  if (b == nullptr || x == nullptr) return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: NULL vector");
+  if (b == x) return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: b and x alias");
+  if (!(rtol > 0.0) || !(rtol < 1.0))
+    return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: rtol=%g outside (0, 1)", rtol);
+  if (maxit < 1) return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: maxit=%d < 1", maxit);
+  if (mode != DG_CG_FP64 && mode != DG_CG_MIXED_IR && mode != DG_CG_MIXED_IR_RESTART)
+    return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: unknown mode %d", mode);
+  dg_mesh* m = const_cast<dg_mesh*>(mc);
+  int rc = dg_ensure_solver_ws(m);
+  if (rc) return rc;
+  const double t0 = now_s();
+  // order the solve after the caller's prior work on its stream
+  DG_CUDA(cudaEventRecord(m->ev, (cudaStream_t)stream));
+  DG_CUDA(cudaStreamWaitEvent(m->solve_stream, m->ev, 0));
+  if (st) *st = dg_cg_stats{};
+  cudaStream_t s = m->solve_stream;
+  if (mode == DG_CG_FP64)
+    rc = cg_fp64(m, b, x, rtol, maxit, st, s);
+  else if (mode == DG_CG_MIXED_IR)
+    rc = cg_mixed(m, b, x, rtol, maxit, st, s);
+  else
+    rc = cg_mixed_restart(m, b, x, rtol, maxit, st, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (rc == DG_OK && e != cudaSuccess) rc = dg_cuda_fail(e, "dg_cg_solve: synchronize");
+  if (st) {
+    st->seconds = now_s() - t0;
+    st->status = rc;
+  }
+  return rc;
+}

@@ -1,0 +1,135 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/dg.h"
+
+#define DG_MAXN 9  // points (= modes) per direction, degree <= 8
+
+// 1D tables on the reference interval [0,1] for n = degree + 1 Gauss points.
+// Passed to kernels by value (kernel parameters live in constant memory, so
+// every table entry is a uniform constant operand).
+template <typename T>
+struct DGTab {
+  T B[DG_MAXN][DG_MAXN];   // B[a][i]  = L_i(xi_a)      modal -> nodal values
+  T Bd[DG_MAXN][DG_MAXN];  // Bd[a][i] = L_i'(xi_a)     modal -> nodal derivative
+  T D[DG_MAXN][DG_MAXN];   // D[a][b]  = l_b'(xi_a)     nodal collocation derivative
+  T w[DG_MAXN];            // Gauss weights on [0,1] (sum 1)
+  T a0[DG_MAXN], a1[DG_MAXN];    // L_i(0), L_i(1)
+  T d0[DG_MAXN], d1[DG_MAXN];    // L_i'(0), L_i'(1)
+  T l0[DG_MAXN], l1[DG_MAXN];    // l_a(0), l_a(1)     (Lagrange basis on the Gauss points)
+  T dl0[DG_MAXN], dl1[DG_MAXN];  // l_a'(0), l_a'(1)
+  T sigma;                        // penalty factor 2(k+1)^2 (dimensionless)
+};
+
+// Host-side construction of the FP64 tables (dg_tables.cpp) and rounding to FP32.
+void dg_build_tables(int n, double sigma, DGTab<double>* t64, DGTab<float>* t32);
+
+// CG scalar state kept on the device (one per solve / per batched sample).
+struct DGCGState {
+  double rho;       // <r, r> of the current residual
+  double pq;        // <p, A p>
+  double alpha;     // rho / pq
+  double beta;      // rho_new / rho
+  double tol2;      // (stopping tolerance)^2 for <r, r>
+  double bnorm2;    // <b, b>
+  double res2;      // ||b - A x||^2 of the last true-residual check
+  double b2;        // ||b||^2 of the last true-residual check
+  double rho_new;   // <r, r> after the current update (mixed mode)
+  double rmax2;     // ||r||^2 at the last FP64 residual refinement (mixed mode)
+  double delta2;    // refine when <r,r> drops below delta2 * rmax2 (mixed mode)
+  int done;         // 1 once converged, broken down or out of iterations
+  int breakdown;    // 1 if pq <= 0 or a scalar became non-finite
+  int iters;        // iterations performed
+  int maxit;        // iteration cap
+  unsigned int ticket;  // completion counter of the last-block reductions
+  int ru_skip;      // 0 when this iteration ends with an FP64 refinement (mixed mode)
+  int n_refine;     // FP64 residual refinements performed (mixed mode)
+  int pad;
+};
+
+struct dg_mesh {
+  int N;            // cells per direction
+  int k;            // degree
+  int n;            // points per direction = k + 1
+  long long ncells; // N^3
+  long long ndofs;  // N^3 n^3
+  double h;
+  double sigma;
+  int device;
+  int sm_count;
+  DGTab<double> tab64;
+  DGTab<float> tab32;
+
+  // coefficient data (dg_set_coefficient)
+  bool has_coef;
+  double* kt64;     // h w_q K_{c,q}                  [c][q]
+  float* kt32;
+  double* gh64;     // h gamma_F per face side        [c][6] (x-, x+, y-, y+, z-, z+)
+  float* gh32;
+  double* dgam;     // d gamma_F / d log Kbar_c       [c][6]
+  double* kbar;     // Kbar_c                          [c]
+  int* dflag;       // device-side error flag of the setup kernels
+
+  // apply workspaces: nodal values, x-modal/yz-nodal values, face traces
+  double *U64, *X64, *TR64;
+  float *U32, *X32, *TR32;
+  // second set for the coefficient gradient (traces of v), lazily allocated
+  double *U64b, *X64b, *TR64b;
+  // host staging for dg_apply_host
+  void *hx_dev, *hy_dev;
+
+  // solver workspaces, lazily allocated
+  double *r64, *p64, *q64, *t64;
+  float *d32, *r32, *p32, *q32;
+  double* partials;       // reduction partials (DG_RED_BLOCKS doubles x 2)
+  DGCGState* state;       // device CG state
+  DGCGState* state_host;  // pinned mirror
+  cudaStream_t solve_stream;
+  cudaEvent_t ev;
+
+  // optional per-pass kernel timing (dg_timing_enable / dg_timing_read)
+  cudaEvent_t* tev;       // 3 events per recorded application
+  int tev_cap;            // applications the event array holds
+  int tev_used;           // applications recorded so far
+  bool timing;
+};
+
+// record the timing event `slot` (0 before pass 1, 1 between passes, 2 after
+// pass 2) of the current application when timing is enabled (dg_mesh.cu)
+void dg_timing_mark(const dg_mesh* m, int slot, cudaStream_t s);
+
+// Deterministic two-level reductions use this fixed grid.
+#define DG_RED_BLOCKS 608   // 4 x 152 SMs
+#define DG_RED_THREADS 256
+
+// error reporting (dg_mesh.cu)
+int dg_fail(int code, const char* fmt, ...);
+int dg_cuda_fail(cudaError_t e, const char* what);
+#define DG_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e__ = (call);                           \
+    if (e__ != cudaSuccess) return dg_cuda_fail(e__, #call); \
+  } while (0)
+
+// launchers (dg_apply_f64.cu / dg_apply_f32.cu)
+int dg_launch_apply_f64(const dg_mesh* m, const double* x, double* y, const int* skip,
+                        cudaStream_t s);
+int dg_launch_apply_f32(const dg_mesh* m, const float* x, float* y, const int* skip,
+                        cudaStream_t s);
+// traces only (used by the coefficient gradient): U, X, TR of x into the given buffers
+int dg_launch_trace_f64(const dg_mesh* m, const double* x, double* U, double* X, double* TR,
+                        cudaStream_t s);
+int dg_launch_coeff_grad(const dg_mesh* m, double* g, cudaStream_t s);
+// one-time kernel attributes (dynamic shared memory) for points-per-direction n
+int dg_prepare_apply_f64(int n);
+int dg_prepare_apply_f32(int n);
+int dg_prepare_grad(int n);
+
+// workspace helpers (dg_mesh.cu)
+int dg_ensure_solver_ws(dg_mesh* m);
+int dg_ensure_grad_ws(dg_mesh* m);

@@ -1,0 +1,153 @@
+"""GPU CG solves (FP64 and mixed-precision iterative refinement) checked by the
+oracle: the residual b - A x of the returned x is recomputed in FP64 on the
+host, and x is compared with a direct solve within the conditioning bound."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import SIPG
+from paper_1911_01492_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dg(cuda_device):
+    import paper_1911_01492_gb300 as dg
+    dg.library()
+    return dg
+
+
+def u_exact(x, y, z):
+    return np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+
+
+def f_exact(x, y, z):
+    return 3 * np.pi ** 2 * u_exact(x, y, z)
+
+
+def oracle_rel_residual(D, K, b, x):
+    return float(np.linalg.norm(b - D.apply(K, x)) / np.linalg.norm(b))
+
+
+def test_cg_fp64_manufactured_8cubed_q2(dg):
+    """8^3 Q2, K = 1, f from u = sin sin sin, CG to 1e-10."""
+    import torch
+    N, k = 8, 2
+    D = SIPG(N, k)
+    K = inputs.unit_coefficient(N, k)
+    b = D.load_vector(f_exact)
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(K).cuda())
+    x, st = m.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-10)
+    x = x.cpu().numpy()
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-10
+    assert oracle_rel_residual(D, K, b, x) <= 1.05e-10
+    xd = spla.spsolve(D.assemble(K).tocsc(), b)
+    assert np.linalg.norm(x - xd) <= 1e-10 * 2.3e3 * 10 * np.linalg.norm(xd)
+    # the discrete solution approximates u to O(h^3)
+    assert D.l2_error(x, u_exact) < 2e-3
+
+
+def small_mesh_field(N, k, seed):
+    """Lognormal K with the per-cell statistics of the 64^3 workload: the
+    correlation length is scaled so that it spans the same number of cells
+    (0.1 at N = 64).  With the unscaled length 0.1 a coarse cell spans several
+    correlation lengths and the SIPG matrix can be indefinite (see
+    test_cg_reports_indefinite_coarse_mesh)."""
+    return inputs.lognormal_coefficient(N, k, seed=seed, corr_len=0.1 * 64 / N)
+
+
+@pytest.mark.parametrize("N,k,seed", [(4, 3, 5), (5, 2, 6), (3, 4, 4)])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_cg_lognormal_residual_checked_by_oracle(dg, N, k, seed, mode):
+    import torch
+    D = SIPG(N, k)
+    K = small_mesh_field(N, k, seed)
+    b = inputs.constant_load_vector(N, k)
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(K).cuda())
+    x, st = m.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-10, mode=mode)
+    x = x.cpu().numpy()
+    assert st["status"] == 0
+    assert oracle_rel_residual(D, K, b, x) <= 1.05e-10
+    if mode == 1:
+        assert st["outer_iterations"] >= 1
+
+
+def test_cg_nonzero_initial_guess_and_zero_rhs(dg):
+    import torch
+    N, k = 3, 3
+    D = SIPG(N, k)
+    K = small_mesh_field(N, k, 9)
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(K).cuda())
+    b = inputs.uniform_vector(N, k, 10)
+    x0 = torch.from_numpy(inputs.uniform_vector(N, k, 11)).cuda()
+    x, st = m.cg_solve(torch.from_numpy(b).cuda(), x=x0, rtol=1e-11)
+    assert oracle_rel_residual(D, K, b, x.cpu().numpy()) <= 1.05e-11
+    z = torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda")
+    x, st = m.cg_solve(z.clone(), x=torch.ones_like(z), rtol=1e-10)
+    assert st["status"] == 0
+
+
+def test_cg_maxit_reports_not_converged(dg):
+    import torch
+    N, k = 4, 2
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(inputs.unit_coefficient(N, k)).cuda())
+    b = torch.from_numpy(inputs.constant_load_vector(N, k)).cuda()
+    x, st = m.cg_solve(b, rtol=1e-12, maxit=5, raise_on_error=False)
+    assert st["status"] == dg.DG_ERR_NOT_CONVERGED
+    assert st["iterations"] == 5
+    with pytest.raises(dg.DGError, match="NOT_CONVERGED"):
+        m.cg_solve(b, rtol=1e-12, maxit=5)
+
+
+def test_cg_non_finite_rhs_reports_breakdown(dg):
+    import torch
+    N, k = 2, 2
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(inputs.unit_coefficient(N, k)).cuda())
+    b = torch.from_numpy(inputs.uniform_vector(N, k, 3)).cuda()
+    b[5] = float("nan")
+    x, st = m.cg_solve(b, rtol=1e-10, raise_on_error=False)
+    assert st["status"] == dg.DG_ERR_BREAKDOWN
+
+
+def test_invalid_coefficient_and_aliasing_are_rejected(dg):
+    import torch
+    N, k = 2, 2
+    m = dg.Mesh(N, k)
+    K = torch.from_numpy(inputs.unit_coefficient(N, k)).cuda()
+    K[7] = -1.0
+    with pytest.raises(dg.DGError, match="INVALID_ARG"):
+        m.set_coefficient(K)
+    x = torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda")
+    with pytest.raises(dg.DGError, match="coefficient not set"):
+        m.apply(x)
+    K[7] = float("inf")
+    with pytest.raises(dg.DGError, match="INVALID_ARG"):
+        m.set_coefficient(K)
+    K[7] = 1.0
+    m.set_coefficient(K)
+    with pytest.raises(dg.DGError, match="alias"):
+        m.apply(x, x)
+    with pytest.raises(TypeError):
+        m.apply(x.to(torch.int64))
+
+
+def test_cg_reports_indefinite_coarse_mesh(dg):
+    """3^3 Q4 with correlation length 0.1: K varies by ~1000x inside a cell and
+    the SIPG matrix has two negative eigenvalues (pinned in the oracle tests).
+    Both solvers must report the failure instead of returning a solution."""
+    import torch
+    N, k = 3, 4
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(inputs.lognormal_coefficient(N, k, seed=4)).cuda())
+    b = torch.from_numpy(inputs.constant_load_vector(N, k)).cuda()
+    for mode in (0, 1):
+        x, st = m.cg_solve(b, rtol=1e-10, maxit=3000, mode=mode, raise_on_error=False)
+        assert st["status"] in (dg.DG_ERR_BREAKDOWN, dg.DG_ERR_NOT_CONVERGED), st

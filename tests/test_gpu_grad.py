@@ -1,0 +1,121 @@
+"""Differentiation through the operator and the solve (autograd layer over the
+C ABI), checked against the oracle's gradient and central finite differences."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import SIPG
+from paper_1911_01492_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dg(cuda_device):
+    import paper_1911_01492_gb300 as dg
+    dg.library()
+    return dg
+
+
+def test_apply_gradients_match_oracle(dg):
+    import torch
+    from paper_1911_01492_gb300 import autograd as dga
+    N, k = 3, 2
+    D = SIPG(N, k)
+    K = inputs.lognormal_coefficient(N, k, seed=3)
+    x = torch.from_numpy(inputs.uniform_vector(N, k, 4)).cuda().requires_grad_()
+    w = torch.from_numpy(inputs.uniform_vector(N, k, 5)).cuda()
+    logK = torch.from_numpy(np.log(K)).cuda().requires_grad_()
+    m = dg.Mesh(N, k)
+    y = dga.apply(x, logK, m)
+    (w * y).sum().backward()
+    A = D.assemble(K)
+    gx_ref = A.T @ w.cpu().numpy()
+    gk_ref = D.coeff_grad(K, x.detach().cpu().numpy(), w.cpu().numpy()).reshape(-1)
+    gx = x.grad.cpu().numpy()
+    gk = logK.grad.cpu().numpy()
+    assert np.abs(gx - gx_ref).max() <= 1e-12 * np.abs(gx_ref).max()
+    assert np.abs(gk - gk_ref).max() <= 1e-12 * np.abs(gk_ref).max()
+
+
+def test_apply_gradcheck_tiny(dg):
+    import torch
+    from paper_1911_01492_gb300 import autograd as dga
+    N, k = 2, 1
+    m = dg.Mesh(N, k)
+    x = torch.from_numpy(inputs.uniform_vector(N, k, 6)).cuda().requires_grad_()
+    logK = torch.from_numpy(0.3 * inputs.uniform_vector(N, k, 7)).cuda().requires_grad_()
+    assert torch.autograd.gradcheck(lambda a, b: dga.apply(a, b, m), (x, logK), eps=1e-6,
+                                    atol=1e-7, rtol=1e-6)
+
+
+def observed_solution(D, K_ref_np, b, seed):
+    A = D.assemble(K_ref_np).tocsc()
+    u = spla.spsolve(A, b)
+    rng = np.random.default_rng(seed)
+    return u + 0.01 * np.sqrt(np.mean(u ** 2)) * rng.standard_normal(u.shape)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_solve_gradient_matches_oracle_on_4cubed(dg, k):
+    """dL/dlogK for L = 0.5 ||u(K) - u_obs||^2 against the oracle's assembled
+    adjoint gradient -g(u, A^{-1}(u - u_obs))."""
+    import torch
+    from paper_1911_01492_gb300 import autograd as dga
+    N = 4
+    D = SIPG(N, k)
+    K = inputs.lognormal_coefficient(N, k, seed=5)
+    b = inputs.constant_load_vector(N, k)
+    u_obs = observed_solution(D, inputs.lognormal_coefficient(N, k, seed=40), b, 41)
+    A = D.assemble(K).tocsc()
+    u = spla.spsolve(A, b)
+    lam = spla.spsolve(A, u - u_obs)
+    g_ref = -D.coeff_grad(K, u, lam).reshape(-1)
+
+    m = dg.Mesh(N, k)
+    logK = torch.from_numpy(np.log(K)).cuda().requires_grad_()
+    bd = torch.from_numpy(b).cuda()
+    ud = dga.solve(bd, logK, m, rtol=1e-13)
+    L = 0.5 * ((ud - torch.from_numpy(u_obs).cuda()) ** 2).sum()
+    L.backward()
+    g = logK.grad.cpu().numpy()
+    assert np.abs(g - g_ref).max() <= 1e-8 * np.abs(g_ref).max()
+
+
+@pytest.mark.slow
+def test_solve_gradient_central_differences_32cubed_q3(dg):
+    """32^3 Q3 lognormal K: gradient by adjoint CG against central finite
+    differences along 20 seeded directions (eps = 1e-4, solves to 1e-12)."""
+    import torch
+    from paper_1911_01492_gb300 import autograd as dga
+    N, k = 32, 3
+    m = dg.Mesh(N, k)
+    b = torch.from_numpy(inputs.constant_load_vector(N, k)).cuda()
+    Kref = torch.from_numpy(inputs.lognormal_coefficient(N, k, seed=40)).cuda()
+    m.set_coefficient(Kref)
+    uref, _ = m.cg_solve(b, rtol=1e-12, mode=1)
+    rng = np.random.default_rng(41)
+    rms = float(torch.sqrt(torch.mean(uref ** 2)))
+    u_obs = uref + 0.01 * rms * torch.from_numpy(rng.standard_normal(m.n_dofs)).cuda()
+    logK = torch.from_numpy(np.log(inputs.lognormal_coefficient(N, k, seed=5))).cuda()
+
+    def loss(lk):
+        m._logk_key = None
+        u = dga.solve(b, lk, m, rtol=1e-12, mode=1)
+        return 0.5 * float(((u - u_obs) ** 2).sum())
+
+    lk = logK.clone().requires_grad_()
+    u = dga.solve(b, lk, m, rtol=1e-12, mode=1)
+    (0.5 * ((u - u_obs) ** 2).sum()).backward()
+    g = lk.grad.clone()
+    drng = np.random.default_rng(42)
+    eps = 1e-4
+    worst = 0.0
+    for _ in range(20):
+        d = torch.from_numpy(drng.standard_normal(m.n_dofs)).cuda()
+        fd = (loss(logK + eps * d) - loss(logK - eps * d)) / (2 * eps)
+        an = float(torch.dot(g, d))
+        worst = max(worst, abs(fd - an) / abs(an))
+    assert worst <= 1e-4, worst

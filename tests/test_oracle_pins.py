@@ -206,6 +206,18 @@ def test_positive_definite_under_lognormal_coefficient(N, k, seed):
     assert np.linalg.eigvalsh(A)[0] > 0
 
 
+def test_coarse_cells_with_strong_coefficient_variation_can_be_indefinite():
+    """A limitation of the per-cell face coefficient: on 3^3 Q4 with correlation
+    length 0.1 (a cell spans ~3 correlation lengths, K varies ~1000x inside it)
+    the face terms outweigh the local volume term and A has negative
+    eigenvalues.  With the workload's per-cell statistics it is SPD."""
+    D = SIPG(3, 4)
+    ev = np.linalg.eigvalsh(D.assemble(inputs.lognormal_coefficient(3, 4, seed=4)).toarray())
+    assert (ev < 0).sum() == 2
+    K = inputs.lognormal_coefficient(3, 4, seed=4, corr_len=0.1 * 64 / 3)
+    assert np.linalg.eigvalsh(D.assemble(K).toarray())[0] > 0
+
+
 def test_smallest_eigenvalue_approaches_continuum():
     # lambda_min(M^-1 A) -> 3 pi^2 for -Laplace on the unit cube, M = h^3 I
     D = SIPG(8, 2)
