@@ -144,6 +144,23 @@ int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, const double* c
 int dg_timing_enable(dg_mesh* mesh, int max_applies);
 int dg_timing_read(dg_mesh* mesh, int* n_applies, double* ms_pass1, double* ms_pass2);
 
+/* y = A(K) x in FP64, for callers that cannot allocate device memory (the
+ * paper has no counterpart; this is a deployment variant of dg_apply).
+ * Callers that cannot call cudaMalloc -- code inside a captured CUDA graph,
+ * allocator-free runtimes, or frameworks that own every device allocation --
+ * pass K (FP64 at the volume Gauss points, layout as dg_set_coefficient), x and
+ * y (FP64, n_cells^3 (degree+1)^3 values, device pointers) and get y without
+ * any allocation.  Temporaries live in a 64 MiB file-scope device array that
+ * every GPU loading the library holds until exit; sizes whose temporaries do
+ * not fit (about 50 bytes per DOF, e.g. more than 27^3 cells at degree 3)
+ * return INVALID_ARG with the needed size.  The first call on a device looks up
+ * the array's device address, so it should come before any stream capture.
+ * The array is shared by all calls: calls that overlap on the GPU race.
+ * Blocks until y is written (it reads back the K validity flag); K <= 0 or
+ * non-finite returns INVALID_ARG.  Calls no cudaMalloc/cudaFree. */
+int dg_apply_static(int n_cells, int degree, const double* K, const double* x, double* y,
+                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

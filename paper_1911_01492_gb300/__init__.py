@@ -56,6 +56,7 @@ _SIGS = {
     "dg_cg_solve_batched": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int,
                                            ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                            ctypes.c_double, ctypes.c_int, _VP, _VP]),
+    "dg_apply_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "dg_timing_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "dg_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_double),
@@ -255,6 +256,20 @@ def cg_solve_batched(meshes, bs, xs, rtol: float = 1e-8, maxit: int = 100000, st
     if raise_on_error:
         _check(rc, "dg_cg_solve_batched")
     return [s.as_dict() for s in st]
+
+
+def apply_static(n_cells: int, degree: int, K, x, y=None, stream=None):
+    """y = A(K) x in FP64 without any device allocation by the library (its
+    temporaries live in a fixed 64 MiB device array; see dg_apply_static).
+    For callers that cannot allocate; everyone else should use Mesh."""
+    import torch
+    nd = n_cells ** 3 * (degree + 1) ** 3
+    if y is None:
+        y = torch.empty_like(x)
+    _check(library().dg_apply_static(int(n_cells), int(degree), _ptr(K, _f64(), nd, "K"),
+                                      _ptr(x, _f64(), nd, "x"), _ptr(y, _f64(), nd, "y"),
+                                      _stream(stream)), "dg_apply_static")
+    return y
 
 
 def _f64():

@@ -1,0 +1,51 @@
+"""dg_apply_static: the operator application for callers that cannot allocate
+device memory (code inside a captured CUDA graph, allocator-free runtimes,
+frameworks that own all device allocations).  Its temporaries live in a fixed
+file-scope device array instead of cudaMalloc'd workspaces.  This test calls it
+through the C ABI and compares it with dg_apply on two calls in a row; the
+second call runs on a different mesh after the first has filled the shared
+array, so a stale temporary would show.  This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1911_01492_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def test_static_apply_matches_dg_apply_on_two_calls_in_a_row(cuda_device):
+    import torch
+    import paper_1911_01492_gb300 as dg
+    lib = dg.library()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for (N, k, kseed, xseed) in [(6, 3, 7, 8), (5, 4, 9, 10)]:
+        K = torch.from_numpy(inputs.lognormal_coefficient(N, k, seed=kseed)).cuda()
+        x = torch.from_numpy(inputs.uniform_vector(N, k, xseed)).cuda()
+        m = dg.Mesh(N, k)
+        m.set_coefficient(K)
+        y_ref = m.apply(x)
+        y = torch.full_like(x, float("nan"))
+        rc = lib.dg_apply_static(N, k, _vp(K), _vp(x), _vp(y), stream)
+        assert rc == dg.DG_OK, lib.dg_last_error().decode()
+        torch.cuda.synchronize()
+        err = float((y - y_ref).abs().max() / y_ref.abs().max())
+        assert err <= TOL64, (N, k, err)
+
+
+def test_static_apply_rejects_sizes_beyond_its_array(cuda_device):
+    import torch
+    import paper_1911_01492_gb300 as dg
+    lib = dg.library()
+    z = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rc = lib.dg_apply_static(40, 3, _vp(z), _vp(z), _vp(torch.zeros_like(z)), None)
+    assert rc == dg.DG_ERR_INVALID_ARG
+    assert b"static scratch" in lib.dg_last_error()
