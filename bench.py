@@ -29,8 +29,14 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = {"n_cells": 64, "degree": 3, "K": "lognormal", "K_seed": 2, "x_seed": 3}
 CG_WORKLOAD = {"n_cells": 48, "degree": 4, "K": "lognormal", "K_seed": 4, "rtol": 1e-10}
+# 256 lognormal samples on three uneven levels (multilevel Monte-Carlo shape)
+BATCH_LEVELS = [(128, 16, 2), (96, 24, 3), (32, 32, 4)]   # (samples, n_cells, degree)
 METRIC = "SIPG-DG apply GDOF/s (FP64)"
 NOMINAL_FP64_TFLOPS = 1.25   # GB300 FP64 rate: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
+# DRAM bytes (read + write) of one k_cell<4,double> launch, from an ncu capture
+# of the 40^3 Q3 case (318.9 MB for 4,096,000 DOFs) scaled by DOFs to 64^3 Q3;
+# must be re-measured whenever k_cell changes.
+K_CELL_TRAFFIC_PER_DOF = 318.9e6 / 4096000
 
 
 def flops_per_dof(n: int):
@@ -135,27 +141,24 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-def run_cpu_baseline(K, x, N, k, target_s: float = 12.0):
-    """Time the oracle's element-wise apply on a bounded sample of cells."""
-    import numpy as np
+def run_cpu_baseline(K, x, N, k, target_s: float = 10.0):
+    """Time the oracle's element-wise apply (the whole mesh, repeated until
+    target_s seconds of CPU work have been timed)."""
     from oracle import SIPG
     D = SIPG(N, k)
     n3 = (k + 1) ** 3
-    rng = np.random.default_rng(0)
-    ncell = 512
-    D.apply(K, x, cells=rng.choice(N ** 3, 64, replace=False))      # warm up BLAS
-    t0 = time.perf_counter()
-    D.apply(K, x, cells=rng.choice(N ** 3, ncell, replace=False))
-    dt = time.perf_counter() - t0
-    ncell = int(min(N ** 3, max(ncell, ncell * target_s / max(dt, 1e-3))))
-    cells = rng.choice(N ** 3, ncell, replace=False)
-    t0 = time.perf_counter()
-    D.apply(K, x, cells=cells)
-    dt = time.perf_counter() - t0
-    return {"value": ncell * n3 / dt / 1e9, "unit": "GDOF/s", "cores": cpu_threads(),
+    D.apply(K, x, cells=list(range(64)))                 # warm up BLAS
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        D.apply(K, x)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= target_s:
+            break
+    return {"value": reps * N ** 3 * n3 / dt / 1e9, "unit": "GDOF/s", "cores": cpu_threads(),
             "kind": "oracle",
-            "sample": f"element-wise FP64 apply (full 3D quadrature tables) on {ncell} random "
-                      f"cells of the {N}^3 Q{k} mesh ({ncell * n3} DOFs), {dt:.1f} s"}
+            "sample": f"element-wise FP64 apply (full 3D quadrature tables) of the whole {N}^3 "
+                      f"Q{k} mesh ({N ** 3 * n3} DOFs), {reps} times in {dt:.1f} s"}
 
 
 def cpu_threads() -> int:
@@ -273,6 +276,63 @@ def run_cg(world):
     return out
 
 
+def run_batched(world, rank, sequential_samples: int = 0):
+    """Batched lock-step CG over 256 samples (FP64, rtol 1e-8): aggregate DOF/s of
+    the persistent batched solve, and of one sample per dg_cg_solve call."""
+    import torch
+    import paper_1911_01492_gb300 as dg
+    from paper_1911_01492_gb300 import inputs
+    meshes, bs, xs, sizes = [], [], [], []
+    s = 0
+    for count, N, k in BATCH_LEVELS:
+        for _ in range(count):
+            m = dg.Mesh(N, k)
+            m.set_coefficient(torch.from_numpy(
+                inputs.lognormal_coefficient(N, k, seed=1000 + s)).cuda())
+            meshes.append(m)
+            bs.append(torch.from_numpy(inputs.constant_load_vector(N, k)).cuda())
+            xs.append(torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda"))
+            sizes.append((N, k, m.n_dofs))
+            s += 1
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    stats = dg.cg_solve_batched(meshes, bs, xs, rtol=1e-8, maxit=200000, raise_on_error=False)
+    torch.cuda.synchronize()
+    t_batch = max_over_ranks(time.perf_counter() - t0, world)
+    dof_applies = sum(st["iterations"] * sz[2] for st, sz in zip(stats, sizes))
+    total_dofs = sum(sz[2] for sz in sizes)
+    out = {"workload": "256 lognormal-K samples: 128 x 16^3 Q2, 96 x 24^3 Q3, 32 x 32^3 Q4 "
+                       f"({total_dofs} DOFs), FP64 CG to 1e-8",
+           "batched": {"seconds": t_batch, "gdof_per_s": world * dof_applies / t_batch / 1e9,
+                       "all_converged": all(st["status"] == 0 for st in stats),
+                       "max_rel_residual": max(st["rel_residual"] for st in stats),
+                       "iterations_min_max": [min(st["iterations"] for st in stats),
+                                              max(st["iterations"] for st in stats)]}}
+    if sequential_samples:
+        # one sample per dg_cg_solve call, on the first samples of every level
+        picked = []
+        start = 0
+        for count, N, k in BATCH_LEVELS:
+            picked += list(range(start, start + min(count, sequential_samples)))
+            start += count
+        t_seq, dof_seq = 0.0, 0
+        for i in picked:
+            x = torch.zeros_like(xs[i])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = meshes[i].cg_solve(bs[i], x, rtol=1e-8, maxit=200000)
+            torch.cuda.synchronize()
+            t_seq += time.perf_counter() - t0
+            dof_seq += st["iterations"] * sizes[i][2]
+        out["one_sample_per_launch"] = {"samples": len(picked), "seconds": t_seq,
+                                        "gdof_per_s": dof_seq / t_seq / 1e9}
+        out["speedup_batched"] = out["batched"]["gdof_per_s"] / out["one_sample_per_launch"]["gdof_per_s"]
+    for m in meshes:
+        m.close()
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,6 +342,10 @@ def main(argv=None):
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution part")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--batched", action="store_true",
+                    help="also run the 256-sample batched CG workload")
+    ap.add_argument("--batched-sequential", type=int, default=4,
+                    help="samples per level re-solved one per call for the comparison")
     ap.add_argument("--n-cells", type=int, default=WORKLOAD["n_cells"],
                     help="cells per direction (default: the 64^3 workload)")
     ap.add_argument("--degree", type=int, default=WORKLOAD["degree"])
@@ -316,9 +380,12 @@ def main(argv=None):
     t1, t2 = ms1 / max(napp, 1), ms2 / max(napp, 1)
     dom_ms, dom_flops, dom_name = (t2, f2 * nd, "k_cell") if t2 >= t1 else (t1, f1 * nd, "k_trace")
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
+    traffic = K_CELL_TRAFFIC_PER_DOF * nd if (dom_name == "k_cell" and n == 4) else None
     roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved,
                 "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
+                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_cell "
+                                  "on 40^3 Q3, scaled by DOFs",
                 "peak_source": "nominal GB300 FP64 rate (derived: 152 SMs x 2 DFMA/clk x 2 x "
                                "2.06 GHz); a DFMA throughput probe measured 1.0 TFLOP/s",
                 "pass_ms": {"k_trace": t1, "k_cell": t2},
@@ -342,6 +409,11 @@ def main(argv=None):
         torch.cuda.empty_cache()
         cg = run_cg(world)
 
+    batched = None
+    if args.batched:
+        torch.cuda.empty_cache()
+        batched = run_batched(world, rank, args.batched_sequential)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(K, x, N, k)
@@ -357,6 +429,8 @@ def main(argv=None):
                            "l2": "inputs larger than L2 (x, h w K and y are 134 MB each)"},
                 "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * args.steps,
                 "clocks": clk.summary(), "cpu_baseline": cpu, "cg": cg}
+        if batched is not None:
+            line["batched_cg"] = batched
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

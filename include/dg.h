@@ -152,7 +152,7 @@ int dg_timing_read(dg_mesh* mesh, int* n_applies, double* ms_pass1, double* ms_p
  * y (FP64, n_cells^3 (degree+1)^3 values, device pointers) and get y without
  * any allocation.  Temporaries live in a 64 MiB file-scope device array that
  * every GPU loading the library holds until exit; sizes whose temporaries do
- * not fit (about 50 bytes per DOF, e.g. more than 27^3 cells at degree 3)
+ * not fit (about 75 bytes per DOF, e.g. more than 24^3 cells at degree 3)
  * return INVALID_ARG with the needed size.  The first call on a device looks up
  * the array's device address, so it should come before any stream capture.
  * The array is shared by all calls: calls that overlap on the GPU race.

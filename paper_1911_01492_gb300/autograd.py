@@ -2,7 +2,7 @@
 
 Both functions take log K (the coefficient at the volume Gauss points, CUDA
 float64) as an input so that gradients flow to it; the mesh's coefficient is
-re-derived only when that tensor changes.
+re-derived from it on every forward and backward call.
 
 apply(x, logK, mesh) = A(K) x
     d/dx:     A^T ybar                      (dg_apply_adjoint)
@@ -20,10 +20,9 @@ from . import DG_CG_FP64, Mesh
 
 
 def _ensure_coefficient(mesh: Mesh, logK: torch.Tensor):
-    key = (logK.data_ptr(), logK._version, logK.numel())
-    if getattr(mesh, "_logk_key", None) != key:
-        mesh.set_coefficient(torch.exp(logK.detach()).contiguous())
-        mesh._logk_key = key
+    # Always re-derive: a tensor's storage can change without its version
+    # counter (writes through .data), and the derivation costs one pass over K.
+    mesh.set_coefficient(torch.exp(logK.detach()).contiguous())
 
 
 class ApplyFn(torch.autograd.Function):

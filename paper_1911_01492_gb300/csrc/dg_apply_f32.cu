@@ -6,7 +6,7 @@ int dg_launch_apply_f32(const dg_mesh* m, const float* x, float* y, const int* s
                         cudaStream_t s) {
   cudaError_t e = dgk::dispatch_n<float, dgk::ApplyF>(m->n, m, x, y, m->U32, m->X32, m->TR32,
                                                       (const float*)m->kt32,
-                                                      (const float*)m->gh32, m->ncells, m->N,
+                                                      (const float*)m->fw32, m->ncells, m->N,
                                                       skip, &m->tab32, s);
   if (e != cudaSuccess) return dg_cuda_fail(e, "apply (fp32) launch");
   return DG_OK;

@@ -5,7 +5,7 @@ int dg_launch_apply_f64(const dg_mesh* m, const double* x, double* y, const int*
                         cudaStream_t s) {
   cudaError_t e = dgk::dispatch_n<double, dgk::ApplyF>(m->n, m, x, y, m->U64, m->X64, m->TR64,
                                                        (const double*)m->kt64,
-                                                       (const double*)m->gh64, m->ncells, m->N,
+                                                       (const double*)m->fw64, m->ncells, m->N,
                                                        skip, &m->tab64, s);
   if (e != cudaSuccess) return dg_cuda_fail(e, "apply (fp64) launch");
   return DG_OK;

@@ -9,14 +9,26 @@
 // end values l_a(0|1), l_a'(0|1)).
 //
 // Pass 2 (cell kernel), per cell: reads U, X, the weighted coefficient
-// h w_q K_q, its own face traces and its six neighbours' face traces, and forms
-//   r = sum_d D_d^T (Kt . D_d u)  (collocation derivative along y and z,
-//       L_i' contraction from X along x),
-// adds the face terms -{d_n u}[phi] - {d_n phi}[u] + sigma [u][phi] with weight
-// h gamma_F w_s w_t at each face point, and maps back to modal coefficients
-// with B^T along x, y, z.  No FP64 work is repeated between the passes: the
-// only duplicated arithmetic is the pointwise flux of an interior face, which
-// both of its cells evaluate.
+// Kt_q = h w_q K_q, precomputed face-point weights, its own face traces and its
+// six neighbours' face traces, and forms
+//   r = sum_d D_d^T (Kt . D_d u)   (collocation derivative along y and z;
+//                                   L_i' contraction from X along x),
+// adds the face terms -{d_n u}[phi] - {d_n phi}[u] + sigma [u][phi], and maps
+// back to modal coefficients with B^T along x, y, z.
+//
+// FP64 operations are the scarce resource on GB300 (FP64 runs ~75x slower than
+// FP32), so the kernels minimise them:
+//   * the Gauss points are symmetric about 1/2 and L_i(1 - t) = (-1)^i L_i(t),
+//     so every B, B^T, L', L'^T line contraction splits into even and odd
+//     modes (about n^2/2 + n operations instead of n^2); L_0 = 1 and L_0' = 0
+//     remove further terms;
+//   * x-face traces and x-face test functions use the same parity split;
+//   * face-point weights W/2 = h gamma_F w_s w_t / 2 and the derivative weight
+//     (W/2 inside, W on the boundary) are precomputed when K is set, and
+//     2 sigma = 4 n^2 is a compile-time constant, so a face point costs five
+//     operations.
+// The only duplicated arithmetic is the pointwise flux of an interior face,
+// which both of its cells evaluate.
 //
 // Thread layout: n^2 threads per cell; a block holds CPB cells.  Each thread
 // owns one 1D line of its cell at every stage; lines are exchanged through
@@ -35,36 +47,184 @@ struct Cfg {
   static constexpr int THREADS = CPB * N * N;
 };
 
-// Face flux at one face point (reference units: derivatives d/dxi along +axis,
-// weight W = h gamma_F w_s w_t).  `upper`: this cell is the lower-index (-)
-// side of the face (its xi = 1 face).  Interior:  J = u- - u+, G = g- + g+,
-//   s_v = W (sigma J - G/2),  s_d = -W J / 2;
-// the (-) cell adds  s_v phi + s_d dphi, the (+) cell  -s_v phi + s_d dphi.
-// Boundary faces are the one-sided form with outward normal:
-//   -(d_n u) phi - (d_n phi) u + sigma u phi,
-// obtained from the same expressions with the missing side's value set to 0,
-// its derivative set to the own one, and the factor 1/2 of s_d replaced by 1.
-// Returns the multipliers (cv, cd) of the own test function's value and
-// reference normal derivative.
-template <bool UPPER, typename T>
-__device__ __forceinline__ void face_flux(bool interior, T uo, T go, T un, T gn, T W, T sigma,
-                                          T& cv, T& cd) {
-  T um, gm, up, gp;
-  if (UPPER) {
-    um = uo; gm = go;
-    up = interior ? un : T(0);
-    gp = interior ? gn : go;
-  } else {
-    up = uo; gp = go;
-    um = interior ? un : T(0);
-    gm = interior ? gn : go;
+// ---------------------------------------------------------------------------
+// 1D line contractions with the parity split (H = N/2 mirror pairs a, N-1-a;
+// for odd N the middle point m = N/2 sits at xi = 1/2).
+// ---------------------------------------------------------------------------
+
+// u[a] = sum_i B[a][i] X[i]   (modal -> nodal values)
+template <int N, typename T>
+__device__ __forceinline__ void b_fwd(const DGTab<T>& t, const T (&X)[N], T (&u)[N]) {
+  constexpr int H = N / 2;
+#pragma unroll
+  for (int a = 0; a < H; ++a) {
+    T E = X[0];  // L_0 = 1
+#pragma unroll
+    for (int i = 2; i < N; i += 2) E = fma(t.B[a][i], X[i], E);
+    T O = t.B[a][1] * X[1];
+#pragma unroll
+    for (int i = 3; i < N; i += 2) O = fma(t.B[a][i], X[i], O);
+    u[a] = E + O;
+    u[N - 1 - a] = E - O;
   }
-  const T J = um - up;
-  const T G = gm + gp;
-  const T sv = W * (sigma * J - T(0.5) * G);
-  const T hw = interior ? T(-0.5) * W : -W;
-  cv = UPPER ? sv : -sv;
-  cd = hw * J;
+  if (N % 2 == 1) {  // L_odd(1/2) = 0
+    T E = X[0];
+#pragma unroll
+    for (int i = 2; i < N; i += 2) E = fma(t.B[H][i], X[i], E);
+    u[H] = E;
+  }
+}
+
+// g[a] = sum_i L_i'(xi_a) X[i]   (modal -> nodal derivative; L_1' is constant)
+template <int N, typename T>
+__device__ __forceinline__ void bd_fwd(const DGTab<T>& t, const T (&X)[N], T (&g)[N]) {
+  constexpr int H = N / 2;
+  const T c1 = t.Bd[0][1] * X[1];
+#pragma unroll
+  for (int a = 0; a < H; ++a) {
+    T O = c1;
+#pragma unroll
+    for (int i = 3; i < N; i += 2) O = fma(t.Bd[a][i], X[i], O);
+    if (N > 2) {
+      T E = t.Bd[a][2] * X[2];
+#pragma unroll
+      for (int i = 4; i < N; i += 2) E = fma(t.Bd[a][i], X[i], E);
+      g[a] = O + E;
+      g[N - 1 - a] = O - E;
+    } else {
+      g[a] = O;
+      g[N - 1 - a] = O;
+    }
+  }
+  if (N % 2 == 1) {  // L_even'(1/2) = 0
+    T O = c1;
+#pragma unroll
+    for (int i = 3; i < N; i += 2) O = fma(t.Bd[H][i], X[i], O);
+    g[H] = O;
+  }
+}
+
+// R[i] = sum_a B[a][i] r[a] + sum_a L_i'(xi_a) k[a]   (nodal -> modal, both parts)
+template <int N, typename T>
+__device__ __forceinline__ void bt_bdt(const DGTab<T>& t, const T (&r)[N], const T (&k)[N],
+                                       T (&R)[N]) {
+  constexpr int H = N / 2;
+  T re[H > 0 ? H : 1], ro[H > 0 ? H : 1], ke[H > 0 ? H : 1], ko[H > 0 ? H : 1];
+#pragma unroll
+  for (int a = 0; a < H; ++a) {
+    re[a] = r[a] + r[N - 1 - a];
+    ro[a] = r[a] - r[N - 1 - a];
+    ke[a] = k[a] + k[N - 1 - a];
+    ko[a] = k[a] - k[N - 1 - a];
+  }
+  // i = 0: L_0 = 1, L_0' = 0
+  {
+    T acc = re[0];
+#pragma unroll
+    for (int a = 1; a < H; ++a) acc = acc + re[a];
+    if (N % 2 == 1) acc = acc + r[H];
+    R[0] = acc;
+  }
+#pragma unroll
+  for (int i = 1; i < N; ++i) {
+    T acc;
+    if (i % 2 == 0) {  // even mode: value part symmetric, derivative part antisymmetric
+      acc = t.B[0][i] * re[0];
+#pragma unroll
+      for (int a = 1; a < H; ++a) acc = fma(t.B[a][i], re[a], acc);
+      if (N % 2 == 1) acc = fma(t.B[H][i], r[H], acc);
+#pragma unroll
+      for (int a = 0; a < H; ++a) acc = fma(t.Bd[a][i], ko[a], acc);
+    } else {           // odd mode: value part antisymmetric, derivative part symmetric
+      acc = t.B[0][i] * ro[0];
+#pragma unroll
+      for (int a = 1; a < H; ++a) acc = fma(t.B[a][i], ro[a], acc);
+#pragma unroll
+      for (int a = 0; a < H; ++a) acc = fma(t.Bd[a][i], ke[a], acc);
+      if (N % 2 == 1) acc = fma(t.Bd[H][i], k[H], acc);
+    }
+    R[i] = acc;
+  }
+}
+
+// R[i] = sum_a B[a][i] r[a]   (nodal -> modal values)
+template <int N, typename T>
+__device__ __forceinline__ void b_bwd(const DGTab<T>& t, const T (&r)[N], T (&R)[N]) {
+  constexpr int H = N / 2;
+  T re[H > 0 ? H : 1], ro[H > 0 ? H : 1];
+#pragma unroll
+  for (int a = 0; a < H; ++a) {
+    re[a] = r[a] + r[N - 1 - a];
+    ro[a] = r[a] - r[N - 1 - a];
+  }
+  {
+    T acc = re[0];
+#pragma unroll
+    for (int a = 1; a < H; ++a) acc = acc + re[a];
+    if (N % 2 == 1) acc = acc + r[H];
+    R[0] = acc;
+  }
+#pragma unroll
+  for (int i = 1; i < N; ++i) {
+    T acc;
+    if (i % 2 == 0) {
+      acc = t.B[0][i] * re[0];
+#pragma unroll
+      for (int a = 1; a < H; ++a) acc = fma(t.B[a][i], re[a], acc);
+      if (N % 2 == 1) acc = fma(t.B[H][i], r[H], acc);
+    } else {
+      acc = t.B[0][i] * ro[0];
+#pragma unroll
+      for (int a = 1; a < H; ++a) acc = fma(t.B[a][i], ro[a], acc);
+    }
+    R[i] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Face flux at one face point.  Reference units: g = d/dxi along +axis.
+// UPPER: this cell is the lower-index (-) side of the face (its xi = 1 face).
+//   J = u- - u+, G = g- + g+ ; the (-) cell's test value gets
+//   W (sigma J - G/2) = Wh (2 sigma J - G), the (+) cell's the negative; both
+//   test derivatives get -Wd J (Wd = W/2 inside, W on the boundary).
+// On a boundary face the missing side is (u, g) = (0, own g), which turns the
+// interior formula into the one-sided form -(d_n u) phi - (d_n phi) u + sigma u phi.
+// Returns cv (multiplier of the test value) and cdm = Wd J (the test
+// derivative's multiplier is -cdm).
+// ---------------------------------------------------------------------------
+template <int N, bool UPPER, typename T>
+__device__ __forceinline__ void flux(T uo, T go, T un, T gn, T Wh, T Wd, T& cv, T& cdm) {
+  constexpr T S2 = T(4 * N * N);  // 2 sigma, sigma = 2 (k+1)^2
+  const T J = UPPER ? uo - un : un - uo;
+  const T G = go + gn;
+  const T tt = UPPER ? fma(S2, J, -G) : fma(-S2, J, G);
+  cv = Wh * tt;
+  cdm = Wd * J;
+}
+
+// Load a face trace pair (value, derivative) of face f of cell c at point pt.
+template <int N, typename T>
+__device__ __forceinline__ void load_trace(const T* __restrict__ TR, long long c, int f, int pt,
+                                           T& v, T& g) {
+  constexpr int N2 = N * N;
+  const T* tr = TR + c * (12 * N2) + (2 * f) * N2 + pt;
+  v = tr[0];
+  g = tr[N2];
+}
+
+// Own and neighbour traces plus weights of face f at point pt; on a boundary
+// face the neighbour is (0, own derivative).
+template <int N, bool UPPER, typename T>
+__device__ __forceinline__ void face_point(const T* __restrict__ TR, const T* __restrict__ FW,
+                                           long long c, int f, bool interior, long long cn, int fn,
+                                           int pt, T& cv, T& cdm) {
+  constexpr int N2 = N * N;
+  T uo, go;
+  load_trace<N>(TR, c, f, pt, uo, go);
+  T un = T(0), gn = go;
+  if (interior) load_trace<N>(TR, cn, fn, pt, un, gn);
+  const T* fw = FW + c * (12 * N2) + (2 * f) * N2 + pt;
+  flux<N, UPPER>(uo, go, un, gn, fw[0], fw[N2], cv, cdm);
 }
 
 // ---------------------------------------------------------------------------
@@ -73,16 +233,14 @@ __device__ __forceinline__ void face_flux(bool interior, T uo, T go, T un, T gn,
 // comp 0 = value, 1 = d/dxi along +axis; pt = (b + n e) on x-faces,
 // (a + n e) on y-faces, (a + n b) on z-faces.
 // ---------------------------------------------------------------------------
+// Pass 1 over the cells c0 .. c0+nblk-1 (nblk <= CPB) by the calling block;
+// s: CPB n^3 values of shared memory.  Threads beyond CPB n^2 only take part
+// in the loads and barriers.
 template <int N, typename T>
-__global__ void __launch_bounds__(Cfg<N>::THREADS)
-k_trace(const T* __restrict__ x, T* __restrict__ U, T* __restrict__ Xm, T* __restrict__ TR,
-        long long ncells, const int* __restrict__ skip, const __grid_constant__ DGTab<T> tab) {
-  constexpr int N2 = N * N, N3 = N * N * N, C = Cfg<N>::CPB;
-  if (skip != nullptr && *skip) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* s = reinterpret_cast<T*>(smem_raw);
-  const long long c0 = (long long)blockIdx.x * C;
-  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
+__device__ __forceinline__ void trace_cells(const T* __restrict__ x, T* __restrict__ U,
+                                            T* __restrict__ Xm, T* __restrict__ TR, long long c0,
+                                            int nblk, const DGTab<T>& tab, T* s) {
+  constexpr int N2 = N * N, N3 = N * N * N, H = N / 2;
   const T* xb = x + c0 * N3;
   for (int t = threadIdx.x; t < nblk * N3; t += blockDim.x) s[t] = xb[t];
   __syncthreads();
@@ -96,72 +254,75 @@ k_trace(const T* __restrict__ x, T* __restrict__ U, T* __restrict__ Xm, T* __res
 
   // along z: thread owns (i = p, j = q)
   if (active) {
-    T v[N];
+    T v[N], u[N];
 #pragma unroll
     for (int l = 0; l < N; ++l) v[l] = sc[l * N2 + q * N + p];
+    b_fwd<N>(tab, v, u);
 #pragma unroll
-    for (int e = 0; e < N; ++e) {
-      T acc = tab.B[e][0] * v[0];
-#pragma unroll
-      for (int l = 1; l < N; ++l) acc = fma(tab.B[e][l], v[l], acc);
-      sc[e * N2 + q * N + p] = acc;
-    }
+    for (int e = 0; e < N; ++e) sc[e * N2 + q * N + p] = u[e];
   }
   __syncthreads();
   // along y: thread owns (i = p, e = q)
   if (active) {
-    T v[N];
+    T v[N], u[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) v[j] = sc[q * N2 + j * N + p];
+    b_fwd<N>(tab, v, u);
 #pragma unroll
-    for (int b = 0; b < N; ++b) {
-      T acc = tab.B[b][0] * v[0];
-#pragma unroll
-      for (int j = 1; j < N; ++j) acc = fma(tab.B[b][j], v[j], acc);
-      sc[q * N2 + b * N + p] = acc;
-    }
+    for (int b = 0; b < N; ++b) sc[q * N2 + b * N + p] = u[b];
   }
   __syncthreads();
   // along x: thread owns (b = p, e = q); X is modal in x, nodal in y and z
   T* tr = TR + c * (12 * N2);
   if (active) {
-    T X[N];
+    T X[N], u[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) X[i] = sc[q * N2 + p * N + i];
     T* xm = Xm + c * N3 + q * N2 + p * N;
 #pragma unroll
     for (int i = 0; i < N; ++i) xm[i] = X[i];
-    T vm = tab.a0[0] * X[0], vp = tab.a1[0] * X[0];
-    T gm = tab.d0[0] * X[0], gp = tab.d1[0] * X[0];
+    // x-face traces from the modes: L_i(1) = a_i, L_i(0) = (-1)^i a_i,
+    // L_i'(1) = d_i, L_i'(0) = (-1)^(i+1) d_i, a_0 = 1, d_0 = 0
+    T Se = X[0], So = tab.a1[1] * X[1];
 #pragma unroll
-    for (int i = 1; i < N; ++i) {
-      vm = fma(tab.a0[i], X[i], vm);
-      vp = fma(tab.a1[i], X[i], vp);
-      gm = fma(tab.d0[i], X[i], gm);
-      gp = fma(tab.d1[i], X[i], gp);
+    for (int i = 2; i < N; i += 2) Se = fma(tab.a1[i], X[i], Se);
+#pragma unroll
+    for (int i = 3; i < N; i += 2) So = fma(tab.a1[i], X[i], So);
+    T Do = tab.d1[1] * X[1];
+#pragma unroll
+    for (int i = 3; i < N; i += 2) Do = fma(tab.d1[i], X[i], Do);
+    T De = T(0);
+    if (N > 2) {
+      De = tab.d1[2] * X[2];
+#pragma unroll
+      for (int i = 4; i < N; i += 2) De = fma(tab.d1[i], X[i], De);
     }
     const int pt = p + N * q;
-    tr[0 * N2 + pt] = vm;
-    tr[1 * N2 + pt] = gm;
-    tr[2 * N2 + pt] = vp;
-    tr[3 * N2 + pt] = gp;
+    tr[0 * N2 + pt] = Se - So;                 // x- value
+    tr[1 * N2 + pt] = (N > 2) ? Do - De : Do;  // x- derivative
+    tr[2 * N2 + pt] = Se + So;                 // x+ value
+    tr[3 * N2 + pt] = (N > 2) ? Do + De : Do;  // x+ derivative
+    b_fwd<N>(tab, X, u);
     T* ug = U + c * N3 + q * N2 + p * N;
 #pragma unroll
     for (int a = 0; a < N; ++a) {
-      T acc = tab.B[a][0] * X[0];
-#pragma unroll
-      for (int i = 1; i < N; ++i) acc = fma(tab.B[a][i], X[i], acc);
-      sc[q * N2 + p * N + a] = acc;
-      ug[a] = acc;
+      sc[q * N2 + p * N + a] = u[a];
+      ug[a] = u[a];
     }
   }
   __syncthreads();
   if (active) {
-    // y-faces: thread owns points (a = p, e = q)
-    {
-      T u[N];
+    // y-faces: thread owns points (a = p, e = q); z-faces: (a = p, b = q)
 #pragma unroll
-      for (int b = 0; b < N; ++b) u[b] = sc[q * N2 + b * N + p];
+    for (int dir = 0; dir < 2; ++dir) {
+      T u[N];
+      if (dir == 0) {
+#pragma unroll
+        for (int b = 0; b < N; ++b) u[b] = sc[q * N2 + b * N + p];
+      } else {
+#pragma unroll
+        for (int e = 0; e < N; ++e) u[e] = sc[e * N2 + q * N + p];
+      }
       T vm = tab.l0[0] * u[0], vp = tab.l1[0] * u[0];
       T gm = tab.dl0[0] * u[0], gp = tab.dl1[0] * u[0];
 #pragma unroll
@@ -172,61 +333,46 @@ k_trace(const T* __restrict__ x, T* __restrict__ U, T* __restrict__ Xm, T* __res
         gp = fma(tab.dl1[b], u[b], gp);
       }
       const int pt = p + N * q;
-      tr[4 * N2 + pt] = vm;
-      tr[5 * N2 + pt] = gm;
-      tr[6 * N2 + pt] = vp;
-      tr[7 * N2 + pt] = gp;
-    }
-    // z-faces: thread owns points (a = p, b = q)
-    {
-      T u[N];
-#pragma unroll
-      for (int e = 0; e < N; ++e) u[e] = sc[e * N2 + q * N + p];
-      T vm = tab.l0[0] * u[0], vp = tab.l1[0] * u[0];
-      T gm = tab.dl0[0] * u[0], gp = tab.dl1[0] * u[0];
-#pragma unroll
-      for (int e = 1; e < N; ++e) {
-        vm = fma(tab.l0[e], u[e], vm);
-        vp = fma(tab.l1[e], u[e], vp);
-        gm = fma(tab.dl0[e], u[e], gm);
-        gp = fma(tab.dl1[e], u[e], gp);
-      }
-      const int pt = p + N * q;
-      tr[8 * N2 + pt] = vm;
-      tr[9 * N2 + pt] = gm;
-      tr[10 * N2 + pt] = vp;
-      tr[11 * N2 + pt] = gp;
+      const int f0 = 4 + 4 * dir;
+      tr[(f0 + 0) * N2 + pt] = vm;
+      tr[(f0 + 1) * N2 + pt] = gm;
+      tr[(f0 + 2) * N2 + pt] = vp;
+      tr[(f0 + 3) * N2 + pt] = gp;
     }
   }
+  (void)H;
 }
 
-// Load a face trace pair (value, derivative) of face f of cell c at point pt.
 template <int N, typename T>
-__device__ __forceinline__ void load_trace(const T* __restrict__ TR, long long c, int f, int pt,
-                                           T& v, T& g) {
-  constexpr int N2 = N * N;
-  const T* tr = TR + c * (12 * N2) + (2 * f) * N2 + pt;
-  v = tr[0];
-  g = tr[N2];
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+k_trace(const T* __restrict__ x, T* __restrict__ U, T* __restrict__ Xm, T* __restrict__ TR,
+        long long ncells, const int* __restrict__ skip, const __grid_constant__ DGTab<T> tab) {
+  constexpr int C = Cfg<N>::CPB;
+  if (skip != nullptr && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long c0 = (long long)blockIdx.x * C;
+  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
+  trace_cells<N, T>(x, U, Xm, TR, c0, nblk, tab, reinterpret_cast<T*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
 // Pass 2: volume and face terms, back to modal coefficients.
+// FW layout: FW[((c*6 + f)*2 + comp)*n^2 + pt], comp 0 = W/2, 1 = derivative
+// weight (W/2 inside, W on the boundary), W = h gamma_F w_s w_t.
 // ---------------------------------------------------------------------------
+// Pass 2 over the cells c0 .. c0+nblk-1 (nblk <= CPB) by the calling block;
+// smem: 4 CPB n^3 values of shared memory.
 template <int N, typename T>
-__global__ void __launch_bounds__(Cfg<N>::THREADS)
-k_cell(const T* __restrict__ U, const T* __restrict__ Xm, const T* __restrict__ TR,
-       const T* __restrict__ kt, const T* __restrict__ gh, T* __restrict__ y, long long ncells,
-       int Nc, const int* __restrict__ skip, const __grid_constant__ DGTab<T> tab) {
+__device__ __forceinline__ void cell_cells(const T* __restrict__ U, const T* __restrict__ Xm,
+                                           const T* __restrict__ TR, const T* __restrict__ kt,
+                                           const T* __restrict__ FW, T* __restrict__ y,
+                                           long long c0, int nblk, int Nc, const DGTab<T>& tab,
+                                           T* smem) {
   constexpr int N2 = N * N, N3 = N * N * N, C = Cfg<N>::CPB;
-  if (skip != nullptr && *skip) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* su = reinterpret_cast<T*>(smem_raw);
+  T* su = smem;
   T* sx = su + C * N3;
   T* sr = sx + C * N3;
   T* sk = sr + C * N3;
-  const long long c0 = (long long)blockIdx.x * C;
-  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
   {
     const T* ub = U + c0 * N3;
     const T* xb = Xm + c0 * N3;
@@ -249,175 +395,101 @@ k_cell(const T* __restrict__ U, const T* __restrict__ Xm, const T* __restrict__ 
   const int cz = (int)(c / ((long long)Nc * Nc));
   const long long sy = Nc, sz = (long long)Nc * Nc;
   const int o = lc * N3;
-  const T sigma = tab.sigma;
-  const T* ghc = gh + c * 6;
+  const int pt = p + N * q;
 
-  // z-lines: thread owns (a = p, b = q)
-  if (active) {
-    T u[N], kg[N], r[N];
+  // z-lines then y-lines: collocation derivative, Kt, transpose, face terms
 #pragma unroll
-    for (int e = 0; e < N; ++e) u[e] = su[o + e * N2 + q * N + p];
+  for (int dir = 0; dir < 2; ++dir) {
+    if (active) {
+      // dir 0: z-line of (a = p, b = q); dir 1: y-line of (a = p, e = q)
+      const int base = (dir == 0) ? (q * N + p) : (q * N2 + p);
+      const int step = (dir == 0) ? N2 : N;
+      T u[N], kg[N], r[N];
 #pragma unroll
-    for (int e = 0; e < N; ++e) {
-      T g = tab.D[e][0] * u[0];
+      for (int e = 0; e < N; ++e) u[e] = su[o + base + e * step];
 #pragma unroll
-      for (int f = 1; f < N; ++f) g = fma(tab.D[e][f], u[f], g);
-      kg[e] = sk[o + e * N2 + q * N + p] * g;
+      for (int e = 0; e < N; ++e) {
+        T g = tab.D[e][0] * u[0];
+#pragma unroll
+        for (int f = 1; f < N; ++f) g = fma(tab.D[e][f], u[f], g);
+        kg[e] = sk[o + base + e * step] * g;
+      }
+#pragma unroll
+      for (int e = 0; e < N; ++e) {
+        T acc = (dir == 0) ? tab.D[0][e] * kg[0] : fma(tab.D[0][e], kg[0], sr[o + base + e * step]);
+#pragma unroll
+        for (int f = 1; f < N; ++f) acc = fma(tab.D[f][e], kg[f], acc);
+        r[e] = acc;
+      }
+      const int fu = (dir == 0) ? 5 : 3, fl = fu - 1;
+      const bool inu = (dir == 0) ? (cz < Nc - 1) : (cy < Nc - 1);
+      const bool inl = (dir == 0) ? (cz > 0) : (cy > 0);
+      const long long st = (dir == 0) ? sz : sy;
+      T cv1, cd1, cv0, cd0;
+      face_point<N, true>(TR, FW, c, fu, inu, c + st, fl, pt, cv1, cd1);
+      face_point<N, false>(TR, FW, c, fl, inl, c - st, fu, pt, cv0, cd0);
+#pragma unroll
+      for (int e = 0; e < N; ++e) {
+        T acc = fma(tab.l1[e], cv1, r[e]);
+        acc = fma(-tab.dl1[e], cd1, acc);
+        acc = fma(tab.l0[e], cv0, acc);
+        r[e] = fma(-tab.dl0[e], cd0, acc);
+      }
+#pragma unroll
+      for (int e = 0; e < N; ++e) sr[o + base + e * step] = r[e];
     }
-#pragma unroll
-    for (int e = 0; e < N; ++e) {
-      T acc = tab.D[0][e] * kg[0];
-#pragma unroll
-      for (int f = 1; f < N; ++f) acc = fma(tab.D[f][e], kg[f], acc);
-      r[e] = acc;
-    }
-    const int pt = p + N * q;
-    const T ww = tab.w[p] * tab.w[q];
-    {  // z+ face: this cell is the (-) side
-      const bool in = cz < Nc - 1;
-      T uo, go, un = T(0), gn = T(0);
-      load_trace<N>(TR, c, 5, pt, uo, go);
-      if (in) load_trace<N>(TR, c + sz, 4, pt, un, gn);
-      T cv, cd;
-      face_flux<true>(in, uo, go, un, gn, ghc[5] * ww, sigma, cv, cd);
-#pragma unroll
-      for (int e = 0; e < N; ++e) r[e] = fma(tab.l1[e], cv, fma(tab.dl1[e], cd, r[e]));
-    }
-    {  // z- face: this cell is the (+) side
-      const bool in = cz > 0;
-      T uo, go, un = T(0), gn = T(0);
-      load_trace<N>(TR, c, 4, pt, uo, go);
-      if (in) load_trace<N>(TR, c - sz, 5, pt, un, gn);
-      T cv, cd;
-      face_flux<false>(in, uo, go, un, gn, ghc[4] * ww, sigma, cv, cd);
-#pragma unroll
-      for (int e = 0; e < N; ++e) r[e] = fma(tab.l0[e], cv, fma(tab.dl0[e], cd, r[e]));
-    }
-#pragma unroll
-    for (int e = 0; e < N; ++e) sr[o + e * N2 + q * N + p] = r[e];
+    __syncthreads();
   }
-  __syncthreads();
-  // y-lines: thread owns (a = p, e = q)
-  if (active) {
-    T u[N], kg[N], r[N];
-#pragma unroll
-    for (int b = 0; b < N; ++b) u[b] = su[o + q * N2 + b * N + p];
-#pragma unroll
-    for (int b = 0; b < N; ++b) {
-      T g = tab.D[b][0] * u[0];
-#pragma unroll
-      for (int f = 1; f < N; ++f) g = fma(tab.D[b][f], u[f], g);
-      kg[b] = sk[o + q * N2 + b * N + p] * g;
-    }
-#pragma unroll
-    for (int b = 0; b < N; ++b) {
-      T acc = sr[o + q * N2 + b * N + p];
-#pragma unroll
-      for (int f = 0; f < N; ++f) acc = fma(tab.D[f][b], kg[f], acc);
-      r[b] = acc;
-    }
-    const int pt = p + N * q;
-    const T ww = tab.w[p] * tab.w[q];
-    {  // y+ face
-      const bool in = cy < Nc - 1;
-      T uo, go, un = T(0), gn = T(0);
-      load_trace<N>(TR, c, 3, pt, uo, go);
-      if (in) load_trace<N>(TR, c + sy, 2, pt, un, gn);
-      T cv, cd;
-      face_flux<true>(in, uo, go, un, gn, ghc[3] * ww, sigma, cv, cd);
-#pragma unroll
-      for (int b = 0; b < N; ++b) r[b] = fma(tab.l1[b], cv, fma(tab.dl1[b], cd, r[b]));
-    }
-    {  // y- face
-      const bool in = cy > 0;
-      T uo, go, un = T(0), gn = T(0);
-      load_trace<N>(TR, c, 2, pt, uo, go);
-      if (in) load_trace<N>(TR, c - sy, 3, pt, un, gn);
-      T cv, cd;
-      face_flux<false>(in, uo, go, un, gn, ghc[2] * ww, sigma, cv, cd);
-#pragma unroll
-      for (int b = 0; b < N; ++b) r[b] = fma(tab.l0[b], cv, fma(tab.dl0[b], cd, r[b]));
-    }
-#pragma unroll
-    for (int b = 0; b < N; ++b) sr[o + q * N2 + b * N + p] = r[b];
-  }
-  __syncthreads();
   // x-lines: thread owns (b = p, e = q); result is x-modal, yz-nodal
   if (active) {
-    T X[N], kg[N], R[N];
+    const int base = q * N2 + p * N;
+    T X[N], g[N], kg[N], rr[N], R[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) X[i] = sx[o + q * N2 + p * N + i];
+    for (int i = 0; i < N; ++i) X[i] = sx[o + base + i];
+    bd_fwd<N>(tab, X, g);
 #pragma unroll
     for (int a = 0; a < N; ++a) {
-      T g = tab.Bd[a][0] * X[0];
-#pragma unroll
-      for (int i = 1; i < N; ++i) g = fma(tab.Bd[a][i], X[i], g);
-      kg[a] = sk[o + q * N2 + p * N + a] * g;
+      kg[a] = sk[o + base + a] * g[a];
+      rr[a] = sr[o + base + a];
     }
-    T rr[N];
+    bt_bdt<N>(tab, rr, kg, R);
+    T cv1, cd1, cv0, cd0;
+    face_point<N, true>(TR, FW, c, 1, cx < Nc - 1, c + 1, 0, pt, cv1, cd1);
+    face_point<N, false>(TR, FW, c, 0, cx > 0, c - 1, 1, pt, cv0, cd0);
+    // modal test functions: value a_i at 1, (-1)^i a_i at 0; derivative -d_i cd
+    // at 1, -(-1)^(i+1) d_i cd at 0 (a_0 = 1, d_0 = 0)
+    const T sp = cv1 + cv0, sm = cv1 - cv0;
+    const T dp = cd1 + cd0, dm = cd1 - cd0;
+    R[0] = R[0] + sp;
 #pragma unroll
-    for (int a = 0; a < N; ++a) rr[a] = sr[o + q * N2 + p * N + a];
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      T acc = tab.Bd[0][i] * kg[0];
-#pragma unroll
-      for (int a = 1; a < N; ++a) acc = fma(tab.Bd[a][i], kg[a], acc);
-#pragma unroll
-      for (int a = 0; a < N; ++a) acc = fma(tab.B[a][i], rr[a], acc);
-      R[i] = acc;
-    }
-    const int pt = p + N * q;
-    const T ww = tab.w[p] * tab.w[q];
-    {  // x+ face
-      const bool in = cx < Nc - 1;
-      T uo, go, un = T(0), gn = T(0);
-      load_trace<N>(TR, c, 1, pt, uo, go);
-      if (in) load_trace<N>(TR, c + 1, 0, pt, un, gn);
-      T cv, cd;
-      face_flux<true>(in, uo, go, un, gn, ghc[1] * ww, sigma, cv, cd);
-#pragma unroll
-      for (int i = 0; i < N; ++i) R[i] = fma(tab.a1[i], cv, fma(tab.d1[i], cd, R[i]));
-    }
-    {  // x- face
-      const bool in = cx > 0;
-      T uo, go, un = T(0), gn = T(0);
-      load_trace<N>(TR, c, 0, pt, uo, go);
-      if (in) load_trace<N>(TR, c - 1, 1, pt, un, gn);
-      T cv, cd;
-      face_flux<false>(in, uo, go, un, gn, ghc[0] * ww, sigma, cv, cd);
-#pragma unroll
-      for (int i = 0; i < N; ++i) R[i] = fma(tab.a0[i], cv, fma(tab.d0[i], cd, R[i]));
+    for (int i = 1; i < N; ++i) {
+      if (i % 2 == 0)
+        R[i] = fma(tab.a1[i], sp, fma(-tab.d1[i], dm, R[i]));
+      else
+        R[i] = fma(tab.a1[i], sm, fma(-tab.d1[i], dp, R[i]));
     }
 #pragma unroll
-    for (int i = 0; i < N; ++i) sx[o + q * N2 + p * N + i] = R[i];
+    for (int i = 0; i < N; ++i) sx[o + base + i] = R[i];
   }
   __syncthreads();
   // back along y: thread owns (i = p, e = q)
   if (active) {
-    T v[N];
+    T v[N], R[N];
 #pragma unroll
     for (int b = 0; b < N; ++b) v[b] = sx[o + q * N2 + b * N + p];
+    b_bwd<N>(tab, v, R);
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      T acc = tab.B[0][j] * v[0];
-#pragma unroll
-      for (int b = 1; b < N; ++b) acc = fma(tab.B[b][j], v[b], acc);
-      sx[o + q * N2 + j * N + p] = acc;
-    }
+    for (int j = 0; j < N; ++j) sx[o + q * N2 + j * N + p] = R[j];
   }
   __syncthreads();
   // back along z: thread owns (i = p, j = q)
   if (active) {
-    T v[N];
+    T v[N], R[N];
 #pragma unroll
     for (int e = 0; e < N; ++e) v[e] = sx[o + e * N2 + q * N + p];
+    b_bwd<N>(tab, v, R);
 #pragma unroll
-    for (int l = 0; l < N; ++l) {
-      T acc = tab.B[0][l] * v[0];
-#pragma unroll
-      for (int e = 1; e < N; ++e) acc = fma(tab.B[e][l], v[e], acc);
-      sx[o + l * N2 + q * N + p] = acc;
-    }
+    for (int l = 0; l < N; ++l) sx[o + l * N2 + q * N + p] = R[l];
   }
   __syncthreads();
   T* yb = y + c0 * N3;
@@ -425,21 +497,56 @@ k_cell(const T* __restrict__ U, const T* __restrict__ Xm, const T* __restrict__ 
 }
 
 template <int N, typename T>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+k_cell(const T* __restrict__ U, const T* __restrict__ Xm, const T* __restrict__ TR,
+       const T* __restrict__ kt, const T* __restrict__ FW, T* __restrict__ y, long long ncells,
+       int Nc, const int* __restrict__ skip, const __grid_constant__ DGTab<T> tab) {
+  constexpr int C = Cfg<N>::CPB;
+  if (skip != nullptr && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long c0 = (long long)blockIdx.x * C;
+  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
+  cell_cells<N, T>(U, Xm, TR, kt, FW, y, c0, nblk, Nc, tab, reinterpret_cast<T*>(smem_raw));
+}
+
+template <int N, typename T>
 inline size_t trace_smem() { return sizeof(T) * Cfg<N>::CPB * N * N * N; }
 template <int N, typename T>
 inline size_t cell_smem() { return 4 * sizeof(T) * Cfg<N>::CPB * N * N * N; }
 
+// Face-point weights from h*gamma per face side (one thread per cell).
+template <typename T>
+__global__ void k_face_weights(const double* __restrict__ gh, T* __restrict__ FW, int Nc, int n,
+                               const __grid_constant__ DGTab<double> tab) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= (long long)Nc * Nc * Nc) return;
+  const int crd[3] = {(int)(c % Nc), (int)((c / Nc) % Nc), (int)(c / ((long long)Nc * Nc))};
+  const int n2 = n * n;
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1;
+    const bool upper = f & 1;
+    const bool interior = upper ? (crd[d] < Nc - 1) : (crd[d] > 0);
+    const double g = gh[c * 6 + f];
+    for (int pt = 0; pt < n2; ++pt) {
+      const double wh = 0.5 * g * tab.w[pt % n] * tab.w[pt / n];
+      FW[(c * 12 + 2 * f) * n2 + pt] = (T)wh;
+      FW[(c * 12 + 2 * f + 1) * n2 + pt] = (T)(interior ? wh : 2.0 * wh);
+    }
+  }
+}
+
+
 // Launch both passes for one precision.  U, X, TR: workspaces of the mesh.
 template <int N, typename T>
 cudaError_t launch_apply_n(const dg_mesh* m, const T* x, T* y, T* U, T* X, T* TR, const T* kt,
-                           const T* gh, long long ncells, int Nc, const int* skip,
+                           const T* fw, long long ncells, int Nc, const int* skip,
                            const DGTab<T>& tab, cudaStream_t s) {
   const unsigned blocks = (unsigned)((ncells + Cfg<N>::CPB - 1) / Cfg<N>::CPB);
   const size_t s1 = trace_smem<N, T>(), s2 = cell_smem<N, T>();
   dg_timing_mark(m, 0, s);
   k_trace<N, T><<<blocks, Cfg<N>::THREADS, s1, s>>>(x, U, X, TR, ncells, skip, tab);
   dg_timing_mark(m, 1, s);
-  k_cell<N, T><<<blocks, Cfg<N>::THREADS, s2, s>>>(U, X, TR, kt, gh, y, ncells, Nc, skip, tab);
+  k_cell<N, T><<<blocks, Cfg<N>::THREADS, s2, s>>>(U, X, TR, kt, fw, y, ncells, Nc, skip, tab);
   dg_timing_mark(m, 2, s);
   return cudaGetLastError();
 }
@@ -472,9 +579,9 @@ template <int N>
 struct ApplyF {
   template <typename T>
   static cudaError_t run(const dg_mesh* m, const T* x, T* y, T* U, T* X, T* TR, const T* kt,
-                         const T* gh, long long ncells, int Nc, const int* skip,
+                         const T* fw, long long ncells, int Nc, const int* skip,
                          const DGTab<T>* tab, cudaStream_t s) {
-    return launch_apply_n<N, T>(m, x, y, U, X, TR, kt, gh, ncells, Nc, skip, *tab, s);
+    return launch_apply_n<N, T>(m, x, y, U, X, TR, kt, fw, ncells, Nc, skip, *tab, s);
   }
 };
 

@@ -19,7 +19,10 @@
 // residual has dropped below delta times its value at the last refinement (or
 // below the tolerance), the FP32 correction d is added to x in FP64, r = b - A x
 // is recomputed with the FP64 operator, and r replaces the FP32 residual; the
-// search direction p is kept, so the Krylov recurrence is not restarted.  The
+// search direction p is kept, so the Krylov recurrence is not restarted.  When a
+// refinement finds that the true residual fell by less than 2x since the last
+// one (the FP32 operator's error, about u_32 times the condition number, then
+// pollutes the kept directions), the direction is restarted with p = r.  The
 // refinement kernels are in every captured iteration and skip themselves unless
 // the update kernel requested a refinement.
 //
@@ -226,7 +229,7 @@ template <typename T, bool MIXED>
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_update_p(T* __restrict__ p, const T* __restrict__ r, long long n, const DGCGState* st) {
   if (st->done) return;
-  const double beta = MIXED ? st->rho_new / st->rho : st->beta;
+  const double beta = MIXED ? (st->restart ? 0.0 : st->rho_new / st->rho) : st->beta;
   const T be = (T)beta;
   GRID_STRIDE(i, n) p[i] = fma(be, p[i], r[i]);
 }
@@ -235,6 +238,7 @@ k_update_p(T* __restrict__ p, const T* __restrict__ r, long long n, const DGCGSt
 __global__ void k_commit_rho(DGCGState* st) {
   if (st->done) return;
   st->rho = st->rho_new;
+  st->restart = 0;
 }
 
 // refinement step 1 (mixed): x64 += d32, d32 = 0.
@@ -247,8 +251,14 @@ k_refine_x(double* __restrict__ x, float* __restrict__ d, long long n, const DGC
   }
 }
 
+// The FP32 operator's error bounds the accuracy the mixed solver can reach
+// (about u_32 times the condition number, relative).  After this many
+// consecutive refinements without a 2x residual reduction it gives up.
+constexpr int kMaxStall = 30;
+
 // refinement step 2 (mixed), after q = A64 x: r64 = b - q, r32 = (float) r64,
-// rho_new = rmax2 = ||r64||^2; converged when <= tol2; cap on iterations.
+// rho_new = rmax2 = ||r64||^2; converged when <= tol2; cap on iterations and
+// on stagnating refinements.
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_refine_r(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
            float* __restrict__ r32, long long n, double* partials, DGCGState* st) {
@@ -264,13 +274,15 @@ k_refine_r(const double* __restrict__ b, const double* __restrict__ q, double* _
   if (last_block_sums<1>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
     const double rr = tot[0];
     st->n_refine += 1;
+    st->restart = rr > 0.25 * st->rmax2;  // true residual fell by less than 2x
+    st->stall = st->restart ? st->stall + 1 : 0;
     st->rho_new = rr;
     st->rmax2 = rr;
     st->ru_skip = 1;
     if (!finite(rr)) {
       st->breakdown = 1;
       st->done = 1;
-    } else if (rr <= st->tol2 || st->iters >= st->maxit) {
+    } else if (rr <= st->tol2 || st->iters >= st->maxit || st->stall >= kMaxStall) {
       st->done = 1;
     }
   }
@@ -507,7 +519,9 @@ int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_
   if (rel <= rtol) return DG_OK;
   return dg_fail(DG_ERR_NOT_CONVERGED,
                  "dg_cg_solve(mixed): relative residual %.3e > rtol %.3e after %d iterations "
-                 "(%d refinements)", rel, rtol, hs.iters, hs.n_refine);
+                 "(%d refinements%s)", rel, rtol, hs.iters, hs.n_refine,
+                 hs.stall >= kMaxStall ? "; stagnated: the FP32 operator limits the accuracy, "
+                                         "use DG_CG_FP64 for this tolerance" : "");
 }
 
 // Classical refinement: restart an FP32 CG from zero for every correction.

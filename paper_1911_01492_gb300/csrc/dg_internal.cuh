@@ -49,7 +49,8 @@ struct DGCGState {
   unsigned int ticket;  // completion counter of the last-block reductions
   int ru_skip;      // 0 when this iteration ends with an FP64 refinement (mixed mode)
   int n_refine;     // FP64 residual refinements performed (mixed mode)
-  int pad;
+  int restart;      // 1: the next direction update restarts with p = r (mixed mode)
+  int stall;        // consecutive refinements that fell short of a 2x reduction
 };
 
 struct dg_mesh {
@@ -72,6 +73,8 @@ struct dg_mesh {
   double* gh64;     // h gamma_F per face side        [c][6] (x-, x+, y-, y+, z-, z+)
   float* gh32;
   double* dgam;     // d gamma_F / d log Kbar_c       [c][6]
+  double* fw64;     // face-point weights W/2 and derivative weight  [c][6][2][n^2]
+  float* fw32;
   double* kbar;     // Kbar_c                          [c]
   int* dflag;       // device-side error flag of the setup kernels
 

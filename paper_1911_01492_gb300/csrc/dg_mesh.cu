@@ -5,7 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 
-#include "dg_internal.cuh"
+#include "dg_apply_impl.cuh"
 
 // ---------------------------------------------------------------------------
 // error reporting
@@ -96,7 +96,7 @@ static cudaError_t dmalloc(P** p, size_t count) {
 }
 
 static void free_all(dg_mesh* m) {
-  void* ptrs[] = {m->kt64, m->kt32, m->gh64, m->gh32, m->dgam, m->kbar, m->dflag,
+  void* ptrs[] = {m->kt64, m->kt32, m->gh64, m->gh32, m->dgam, m->kbar, m->dflag, m->fw64, m->fw32,
                   m->U64,  m->X64,  m->TR64, m->U32,  m->X32,  m->TR32, m->U64b,
                   m->X64b, m->TR64b, m->hx_dev, m->hy_dev, m->r64, m->p64, m->q64,
                   m->t64,  m->d32,  m->r32, m->p32, m->q32, m->partials, m->state};
@@ -139,6 +139,8 @@ extern "C" int dg_create_mesh(int n_cells, int degree, dg_mesh** out) {
   if (e == cudaSuccess) e = dmalloc(&m->gh64, 6 * nc);
   if (e == cudaSuccess) e = dmalloc(&m->gh32, 6 * nc);
   if (e == cudaSuccess) e = dmalloc(&m->dgam, 6 * nc);
+  if (e == cudaSuccess) e = dmalloc(&m->fw64, ntr);
+  if (e == cudaSuccess) e = dmalloc(&m->fw32, ntr);
   if (e == cudaSuccess) e = dmalloc(&m->kbar, nc);
   if (e == cudaSuccess) e = dmalloc(&m->dflag, 1);
   if (e == cudaSuccess) e = dmalloc(&m->U64, nd);
@@ -233,6 +235,8 @@ extern "C" int dg_set_coefficient(dg_mesh* m, const double* K, void* stream) {
   {
     const unsigned blocks = (unsigned)((m->ncells + 255) / 256);
     k_coef_faces<<<blocks, 256, 0, s>>>(m->kbar, m->gh64, m->gh32, m->dgam, m->N, m->h);
+    dgk::k_face_weights<double><<<blocks, 256, 0, s>>>(m->gh64, m->fw64, m->N, m->n, m->tab64);
+    dgk::k_face_weights<float><<<blocks, 256, 0, s>>>(m->gh64, m->fw32, m->N, m->n, m->tab64);
     DG_CUDA(cudaGetLastError());
   }
   int flag = 0;

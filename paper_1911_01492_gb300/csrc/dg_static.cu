@@ -8,7 +8,7 @@
 // those callers get this entry point instead.  It takes the raw coefficient K,
 // the input x and the output y from the caller.  Its temporaries live in one
 // file-scope __device__ array of DG_STATIC_SCRATCH_BYTES:
-//   the derived coefficients h w_q K and h gamma_F,
+//   the derived coefficients h w_q K, h gamma_F and the face-point weights,
 //   the per-cell Kbar,
 //   the validity flag,
 //   the nodal values, the x-modal values and the face traces of x.
@@ -103,14 +103,14 @@ template <int N>
 struct StaticApplyF {
   template <typename T>
   static cudaError_t run(const double* x, double* y, double* U, double* X, double* TR,
-                         const double* kt, const double* gh, long long ncells, int Nc,
+                         const double* kt, const double* fw, long long ncells, int Nc,
                          const DGTab<double>* tab, cudaStream_t s) {
     using dgk::Cfg;
     const unsigned blocks = (unsigned)((ncells + Cfg<N>::CPB - 1) / Cfg<N>::CPB);
     dgk::k_trace<N, double><<<blocks, Cfg<N>::THREADS, dgk::trace_smem<N, double>(), s>>>(
         x, U, X, TR, ncells, nullptr, *tab);
     dgk::k_cell<N, double><<<blocks, Cfg<N>::THREADS, dgk::cell_smem<N, double>(), s>>>(
-        U, X, TR, kt, gh, y, ncells, Nc, nullptr, *tab);
+        U, X, TR, kt, fw, y, ncells, Nc, nullptr, *tab);
     return cudaGetLastError();
   }
 };
@@ -140,7 +140,8 @@ extern "C" int dg_apply_static(int n_cells, int degree, const double* K, const d
   const size_t o_U = o_kt + align256(sizeof(double) * ndofs);
   const size_t o_X = o_U + align256(sizeof(double) * ndofs);
   const size_t o_TR = o_X + align256(sizeof(double) * ndofs);
-  const size_t total = o_TR + align256(sizeof(double) * 12 * n2 * (size_t)ncells);
+  const size_t o_FW = o_TR + align256(sizeof(double) * 12 * n2 * (size_t)ncells);
+  const size_t total = o_FW + align256(sizeof(double) * 12 * n2 * (size_t)ncells);
   if (total > DG_STATIC_SCRATCH_BYTES)
     return dg_fail(DG_ERR_INVALID_ARG,
                    "dg_apply_static: %d^3 cells of degree %d need %zu bytes of scratch; the "
@@ -156,6 +157,7 @@ extern "C" int dg_apply_static(int n_cells, int degree, const double* K, const d
   double* U = (double*)(base + o_U);
   double* X = (double*)(base + o_X);
   double* TR = (double*)(base + o_TR);
+  double* FW = (double*)(base + o_FW);
 
   DGTab<double> tab;
   DGTab<float> tab32;
@@ -166,9 +168,11 @@ extern "C" int dg_apply_static(int n_cells, int degree, const double* K, const d
   k_static_cells<<<(unsigned)((ncells * 32 + 255) / 256), 256, 0, s>>>(K, kt, kbar, ncells, n, h,
                                                                        flag, tab);
   k_static_faces<<<(unsigned)((ncells + 255) / 256), 256, 0, s>>>(kbar, gh, n_cells, h);
+  dgk::k_face_weights<double><<<(unsigned)((ncells + 255) / 256), 256, 0, s>>>(gh, FW, n_cells, n,
+                                                                              tab);
   DG_CUDA(cudaGetLastError());
   cudaError_t e = dgk::dispatch_n<double, StaticApplyF>(n, x, y, U, X, TR, (const double*)kt,
-                                                        (const double*)gh, ncells, n_cells,
+                                                        (const double*)FW, ncells, n_cells,
                                                         (const DGTab<double>*)&tab, s);
   if (e != cudaSuccess) return dg_cuda_fail(e, "dg_apply_static: launch");
   int hflag = 0;

@@ -87,27 +87,34 @@ def test_solve_gradient_matches_oracle_on_4cubed(dg, k):
 @pytest.mark.slow
 def test_solve_gradient_central_differences_32cubed_q3(dg):
     """32^3 Q3 lognormal K: gradient by adjoint CG against central finite
-    differences along 20 seeded directions (eps = 1e-4, solves to 1e-12)."""
+    differences along 20 seeded directions (eps = 1e-4).  Solves go to a
+    relative residual of 1e-10 recomputed in FP64: 1e-12 is below what FP64 CG
+    can attain on this operator (its true residual floors near 5e-11, about
+    u_64 times the condition number), and 1e-10 keeps the solve error in the
+    difference quotient near 1e-6 relative."""
     import torch
     from paper_1911_01492_gb300 import autograd as dga
     N, k = 32, 3
     m = dg.Mesh(N, k)
     b = torch.from_numpy(inputs.constant_load_vector(N, k)).cuda()
-    Kref = torch.from_numpy(inputs.lognormal_coefficient(N, k, seed=40)).cuda()
-    m.set_coefficient(Kref)
-    uref, _ = m.cg_solve(b, rtol=1e-12, mode=1)
+
+    def solve_accurately():
+        x, _ = m.cg_solve(b, rtol=1e-10, mode=dg.DG_CG_MIXED_IR)
+        return x
+
+    m.set_coefficient(torch.from_numpy(inputs.lognormal_coefficient(N, k, seed=40)).cuda())
+    uref = solve_accurately()
     rng = np.random.default_rng(41)
     rms = float(torch.sqrt(torch.mean(uref ** 2)))
     u_obs = uref + 0.01 * rms * torch.from_numpy(rng.standard_normal(m.n_dofs)).cuda()
     logK = torch.from_numpy(np.log(inputs.lognormal_coefficient(N, k, seed=5))).cuda()
 
     def loss(lk):
-        m._logk_key = None
-        u = dga.solve(b, lk, m, rtol=1e-12, mode=1)
-        return 0.5 * float(((u - u_obs) ** 2).sum())
+        m.set_coefficient(torch.exp(lk))
+        return 0.5 * float(((solve_accurately() - u_obs) ** 2).sum())
 
     lk = logK.clone().requires_grad_()
-    u = dga.solve(b, lk, m, rtol=1e-12, mode=1)
+    u = dga.solve(b, lk, m, rtol=1e-10, mode=dg.DG_CG_FP64)
     (0.5 * ((u - u_obs) ** 2).sum()).backward()
     g = lk.grad.clone()
     drng = np.random.default_rng(42)
