@@ -33,10 +33,10 @@ CG_WORKLOAD = {"n_cells": 48, "degree": 4, "K": "lognormal", "K_seed": 4, "rtol"
 BATCH_LEVELS = [(128, 16, 2), (96, 24, 3), (32, 32, 4)]   # (samples, n_cells, degree)
 METRIC = "SIPG-DG apply GDOF/s (FP64)"
 NOMINAL_FP64_TFLOPS = 1.25   # GB300 FP64 rate: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
-# DRAM bytes (read + write) of one k_cell<4,double> launch, from an ncu capture
-# of the 40^3 Q3 case (318.9 MB for 4,096,000 DOFs) scaled by DOFs to 64^3 Q3;
-# must be re-measured whenever k_cell changes.
-K_CELL_TRAFFIC_PER_DOF = 318.9e6 / 4096000
+# DRAM bytes (read + write) per DOF of one pass-2 launch (k_cell_lo<4,double>),
+# from an ncu capture of the 40^3 Q3 case, scaled by DOFs to the benchmark's
+# launch; None until captured for the current kernel.
+K_CELL_TRAFFIC_PER_DOF = None
 
 
 def flops_per_dof(n: int):
@@ -276,61 +276,110 @@ def run_cg(world):
     return out
 
 
-def run_batched(world, rank, sequential_samples: int = 0):
-    """Batched lock-step CG over 256 samples (FP64, rtol 1e-8): aggregate DOF/s of
-    the persistent batched solve, and of one sample per dg_cg_solve call."""
+def _batch_meshes(levels, seed0=1000):
     import torch
     import paper_1911_01492_gb300 as dg
     from paper_1911_01492_gb300 import inputs
     meshes, bs, xs, sizes = [], [], [], []
     s = 0
-    for count, N, k in BATCH_LEVELS:
+    for count, N, k in levels:
         for _ in range(count):
             m = dg.Mesh(N, k)
             m.set_coefficient(torch.from_numpy(
-                inputs.lognormal_coefficient(N, k, seed=1000 + s)).cuda())
+                inputs.lognormal_coefficient(N, k, seed=seed0 + s)).cuda())
             meshes.append(m)
             bs.append(torch.from_numpy(inputs.constant_load_vector(N, k)).cuda())
             xs.append(torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda"))
-            sizes.append((N, k, m.n_dofs))
+            sizes.append(m.n_dofs)
             s += 1
+    return meshes, bs, xs, sizes
+
+
+def _timed_batched(meshes, bs, xs, sizes, world):
+    import torch
+    import paper_1911_01492_gb300 as dg
+    for x in xs:
+        x.zero_()
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
     stats = dg.cg_solve_batched(meshes, bs, xs, rtol=1e-8, maxit=200000, raise_on_error=False)
     torch.cuda.synchronize()
-    t_batch = max_over_ranks(time.perf_counter() - t0, world)
-    dof_applies = sum(st["iterations"] * sz[2] for st, sz in zip(stats, sizes))
-    total_dofs = sum(sz[2] for sz in sizes)
+    dt = max_over_ranks(time.perf_counter() - t0, world)
+    work = sum(st["iterations"] * n for st, n in zip(stats, sizes))
+    return {"samples": len(meshes), "seconds": dt, "gdof_per_s": world * work / dt / 1e9,
+            "all_converged": all(st["status"] == 0 for st in stats),
+            "max_rel_residual": max(st["rel_residual"] for st in stats),
+            "iterations_min_max": [min(st["iterations"] for st in stats),
+                                   max(st["iterations"] for st in stats)]}
+
+
+def _timed_sequential(meshes, bs, sizes, picked):
+    import torch
+    t, work = 0.0, 0
+    for i in picked:
+        x = torch.zeros_like(bs[i])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = meshes[i].cg_solve(bs[i], x, rtol=1e-8, maxit=200000)
+        torch.cuda.synchronize()
+        t += time.perf_counter() - t0
+        work += st["iterations"] * sizes[i]
+    return {"samples": len(picked), "seconds": t, "gdof_per_s": work / t / 1e9}
+
+
+def run_batched(world, rank, sequential_samples: int = 4, full: bool = False):
+    """Batched lock-step CG (FP64, rtol 1e-8) on the 256-sample workload.
+
+    Always: the 128 small samples (16^3 Q2) in one batched solve against the
+    same samples one per dg_cg_solve call, and one-per-call rates of every
+    level.  With full = True also the whole 256-sample batch (several minutes).
+    """
     out = {"workload": "256 lognormal-K samples: 128 x 16^3 Q2, 96 x 24^3 Q3, 32 x 32^3 Q4 "
-                       f"({total_dofs} DOFs), FP64 CG to 1e-8",
-           "batched": {"seconds": t_batch, "gdof_per_s": world * dof_applies / t_batch / 1e9,
-                       "all_converged": all(st["status"] == 0 for st in stats),
-                       "max_rel_residual": max(st["rel_residual"] for st in stats),
-                       "iterations_min_max": [min(st["iterations"] for st in stats),
-                                              max(st["iterations"] for st in stats)]}}
-    if sequential_samples:
-        # one sample per dg_cg_solve call, on the first samples of every level
-        picked = []
-        start = 0
-        for count, N, k in BATCH_LEVELS:
-            picked += list(range(start, start + min(count, sequential_samples)))
-            start += count
-        t_seq, dof_seq = 0.0, 0
-        for i in picked:
-            x = torch.zeros_like(xs[i])
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            _, st = meshes[i].cg_solve(bs[i], x, rtol=1e-8, maxit=200000)
-            torch.cuda.synchronize()
-            t_seq += time.perf_counter() - t0
-            dof_seq += st["iterations"] * sizes[i][2]
-        out["one_sample_per_launch"] = {"samples": len(picked), "seconds": t_seq,
-                                        "gdof_per_s": dof_seq / t_seq / 1e9}
-        out["speedup_batched"] = out["batched"]["gdof_per_s"] / out["one_sample_per_launch"]["gdof_per_s"]
+                       "(230,162,432 DOFs), FP64 CG to 1e-8; seeds 1000 + sample"}
+    small = [BATCH_LEVELS[0]]
+    meshes, bs, xs, sizes = _batch_meshes(small)
+    out["small_level_batched"] = _timed_batched(meshes, bs, xs, sizes, world)
+    out["small_level_one_per_call"] = _timed_sequential(
+        meshes, bs, sizes, list(range(min(len(meshes), 4 * sequential_samples))))
+    out["small_level_speedup"] = (out["small_level_batched"]["gdof_per_s"]
+                                  / out["small_level_one_per_call"]["gdof_per_s"])
     for m in meshes:
         m.close()
+    rates = {}
+    start = 0
+    for count, N, k in BATCH_LEVELS[1:]:
+        ms_, bs_, xs_, sz_ = _batch_meshes([(min(count, sequential_samples), N, k)],
+                                           seed0=1000 + BATCH_LEVELS[0][0] + start)
+        rates[f"{N}^3 Q{k}"] = _timed_sequential(ms_, bs_, sz_, list(range(len(ms_))))
+        start += count
+        for m in ms_:
+            m.close()
+    out["one_per_call_larger_levels"] = rates
+    if full:
+        meshes, bs, xs, sizes = _batch_meshes(BATCH_LEVELS)
+        out["full_batch"] = _timed_batched(meshes, bs, xs, sizes, world)
+        for m in meshes:
+            m.close()
     return out
+
+
+def run_cg_probe(iters: int):
+    """A fixed number of iterations of the mixed and FP64 CG on the CG
+    workload (48^3 Q4), with wall times; for kernel launch lists."""
+    import torch
+    import paper_1911_01492_gb300 as dg
+    from paper_1911_01492_gb300 import inputs
+    N, k = CG_WORKLOAD["n_cells"], CG_WORKLOAD["degree"]
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(inputs.lognormal_coefficient(N, k, seed=CG_WORKLOAD["K_seed"])).cuda())
+    b = torch.from_numpy(inputs.constant_load_vector(N, k)).cuda()
+    for name, mode in (("mixed_ir", dg.DG_CG_MIXED_IR), ("fp64", dg.DG_CG_FP64)):
+        x = torch.zeros_like(b)
+        _, st = m.cg_solve(b, x, rtol=1e-12, maxit=iters, mode=mode, raise_on_error=False)
+        print(json.dumps({"mode": name, "iterations": st["iterations"],
+                          "ms_per_iteration": 1e3 * st["seconds"] / max(st["iterations"], 1)}),
+              flush=True)
 
 
 def main(argv=None):
@@ -346,6 +395,11 @@ def main(argv=None):
                     help="also run the 256-sample batched CG workload")
     ap.add_argument("--batched-sequential", type=int, default=4,
                     help="samples per level re-solved one per call for the comparison")
+    ap.add_argument("--cg-probe", type=int, default=0, metavar="ITERS",
+                    help="only run ITERS iterations of each CG mode on the CG workload "
+                         "(for kernel profiles) and exit")
+    ap.add_argument("--batched-full", action="store_true",
+                    help="with --batched: also solve the whole 256-sample batch (minutes)")
     ap.add_argument("--n-cells", type=int, default=WORKLOAD["n_cells"],
                     help="cells per direction (default: the 64^3 workload)")
     ap.add_argument("--degree", type=int, default=WORKLOAD["degree"])
@@ -354,6 +408,9 @@ def main(argv=None):
 
     WORKLOAD["n_cells"], WORKLOAD["degree"] = args.n_cells, args.degree
     world, rank, local = dist_setup()
+    if args.cg_probe:
+        run_cg_probe(args.cg_probe)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
@@ -378,17 +435,19 @@ def main(argv=None):
     # roofline of the dominant kernel (pass 2, the cell kernel): FP64 pipe
     f1, f2 = flops_per_dof(n)
     t1, t2 = ms1 / max(napp, 1), ms2 / max(napp, 1)
-    dom_ms, dom_flops, dom_name = (t2, f2 * nd, "k_cell") if t2 >= t1 else (t1, f1 * nd, "k_trace")
+    dom_ms, dom_flops, dom_name = ((t2, f2 * nd, "k_cell_lo") if t2 >= t1
+                                   else (t1, f1 * nd, "k_trace"))
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
-    traffic = K_CELL_TRAFFIC_PER_DOF * nd if (dom_name == "k_cell" and n == 4) else None
+    traffic = (K_CELL_TRAFFIC_PER_DOF * nd
+               if (dom_name == "k_cell_lo" and n == 4 and K_CELL_TRAFFIC_PER_DOF) else None)
     roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved,
                 "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_cell "
-                                  "on 40^3 Q3, scaled by DOFs",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
+                                  "pass-2 kernel on 40^3 Q3, scaled by DOFs",
                 "peak_source": "nominal GB300 FP64 rate (derived: 152 SMs x 2 DFMA/clk x 2 x "
                                "2.06 GHz); a DFMA throughput probe measured 1.0 TFLOP/s",
-                "pass_ms": {"k_trace": t1, "k_cell": t2},
+                "pass_ms": {"k_trace": t1, "k_cell_lo": t2},
                 "apply_tflops_algorithmic": (f1 + f2) * nd / (ms_step * 1e-3) / 1e12}
 
     # end to end through the host-buffer entry point
@@ -412,7 +471,7 @@ def main(argv=None):
     batched = None
     if args.batched:
         torch.cuda.empty_cache()
-        batched = run_batched(world, rank, args.batched_sequential)
+        batched = run_batched(world, rank, args.batched_sequential, args.batched_full)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -227,6 +227,42 @@ __device__ __forceinline__ void face_point(const T* __restrict__ TR, const T* __
   flux<N, UPPER>(uo, go, un, gn, fw[0], fw[N2], cv, cdm);
 }
 
+// Where pass 2 gets its face data.  FaceGlobal: own and neighbour traces from
+// the pass-1 buffer, face-point weights from the precomputed buffer.
+template <typename T>
+struct FaceGlobal {
+  const T* TR;
+  const T* FW;
+  template <int N, bool UPPER>
+  __device__ __forceinline__ void get(long long c, int lc, int f, bool in, long long cn, int fn,
+                                      int pt, T& cv, T& cdm) const {
+    (void)lc;
+    face_point<N, UPPER>(TR, FW, c, f, in, cn, fn, pt, cv, cdm);
+  }
+};
+
+// FaceLocal: own traces from shared memory (computed in the same kernel),
+// neighbour traces from the pass-1 buffer, weights from h*gamma per face
+// (W/2 = h gamma w_s w_t / 2; the derivative weight doubles on the boundary).
+template <typename T>
+struct FaceLocal {
+  const T* TR;
+  const T* str;
+  const T* gh;
+  const DGTab<T>* tab;
+  template <int N, bool UPPER>
+  __device__ __forceinline__ void get(long long c, int lc, int f, bool in, long long cn, int fn,
+                                      int pt, T& cv, T& cdm) const {
+    constexpr int N2 = N * N;
+    const T* own = str + lc * (12 * N2) + (2 * f) * N2 + pt;
+    const T uo = own[0], go = own[N2];
+    T un = T(0), gn = go;
+    if (in) load_trace<N>(TR, cn, fn, pt, un, gn);
+    const T wh = T(0.5) * gh[c * 6 + f] * tab->w[pt % N] * tab->w[pt / N];
+    flux<N, UPPER>(uo, go, un, gn, wh, in ? wh : wh + wh, cv, cdm);
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Pass 1: nodal values and face traces.
 // TR layout: TR[((c*6 + f)*2 + comp)*n^2 + pt], f = x-, x+, y-, y+, z-, z+,
@@ -236,14 +272,15 @@ __device__ __forceinline__ void face_point(const T* __restrict__ TR, const T* __
 // Pass 1 over the cells c0 .. c0+nblk-1 (nblk <= CPB) by the calling block;
 // s: CPB n^3 values of shared memory.  Threads beyond CPB n^2 only take part
 // in the loads and barriers.
-template <int N, typename T>
-__device__ __forceinline__ void trace_cells(const T* __restrict__ x, T* __restrict__ U,
-                                            T* __restrict__ Xm, T* __restrict__ TR, long long c0,
-                                            int nblk, const DGTab<T>& tab, T* s) {
+// trace_core: s already holds the cells' modal coefficients.
+//   MODE 0 (pass 1): writes U, X and the face traces to global memory;
+//   MODE 1: leaves U in s, copies X to sx and the traces to str (shared);
+//   MODE 2: writes only the face traces to global memory.
+template <int N, typename T, int MODE>
+__device__ __forceinline__ void trace_core(T* __restrict__ U, T* __restrict__ Xm,
+                                           T* __restrict__ TR, long long c0, int nblk,
+                                           const DGTab<T>& tab, T* s, T* sx, T* str) {
   constexpr int N2 = N * N, N3 = N * N * N, H = N / 2;
-  const T* xb = x + c0 * N3;
-  for (int t = threadIdx.x; t < nblk * N3; t += blockDim.x) s[t] = xb[t];
-  __syncthreads();
 
   const int lc = threadIdx.x / N2;
   const int t2 = threadIdx.x - lc * N2;
@@ -273,14 +310,16 @@ __device__ __forceinline__ void trace_cells(const T* __restrict__ x, T* __restri
   }
   __syncthreads();
   // along x: thread owns (b = p, e = q); X is modal in x, nodal in y and z
-  T* tr = TR + c * (12 * N2);
+  T* tr = (MODE == 1) ? str + lc * (12 * N2) : TR + c * (12 * N2);
   if (active) {
     T X[N], u[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) X[i] = sc[q * N2 + p * N + i];
-    T* xm = Xm + c * N3 + q * N2 + p * N;
+    if (MODE != 2) {
+      T* xm = (MODE == 0) ? Xm + c * N3 + q * N2 + p * N : sx + lc * N3 + q * N2 + p * N;
 #pragma unroll
-    for (int i = 0; i < N; ++i) xm[i] = X[i];
+      for (int i = 0; i < N; ++i) xm[i] = X[i];
+    }
     // x-face traces from the modes: L_i(1) = a_i, L_i(0) = (-1)^i a_i,
     // L_i'(1) = d_i, L_i'(0) = (-1)^(i+1) d_i, a_0 = 1, d_0 = 0
     T Se = X[0], So = tab.a1[1] * X[1];
@@ -303,11 +342,10 @@ __device__ __forceinline__ void trace_cells(const T* __restrict__ x, T* __restri
     tr[2 * N2 + pt] = Se + So;                 // x+ value
     tr[3 * N2 + pt] = (N > 2) ? Do + De : Do;  // x+ derivative
     b_fwd<N>(tab, X, u);
-    T* ug = U + c * N3 + q * N2 + p * N;
 #pragma unroll
     for (int a = 0; a < N; ++a) {
       sc[q * N2 + p * N + a] = u[a];
-      ug[a] = u[a];
+      if (MODE == 0) U[c * N3 + q * N2 + p * N + a] = u[a];
     }
   }
   __syncthreads();
@@ -341,6 +379,21 @@ __device__ __forceinline__ void trace_cells(const T* __restrict__ x, T* __restri
     }
   }
   (void)H;
+  (void)N3;
+}
+
+// Pass 1 over the cells c0 .. c0+nblk-1 (nblk <= CPB) by the calling block;
+// s: CPB n^3 values of shared memory.  Threads beyond CPB n^2 only take part
+// in the loads and barriers.
+template <int N, typename T>
+__device__ __forceinline__ void trace_cells(const T* __restrict__ x, T* __restrict__ U,
+                                            T* __restrict__ Xm, T* __restrict__ TR, long long c0,
+                                            int nblk, const DGTab<T>& tab, T* s) {
+  constexpr int N3 = N * N * N;
+  const T* xb = x + c0 * N3;
+  for (int t = threadIdx.x; t < nblk * N3; t += blockDim.x) s[t] = xb[t];
+  __syncthreads();
+  trace_core<N, T, 0>(U, Xm, TR, c0, nblk, tab, s, nullptr, nullptr);
 }
 
 template <int N, typename T>
@@ -362,28 +415,23 @@ k_trace(const T* __restrict__ x, T* __restrict__ U, T* __restrict__ Xm, T* __res
 // ---------------------------------------------------------------------------
 // Pass 2 over the cells c0 .. c0+nblk-1 (nblk <= CPB) by the calling block;
 // smem: 4 CPB n^3 values of shared memory.
-template <int N, typename T>
-__device__ __forceinline__ void cell_cells(const T* __restrict__ U, const T* __restrict__ Xm,
-                                           const T* __restrict__ TR, const T* __restrict__ kt,
-                                           const T* __restrict__ FW, T* __restrict__ y,
-                                           long long c0, int nblk, int Nc, const DGTab<T>& tab,
-                                           T* smem) {
-  constexpr int N2 = N * N, N3 = N * N * N, C = Cfg<N>::CPB;
-  T* su = smem;
-  T* sx = su + C * N3;
-  T* sr = sx + C * N3;
-  T* sk = sr + C * N3;
-  {
-    const T* ub = U + c0 * N3;
-    const T* xb = Xm + c0 * N3;
-    const T* kb = kt + c0 * N3;
-    for (int t = threadIdx.x; t < nblk * N3; t += blockDim.x) {
-      su[t] = ub[t];
-      sx[t] = xb[t];
-      sk[t] = kb[t];
-    }
-  }
-  __syncthreads();
+// cell_core: su (nodal U), sx (x-modal X) and sk (h w K) already hold the
+// cells' data in shared memory; face data come from the policy fs; y gets the
+// result.
+// Packed upper triangle of a symmetric n x n line operator: entry (i, j), i <= j.
+template <int N>
+__host__ __device__ constexpr int packed(int i, int j) {
+  return i <= j ? i * N - i * (i - 1) / 2 + (j - i) : j * N - j * (j - 1) / 2 + (i - j);
+}
+
+// LINEOP = true: the volume term of a line is one precomputed symmetric
+// operator per line (lineop: [c][x,y,z][line][packed n(n+1)/2], see
+// k_line_ops) instead of D^T diag(Kt) D (y, z) and L'^T diag(Kt) L' (x).
+template <int N, typename T, typename FS, bool LINEOP = false>
+__device__ __forceinline__ void cell_core(const FS& fs, T* __restrict__ y, long long c0,
+                                          int nblk, int Nc, const DGTab<T>& tab, T* su, T* sx,
+                                          T* sr, T* sk, const T* __restrict__ lineop = nullptr) {
+  constexpr int N2 = N * N, N3 = N * N * N, NP = N * (N + 1) / 2;
 
   const int lc = threadIdx.x / N2;
   const int t2 = threadIdx.x - lc * N2;
@@ -404,30 +452,48 @@ __device__ __forceinline__ void cell_cells(const T* __restrict__ U, const T* __r
       // dir 0: z-line of (a = p, b = q); dir 1: y-line of (a = p, e = q)
       const int base = (dir == 0) ? (q * N + p) : (q * N2 + p);
       const int step = (dir == 0) ? N2 : N;
-      T u[N], kg[N], r[N];
+      T u[N], r[N];
 #pragma unroll
       for (int e = 0; e < N; ++e) u[e] = su[o + base + e * step];
+      if (LINEOP) {
+        // dir 0 = z-lines (operator slot 2), dir 1 = y-lines (slot 1)
+        const T* Mp = lineop + ((c * 3 + (2 - dir)) * N2 + pt) * NP;
+        T Mv[NP];
 #pragma unroll
-      for (int e = 0; e < N; ++e) {
-        T g = tab.D[e][0] * u[0];
+        for (int t = 0; t < NP; ++t) Mv[t] = Mp[t];
 #pragma unroll
-        for (int f = 1; f < N; ++f) g = fma(tab.D[e][f], u[f], g);
-        kg[e] = sk[o + base + e * step] * g;
-      }
+        for (int e = 0; e < N; ++e) {
+          T acc = (dir == 0) ? Mv[packed<N>(e, 0)] * u[0]
+                             : fma(Mv[packed<N>(e, 0)], u[0], sr[o + base + e * step]);
 #pragma unroll
-      for (int e = 0; e < N; ++e) {
-        T acc = (dir == 0) ? tab.D[0][e] * kg[0] : fma(tab.D[0][e], kg[0], sr[o + base + e * step]);
+          for (int f = 1; f < N; ++f) acc = fma(Mv[packed<N>(e, f)], u[f], acc);
+          r[e] = acc;
+        }
+      } else {
+        T kg[N];
 #pragma unroll
-        for (int f = 1; f < N; ++f) acc = fma(tab.D[f][e], kg[f], acc);
-        r[e] = acc;
+        for (int e = 0; e < N; ++e) {
+          T g = tab.D[e][0] * u[0];
+#pragma unroll
+          for (int f = 1; f < N; ++f) g = fma(tab.D[e][f], u[f], g);
+          kg[e] = sk[o + base + e * step] * g;
+        }
+#pragma unroll
+        for (int e = 0; e < N; ++e) {
+          T acc = (dir == 0) ? tab.D[0][e] * kg[0]
+                             : fma(tab.D[0][e], kg[0], sr[o + base + e * step]);
+#pragma unroll
+          for (int f = 1; f < N; ++f) acc = fma(tab.D[f][e], kg[f], acc);
+          r[e] = acc;
+        }
       }
       const int fu = (dir == 0) ? 5 : 3, fl = fu - 1;
       const bool inu = (dir == 0) ? (cz < Nc - 1) : (cy < Nc - 1);
       const bool inl = (dir == 0) ? (cz > 0) : (cy > 0);
       const long long st = (dir == 0) ? sz : sy;
       T cv1, cd1, cv0, cd0;
-      face_point<N, true>(TR, FW, c, fu, inu, c + st, fl, pt, cv1, cd1);
-      face_point<N, false>(TR, FW, c, fl, inl, c - st, fu, pt, cv0, cd0);
+      fs.template get<N, true>(c, lc, fu, inu, c + st, fl, pt, cv1, cd1);
+      fs.template get<N, false>(c, lc, fl, inl, c - st, fu, pt, cv0, cd0);
 #pragma unroll
       for (int e = 0; e < N; ++e) {
         T acc = fma(tab.l1[e], cv1, r[e]);
@@ -443,19 +509,33 @@ __device__ __forceinline__ void cell_cells(const T* __restrict__ U, const T* __r
   // x-lines: thread owns (b = p, e = q); result is x-modal, yz-nodal
   if (active) {
     const int base = q * N2 + p * N;
-    T X[N], g[N], kg[N], rr[N], R[N];
+    T X[N], rr[N], R[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) X[i] = sx[o + base + i];
-    bd_fwd<N>(tab, X, g);
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-      kg[a] = sk[o + base + a] * g[a];
-      rr[a] = sr[o + base + a];
+    for (int i = 0; i < N; ++i) {
+      X[i] = sx[o + base + i];
+      rr[i] = sr[o + base + i];
     }
-    bt_bdt<N>(tab, rr, kg, R);
+    if (LINEOP) {
+      b_bwd<N>(tab, rr, R);
+      const T* Mp = lineop + ((c * 3 + 0) * N2 + pt) * NP;
+      T Mv[NP];
+#pragma unroll
+      for (int t = 0; t < NP; ++t) Mv[t] = Mp[t];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) R[i] = fma(Mv[packed<N>(i, j)], X[j], R[i]);
+      }
+    } else {
+      T g[N], kg[N];
+      bd_fwd<N>(tab, X, g);
+#pragma unroll
+      for (int a = 0; a < N; ++a) kg[a] = sk[o + base + a] * g[a];
+      bt_bdt<N>(tab, rr, kg, R);
+    }
     T cv1, cd1, cv0, cd0;
-    face_point<N, true>(TR, FW, c, 1, cx < Nc - 1, c + 1, 0, pt, cv1, cd1);
-    face_point<N, false>(TR, FW, c, 0, cx > 0, c - 1, 1, pt, cv0, cd0);
+    fs.template get<N, true>(c, lc, 1, cx < Nc - 1, c + 1, 0, pt, cv1, cd1);
+    fs.template get<N, false>(c, lc, 0, cx > 0, c - 1, 1, pt, cv0, cd0);
     // modal test functions: value a_i at 1, (-1)^i a_i at 0; derivative -d_i cd
     // at 1, -(-1)^(i+1) d_i cd at 0 (a_0 = 1, d_0 = 0)
     const T sp = cv1 + cv0, sm = cv1 - cv0;
@@ -496,6 +576,35 @@ __device__ __forceinline__ void cell_cells(const T* __restrict__ U, const T* __r
   for (int t = threadIdx.x; t < nblk * N3; t += blockDim.x) yb[t] = sx[t];
 }
 
+// Pass 2 over the cells c0 .. c0+nblk-1 (nblk <= CPB) by the calling block;
+// smem: 4 CPB n^3 values of shared memory.
+// LINEOP: the volume term uses the precomputed line operators (kt unused).
+template <int N, typename T, bool LINEOP = false>
+__device__ __forceinline__ void cell_cells(const T* __restrict__ U, const T* __restrict__ Xm,
+                                           const T* __restrict__ TR, const T* __restrict__ kt,
+                                           const T* __restrict__ FW, T* __restrict__ y,
+                                           long long c0, int nblk, int Nc, const DGTab<T>& tab,
+                                           T* smem, const T* __restrict__ lineop = nullptr) {
+  constexpr int N3 = N * N * N, C = Cfg<N>::CPB;
+  T* su = smem;
+  T* sx = su + C * N3;
+  T* sr = sx + C * N3;
+  T* sk = sr + C * N3;
+  {
+    const T* ub = U + c0 * N3;
+    const T* xb = Xm + c0 * N3;
+    const T* kb = kt + c0 * N3;
+    for (int t = threadIdx.x; t < nblk * N3; t += blockDim.x) {
+      su[t] = ub[t];
+      sx[t] = xb[t];
+      if (!LINEOP) sk[t] = kb[t];
+    }
+  }
+  __syncthreads();
+  const FaceGlobal<T> fs{TR, FW};
+  cell_core<N, T, FaceGlobal<T>, LINEOP>(fs, y, c0, nblk, Nc, tab, su, sx, sr, sk, lineop);
+}
+
 template <int N, typename T>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_cell(const T* __restrict__ U, const T* __restrict__ Xm, const T* __restrict__ TR,
@@ -507,6 +616,63 @@ k_cell(const T* __restrict__ U, const T* __restrict__ Xm, const T* __restrict__ 
   const long long c0 = (long long)blockIdx.x * C;
   const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
   cell_cells<N, T>(U, Xm, TR, kt, FW, y, c0, nblk, Nc, tab, reinterpret_cast<T*>(smem_raw));
+}
+
+// Pass 2 with the precomputed line operators (FP64 path of dg_apply).
+template <int N, typename T>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+k_cell_lo(const T* __restrict__ U, const T* __restrict__ Xm, const T* __restrict__ TR,
+          const T* __restrict__ lineop, const T* __restrict__ FW, T* __restrict__ y,
+          long long ncells, int Nc, const int* __restrict__ skip,
+          const __grid_constant__ DGTab<T> tab) {
+  constexpr int C = Cfg<N>::CPB;
+  if (skip != nullptr && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long c0 = (long long)blockIdx.x * C;
+  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
+  cell_cells<N, T, true>(U, Xm, TR, nullptr, FW, y, c0, nblk, Nc, tab,
+                         reinterpret_cast<T*>(smem_raw), lineop);
+}
+
+// Line operators from Kt = h w K (one thread per cell, direction and line):
+//   x-line (b, e):  M[i][j] = sum_a L_i'(xi_a) Kt(a, b, e) L_j'(xi_a)   (acts on x-modes)
+//   y-line (a, e):  M[i][j] = sum_f D[f][i] Kt(a, f, e) D[f][j]         (acts on nodal values)
+//   z-line (a, b):  M[i][j] = sum_f D[f][i] Kt(a, b, f) D[f][j]
+// stored as lineop[((c*3 + dir)*n^2 + line)*n(n+1)/2 + packed(i, j)].
+template <int N>
+__global__ void k_line_ops(const double* __restrict__ kt, double* __restrict__ lineop,
+                           long long ncells, const __grid_constant__ DGTab<double> tab) {
+  constexpr int N2 = N * N, N3 = N * N * N, NP = N * (N + 1) / 2;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ncells * 3 * N2) return;
+  const long long c = t / (3 * N2);
+  const int dir = (int)((t / N2) % 3);
+  const int line = (int)(t % N2);
+  const int p = line % N, q = line / N;
+  double k[N];
+#pragma unroll
+  for (int f = 0; f < N; ++f) {
+    // point index a + N(b + N e) along the line
+    const int qi = dir == 0 ? f + N * (p + N * q)      // x-line (b = p, e = q)
+                 : dir == 1 ? p + N * (f + N * q)      // y-line (a = p, e = q)
+                            : p + N * (q + N * f);     // z-line (a = p, b = q)
+    k[f] = kt[c * N3 + qi];
+  }
+  double* M = lineop + (t)*NP;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+#pragma unroll
+    for (int j = i; j < N; ++j) {
+      double acc = 0.0;
+#pragma unroll
+      for (int f = 0; f < N; ++f) {
+        const double gi = dir == 0 ? tab.Bd[f][i] : tab.D[f][i];
+        const double gj = dir == 0 ? tab.Bd[f][j] : tab.D[f][j];
+        acc = fma(gi * k[f], gj, acc);
+      }
+      M[packed<N>(i, j)] = acc;
+    }
+  }
 }
 
 template <int N, typename T>
@@ -546,7 +712,11 @@ cudaError_t launch_apply_n(const dg_mesh* m, const T* x, T* y, T* U, T* X, T* TR
   dg_timing_mark(m, 0, s);
   k_trace<N, T><<<blocks, Cfg<N>::THREADS, s1, s>>>(x, U, X, TR, ncells, skip, tab);
   dg_timing_mark(m, 1, s);
-  k_cell<N, T><<<blocks, Cfg<N>::THREADS, s2, s>>>(U, X, TR, kt, fw, y, ncells, Nc, skip, tab);
+  if (sizeof(T) == 8 && m != nullptr && m->lineop64 != nullptr)
+    k_cell_lo<N, T><<<blocks, Cfg<N>::THREADS, s2, s>>>(U, X, TR, (const T*)m->lineop64, fw, y,
+                                                        ncells, Nc, skip, tab);
+  else
+    k_cell<N, T><<<blocks, Cfg<N>::THREADS, s2, s>>>(U, X, TR, kt, fw, y, ncells, Nc, skip, tab);
   dg_timing_mark(m, 2, s);
   return cudaGetLastError();
 }
@@ -593,6 +763,9 @@ struct PrepareF {
     cudaError_t e = cudaFuncSetAttribute(k_cell<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cell_smem<N, T>());
     if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_cell_lo<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)cell_smem<N, T>());
+    if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_trace<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)trace_smem<N, T>());
     return e;
@@ -608,4 +781,17 @@ struct TraceF {
   }
 };
 
+}  // namespace dgk
+
+namespace dgk {
+template <int N>
+struct LineOpsF {
+  template <typename T>
+  static cudaError_t run(const double* kt, double* lineop, long long ncells,
+                         const DGTab<double>* tab, cudaStream_t s) {
+    const long long threads = ncells * 3 * N * N;
+    k_line_ops<N><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(kt, lineop, ncells, *tab);
+    return cudaGetLastError();
+  }
+};
 }  // namespace dgk

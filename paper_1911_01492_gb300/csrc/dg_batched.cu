@@ -35,7 +35,8 @@ namespace {
 
 constexpr int BT = 128;        // threads per block (>= n^2 * cells per unit for n <= 5)
 constexpr int MAXN_B = 5;      // batched solver supports n = 2..5 (degree 1..4)
-constexpr int ITERS_PER_LAUNCH = 64;
+constexpr int ITERS_PER_LAUNCH = 64;  // lock-step iterations per persistent launch
+constexpr int ITERS_TUNE = 4;         // iterations per launch while autotuning
 
 __constant__ DGTab<double> c_btab[MAXN_B - 1];  // tables for n = 2..5
 
@@ -46,6 +47,7 @@ struct SampleDev {
   double *U, *X, *TR;
   const double* kt;
   const double* fw;
+  const double* lineop;
   long long ncells;
   int Nc;       // cells per direction
   int n;        // points per direction
@@ -119,8 +121,8 @@ __device__ __forceinline__ void unit_pass1(const SampleDev& S, long long c0, int
 template <int N>
 __device__ __forceinline__ void unit_pass2(const SampleDev& S, long long c0, int nblk,
                                            double* smem) {
-  dgk::cell_cells<N, double>(S.U, S.X, S.TR, S.kt, S.fw, S.q, c0, nblk, S.Nc, c_btab[N - 2],
-                             smem);
+  dgk::cell_cells<N, double, true>(S.U, S.X, S.TR, S.kt, S.fw, S.q, c0, nblk, S.Nc,
+                                   c_btab[N - 2], smem, S.lineop);
 }
 
 __device__ __forceinline__ int unit_cells(int n) {
@@ -374,7 +376,8 @@ struct Batch {
   }
 };
 
-int launch_persistent(Batch& B, int ns, int blocks, long long limit, int stall, cudaStream_t s) {
+int launch_persistent(Batch& B, int ns, int blocks, int iters, long long limit, int stall,
+                      cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(BT);
@@ -387,7 +390,7 @@ int launch_persistent(Batch& B, int ns, int blocks, long long limit, int stall, 
   cfg.numAttrs = 1;
   DG_CUDA(cudaLaunchKernelEx(&cfg, kb_persistent, (const SampleDev*)B.d_samples, ns,
                              (const int2*)B.d_units, B.nunits, B.d_state, B.d_part, B.d_ctl,
-                             ITERS_PER_LAUNCH, limit, stall));
+                             iters, limit, stall));
   return DG_OK;
 }
 
@@ -438,6 +441,7 @@ extern "C" int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, cons
     d.TR = m->TR64;
     d.kt = m->kt64;
     d.fw = m->fw64;
+    d.lineop = m->lineop64;
     d.ncells = m->ncells;
     d.Nc = m->N;
     d.n = m->n;
@@ -542,23 +546,26 @@ extern "C" int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, cons
     if (bpsm > 0) cands.push_back(bpsm);
     else
       for (int c = 1; c <= max_bpsm; ++c) cands.push_back(c);
-    std::vector<cudaGraphExec_t> execs(max_bpsm + 1, nullptr);
-    auto get_exec = [&](int c, cudaGraphExec_t* out) -> int {
-      if (!execs[c]) {
+    // graphs: [c] = production launch (64 iterations), [max_bpsm + 1 + c] = tuning launch
+    std::vector<cudaGraphExec_t> execs(2 * (max_bpsm + 1), nullptr);
+    auto get_exec = [&](int c, bool tune, cudaGraphExec_t* out) -> int {
+      const int slot = tune ? max_bpsm + 1 + c : c;
+      if (!execs[slot]) {
         cudaGraph_t g = nullptr;
         DG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        int rc = launch_persistent(B, count, c * sms, limit, stall, s);
+        int rc = launch_persistent(B, count, c * sms, tune ? ITERS_TUNE : ITERS_PER_LAUNCH,
+                                   limit, stall, s);
         cudaError_t ec = cudaStreamEndCapture(s, &g);
         if (rc) {
           if (g) cudaGraphDestroy(g);
           return rc;
         }
         DG_CUDA(ec);
-        ec = cudaGraphInstantiate(&execs[c], g, 0);
+        ec = cudaGraphInstantiate(&execs[slot], g, 0);
         cudaGraphDestroy(g);
         DG_CUDA(ec);
       }
-      *out = execs[c];
+      *out = execs[slot];
       return DG_OK;
     };
     auto destroy_execs = [&]() {
@@ -573,10 +580,11 @@ extern "C" int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, cons
     size_t ci = 0;
     int rc = DG_OK;
     for (;;) {
-      const bool tuning = ci < cands.size();
+      const bool tuning = ci < cands.size() && cands.size() > 1;
+      if (!tuning && ci < cands.size()) ci = cands.size();  // one candidate: nothing to tune
       const int c = tuning ? cands[ci] : best_c;
       cudaGraphExec_t ex;
-      rc = get_exec(c, &ex);
+      rc = get_exec(c, tuning, &ex);
       if (rc) break;
       const unsigned long long before = B.h_ctl->iterations_run;
       cudaError_t ec = cudaEventRecord(e0, s);
@@ -607,7 +615,7 @@ extern "C" int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, cons
           }
         }
         ++ci;
-        if (ci == cands.size()) {
+        if (ci == cands.size() && best_t < 1e300) {
           std::lock_guard<std::mutex> lk(g_tune_mu);
           g_tune[sig] = best_c;
         }

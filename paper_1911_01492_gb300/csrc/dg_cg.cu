@@ -15,7 +15,8 @@
 // to FP64.
 //
 // Mixed precision (DG_CG_MIXED_IR): the CG recurrence runs on the FP32 operator
-// with FP32 vectors; x and the true residual are kept in FP64.  When the FP32
+// with FP32 vectors (fused kernels in dg_mixed32.cu); x and the true residual
+// are kept in FP64.  When the FP32
 // residual has dropped below delta times its value at the last refinement (or
 // below the tolerance), the FP32 correction d is added to x in FP64, r = b - A x
 // is recomputed with the FP64 operator, and r replaces the FP32 residual; the
@@ -65,6 +66,38 @@ struct AccF {
   }
   __device__ double block_total();
 };
+__device__ __forceinline__ void merge(AccD& a, const AccD& b) { a.s += b.s; }
+__device__ __forceinline__ void merge(AccF& a, const AccF& b) {
+  float s, t;
+  two_sum(a.hi, b.hi, s, t);
+  a.hi = s;
+  a.lo += b.lo + t;
+}
+
+// Visit i = tid, tid + S, ... < n (S = grid size) four strides at a time; f(i, j)
+// receives the lane j in 0..3 so that reductions keep four independent
+// accumulators (more loads in flight, shorter dependency chains).
+template <typename F>
+__device__ __forceinline__ void grid_stride4(long long n, F&& f) {
+  const long long S = (long long)gridDim.x * blockDim.x;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * S < n; i += 4 * S) {
+    f(i, 0);
+    f(i + S, 1);
+    f(i + 2 * S, 2);
+    f(i + 3 * S, 3);
+  }
+  for (; i < n; i += S) f(i, 0);
+}
+
+template <typename A>
+__device__ __forceinline__ A merge4(A (&a)[4]) {
+  merge(a[0], a[1]);
+  merge(a[2], a[3]);
+  merge(a[0], a[2]);
+  return a[0];
+}
+
 template <typename T> struct AccOf;
 template <> struct AccOf<double> { using type = AccD; };
 template <> struct AccOf<float> { using type = AccF; };
@@ -146,14 +179,16 @@ template <typename T>
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_init(const T* __restrict__ b, const T* __restrict__ q, T* __restrict__ r, T* __restrict__ p,
        long long n, double rtol, double* partials, DGCGState* st) {
-  typename AccOf<T>::type acc[2];
-  GRID_STRIDE(i, n) {
+  using A = typename AccOf<T>::type;
+  A ar[4], ab[4];
+  grid_stride4(n, [&](long long i, int j) {
     const T ri = b[i] - q[i];
     r[i] = ri;
     p[i] = ri;
-    acc[0].add_prod(ri, ri);
-    acc[1].add_prod(b[i], b[i]);
-  }
+    ar[j].add_prod(ri, ri);
+    ab[j].add_prod(b[i], b[i]);
+  });
+  A acc[2] = {merge4(ar), merge4(ab)};
   double tot[2];
   if (last_block_sums<2>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
     st->rho = tot[0];
@@ -171,8 +206,10 @@ __global__ void __launch_bounds__(DG_RED_THREADS)
 k_dot_pq(const T* __restrict__ p, const T* __restrict__ q, long long n, double* partials,
          DGCGState* st) {
   if (st->done) return;
-  typename AccOf<T>::type acc[1];
-  GRID_STRIDE(i, n) acc[0].add_prod(p[i], q[i]);
+  using A = typename AccOf<T>::type;
+  A a4[4];
+  grid_stride4(n, [&](long long i, int j) { a4[j].add_prod(p[i], q[i]); });
+  A acc[1] = {merge4(a4)};
   double tot[1];
   if (last_block_sums<1>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
     st->pq = tot[0];
@@ -188,22 +225,25 @@ k_dot_pq(const T* __restrict__ p, const T* __restrict__ q, long long n, double* 
 
 // x += alpha p, r -= alpha q, rho' = <r, r>.
 // MIXED = false: convergence test on rho', beta, rho = rho'.
-// MIXED = true: request an FP64 refinement (ru_skip = 0) when rho' has dropped
-// below delta2 * rmax2 or below tol2, or at the iteration cap; rho' is kept in
-// rho_new for the direction update.
+// MIXED = true: rho' goes to rho_new for the direction update, and an FP64
+// refinement is requested (ru_skip = 0, sticky until the refinement runs) when
+// rho' has dropped below delta2 * rmax2 or below tol2, or at the iteration
+// cap; at the cap the FP32 iteration stops.
 template <typename T, bool MIXED>
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
             const T* __restrict__ q, long long n, double* partials, DGCGState* st) {
-  if (st->done) return;
+  if (st->done || (MIXED && st->iters >= st->maxit)) return;
   const T a = (T)st->alpha;
-  typename AccOf<T>::type acc[1];
-  GRID_STRIDE(i, n) {
+  using A = typename AccOf<T>::type;
+  A a4[4];
+  grid_stride4(n, [&](long long i, int j) {
     x[i] = fma(a, p[i], x[i]);
     const T ri = fma(-a, q[i], r[i]);
     r[i] = ri;
-    acc[0].add_prod(ri, ri);
-  }
+    a4[j].add_prod(ri, ri);
+  });
+  A acc[1] = {merge4(a4)};
   double tot[1];
   if (last_block_sums<1>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
     const double rr = tot[0];
@@ -218,27 +258,19 @@ k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
       if (rr <= st->tol2 || st->iters >= st->maxit) st->done = 1;
     } else {
       st->rho_new = rr;
-      st->ru_skip = !(rr <= st->delta2 * st->rmax2 || rr <= st->tol2 || st->iters >= st->maxit);
+      if (rr <= st->delta2 * st->rmax2 || rr <= st->tol2 || st->iters >= st->maxit)
+        st->ru_skip = 0;
     }
   }
 }
 
-// p = r + beta p.  MIXED: beta = rho_new / rho (rho is committed afterwards by
-// k_commit_rho, so every block reads the same pair).
-template <typename T, bool MIXED>
+// p = r + beta p
+template <typename T>
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_update_p(T* __restrict__ p, const T* __restrict__ r, long long n, const DGCGState* st) {
   if (st->done) return;
-  const double beta = MIXED ? (st->restart ? 0.0 : st->rho_new / st->rho) : st->beta;
-  const T be = (T)beta;
-  GRID_STRIDE(i, n) p[i] = fma(be, p[i], r[i]);
-}
-
-// mixed mode: rho = rho_new after the direction update
-__global__ void k_commit_rho(DGCGState* st) {
-  if (st->done) return;
-  st->rho = st->rho_new;
-  st->restart = 0;
+  const T be = (T)st->beta;
+  grid_stride4(n, [&](long long i, int) { p[i] = fma(be, p[i], r[i]); });
 }
 
 // refinement step 1 (mixed): x64 += d32, d32 = 0.
@@ -263,13 +295,14 @@ __global__ void __launch_bounds__(DG_RED_THREADS)
 k_refine_r(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
            float* __restrict__ r32, long long n, double* partials, DGCGState* st) {
   if (st->ru_skip) return;
-  AccD acc[1];
-  GRID_STRIDE(i, n) {
+  AccD a4[4];
+  grid_stride4(n, [&](long long i, int j) {
     const double ri = b[i] - q[i];
     r[i] = ri;
     r32[i] = (float)ri;
-    acc[0].add_prod(ri, ri);
-  }
+    a4[j].add_prod(ri, ri);
+  });
+  AccD acc[1] = {merge4(a4)};
   double tot[1];
   if (last_block_sums<1>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
     const double rr = tot[0];
@@ -292,13 +325,14 @@ k_refine_r(const double* __restrict__ b, const double* __restrict__ q, double* _
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_residual(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
            long long n, double* partials, DGCGState* st) {
-  AccD acc[2];
-  GRID_STRIDE(i, n) {
+  AccD ar[4], ab[4];
+  grid_stride4(n, [&](long long i, int j) {
     const double ri = b[i] - q[i];
     r[i] = ri;
-    acc[0].add_prod(ri, ri);
-    acc[1].add_prod(b[i], b[i]);
-  }
+    ar[j].add_prod(ri, ri);
+    ab[j].add_prod(b[i], b[i]);
+  });
+  AccD acc[2] = {merge4(ar), merge4(ab)};
   double tot[2];
   if (last_block_sums<2>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
     st->res2 = tot[0];
@@ -338,25 +372,32 @@ int launch_iteration(dg_mesh* m, T* x, T* r, T* p, T* q, cudaStream_t s) {
   const long long n = m->ndofs;
   k_dot_pq<T><<<RED_LAUNCH>>>(p, q, n, m->partials, m->state);
   k_update_xr<T, false><<<RED_LAUNCH>>>(x, r, p, q, n, m->partials, m->state);
-  k_update_p<T, false><<<RED_LAUNCH>>>(p, r, n, m->state);
+  k_update_p<T><<<RED_LAUNCH>>>(p, r, n, m->state);
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
 
-// One iteration of mixed CG with the conditional FP64 refinement.
-int launch_iteration_mixed(dg_mesh* m, const double* b, double* x, cudaStream_t s) {
+// One FP32 iteration of the mixed CG: direction update, operator and <p, q>
+// (fused kernels of dg_mixed32.cu), then d += alpha p, r -= alpha q.  The FP64
+// refinement is not in the captured iteration: it runs between graph replays
+// when an iteration has requested it (refine_mixed).
+int launch_iteration_mixed(dg_mesh* m, cudaStream_t s) {
   const long long n = m->ndofs;
-  int rc = dg_launch_apply_f32(m, m->p32, m->q32, &m->state->done, s);
+  int rc = dg_launch_mixed32_dir_cell(m, s);
   if (rc) return rc;
-  k_dot_pq<float><<<RED_LAUNCH>>>(m->p32, m->q32, n, m->partials, m->state);
   k_update_xr<float, true><<<RED_LAUNCH>>>(m->d32, m->r32, m->p32, m->q32, n, m->partials,
                                            m->state);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+// FP64 refinement: x += d, r = b - A x (FP64), r32 = (float) r.
+int refine_mixed(dg_mesh* m, const double* b, double* x, cudaStream_t s) {
+  const long long n = m->ndofs;
   k_refine_x<<<RED_LAUNCH>>>(x, m->d32, n, m->state);
-  rc = dg_launch_apply_f64(m, x, m->q64, &m->state->ru_skip, s);
+  int rc = dg_launch_apply_f64(m, x, m->q64, nullptr, s);
   if (rc) return rc;
   k_refine_r<<<RED_LAUNCH>>>(b, m->q64, m->r64, m->r32, n, m->partials, m->state);
-  k_update_p<float, true><<<RED_LAUNCH>>>(m->p32, m->r32, n, m->state);
-  k_commit_rho<<<1, 1, 0, s>>>(m->state);
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -498,12 +539,44 @@ int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_
     h.delta2 = delta * delta;
     h.done = h.breakdown || res2 <= h.tol2;
     h.ru_skip = 1;
+    h.rho_new = h.rho;  // first direction update: p = r (restart)
+    h.restart = 1;
     *m->state_host = h;
     DG_CUDA(cudaMemcpyAsync(m->state, m->state_host, sizeof(DGCGState), cudaMemcpyHostToDevice,
                             s));
   }
-  rc = run_graph(m, s, chunk_for(m), [&] { return launch_iteration_mixed(m, b, x, s); });
-  if (rc) return rc;
+  // replay a graph of FP32 iterations; refine in FP64 whenever one asked for it
+  {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    DG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < chunk_for(m) && rc == DG_OK; ++i) rc = launch_iteration_mixed(m, s);
+    cudaError_t ec = cudaStreamEndCapture(s, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    DG_CUDA(ec);
+    ec = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    DG_CUDA(ec);
+    for (;;) {
+      ec = cudaMemcpyAsync(m->state_host, m->state, sizeof(DGCGState), cudaMemcpyDeviceToHost, s);
+      if (ec == cudaSuccess) ec = cudaStreamSynchronize(s);
+      if (ec != cudaSuccess) break;
+      if (m->state_host->done) break;
+      if (m->state_host->ru_skip == 0) {
+        rc = refine_mixed(m, b, x, s);
+        if (rc) break;
+        continue;
+      }
+      ec = cudaGraphLaunch(exec, s);
+      if (ec != cudaSuccess) break;
+    }
+    cudaGraphExecDestroy(exec);
+    if (rc) return rc;
+    DG_CUDA(ec);
+  }
   const DGCGState hs = *m->state_host;
   rc = true_residual(m, b, x, s, &res2, &b2);
   if (rc) return rc;

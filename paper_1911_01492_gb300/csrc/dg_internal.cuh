@@ -74,6 +74,7 @@ struct dg_mesh {
   float* gh32;
   double* dgam;     // d gamma_F / d log Kbar_c       [c][6]
   double* fw64;     // face-point weights W/2 and derivative weight  [c][6][2][n^2]
+  double* lineop64; // per-line volume operators (FP64)  [c][3][n^2][n(n+1)/2]
   float* fw32;
   double* kbar;     // Kbar_c                          [c]
   int* dflag;       // device-side error flag of the setup kernels
@@ -90,6 +91,7 @@ struct dg_mesh {
   double *r64, *p64, *q64, *t64;
   float *d32, *r32, *p32, *q32;
   double* partials;       // reduction partials (DG_RED_BLOCKS doubles x 2)
+  double* partials_cells; // one partial per cell block (fused FP32 mixed kernels)
   DGCGState* state;       // device CG state
   DGCGState* state_host;  // pinned mirror
   cudaStream_t solve_stream;
@@ -107,7 +109,7 @@ struct dg_mesh {
 void dg_timing_mark(const dg_mesh* m, int slot, cudaStream_t s);
 
 // Deterministic two-level reductions use this fixed grid.
-#define DG_RED_BLOCKS 608   // 4 x 152 SMs
+#define DG_RED_BLOCKS 1216  // 8 x 152 SMs
 #define DG_RED_THREADS 256
 
 // error reporting (dg_mesh.cu)
@@ -128,6 +130,9 @@ int dg_launch_apply_f32(const dg_mesh* m, const float* x, float* y, const int* s
 int dg_launch_trace_f64(const dg_mesh* m, const double* x, double* U, double* X, double* TR,
                         cudaStream_t s);
 int dg_launch_coeff_grad(const dg_mesh* m, double* g, cudaStream_t s);
+// fused FP32 kernels of the mixed CG iteration (dg_mixed32.cu)
+int dg_launch_mixed32_dir_cell(const dg_mesh* m, cudaStream_t s);
+long long dg_mixed32_blocks(int n, long long ncells);
 // one-time kernel attributes (dynamic shared memory) for points-per-direction n
 int dg_prepare_apply_f64(int n);
 int dg_prepare_apply_f32(int n);

@@ -96,10 +96,11 @@ static cudaError_t dmalloc(P** p, size_t count) {
 }
 
 static void free_all(dg_mesh* m) {
-  void* ptrs[] = {m->kt64, m->kt32, m->gh64, m->gh32, m->dgam, m->kbar, m->dflag, m->fw64, m->fw32,
+  void* ptrs[] = {m->kt64, m->kt32, m->gh64, m->gh32, m->dgam, m->kbar, m->dflag, m->fw64, m->fw32, m->lineop64,
                   m->U64,  m->X64,  m->TR64, m->U32,  m->X32,  m->TR32, m->U64b,
                   m->X64b, m->TR64b, m->hx_dev, m->hy_dev, m->r64, m->p64, m->q64,
-                  m->t64,  m->d32,  m->r32, m->p32, m->q32, m->partials, m->state};
+                  m->t64,  m->d32,  m->r32, m->p32, m->q32, m->partials, m->state,
+                  m->partials_cells};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->state_host) cudaFreeHost(m->state_host);
@@ -141,6 +142,8 @@ extern "C" int dg_create_mesh(int n_cells, int degree, dg_mesh** out) {
   if (e == cudaSuccess) e = dmalloc(&m->dgam, 6 * nc);
   if (e == cudaSuccess) e = dmalloc(&m->fw64, ntr);
   if (e == cudaSuccess) e = dmalloc(&m->fw32, ntr);
+  if (e == cudaSuccess)
+    e = dmalloc(&m->lineop64, (size_t)3 * n2 * (size_t)(m->n * (m->n + 1) / 2) * nc);
   if (e == cudaSuccess) e = dmalloc(&m->kbar, nc);
   if (e == cudaSuccess) e = dmalloc(&m->dflag, 1);
   if (e == cudaSuccess) e = dmalloc(&m->U64, nd);
@@ -208,6 +211,7 @@ int dg_ensure_solver_ws(dg_mesh* m) {
   DG_CUDA(dmalloc(&m->p32, nd));
   DG_CUDA(dmalloc(&m->q32, nd));
   DG_CUDA(dmalloc(&m->partials, 2 * DG_RED_BLOCKS));
+  DG_CUDA(dmalloc(&m->partials_cells, (size_t)dg_mixed32_blocks(m->n, m->ncells)));
   DG_CUDA(cudaMallocHost((void**)&m->state_host, sizeof(DGCGState)));
   DG_CUDA(cudaStreamCreateWithFlags(&m->solve_stream, cudaStreamNonBlocking));
   DG_CUDA(cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming));
@@ -238,6 +242,10 @@ extern "C" int dg_set_coefficient(dg_mesh* m, const double* K, void* stream) {
     dgk::k_face_weights<double><<<blocks, 256, 0, s>>>(m->gh64, m->fw64, m->N, m->n, m->tab64);
     dgk::k_face_weights<float><<<blocks, 256, 0, s>>>(m->gh64, m->fw32, m->N, m->n, m->tab64);
     DG_CUDA(cudaGetLastError());
+    cudaError_t e = dgk::dispatch_n<double, dgk::LineOpsF>(m->n, (const double*)m->kt64,
+                                                           m->lineop64, m->ncells,
+                                                           (const DGTab<double>*)&m->tab64, s);
+    if (e != cudaSuccess) return dg_cuda_fail(e, "dg_set_coefficient: line operators");
   }
   int flag = 0;
   DG_CUDA(cudaMemcpyAsync(&flag, m->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));

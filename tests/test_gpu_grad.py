@@ -87,11 +87,12 @@ def test_solve_gradient_matches_oracle_on_4cubed(dg, k):
 @pytest.mark.slow
 def test_solve_gradient_central_differences_32cubed_q3(dg):
     """32^3 Q3 lognormal K: gradient by adjoint CG against central finite
-    differences along 20 seeded directions (eps = 1e-4).  Solves go to a
-    relative residual of 1e-10 recomputed in FP64: 1e-12 is below what FP64 CG
-    can attain on this operator (its true residual floors near 5e-11, about
-    u_64 times the condition number), and 1e-10 keeps the solve error in the
-    difference quotient near 1e-6 relative."""
+    differences along 20 seeded directions.  Solves go to a relative residual
+    of 1e-10 recomputed in FP64: 1e-12 is below what FP64 CG can attain on this
+    operator (its true residual floors near 5e-11, about u_64 times the
+    condition number).  At that accuracy the solution error is ~1e-7 relative,
+    so eps = 1e-3 (truncation error O(eps^2)) keeps the quotient's error near
+    5e-5; eps = 1e-4 would let the solve error reach ~5e-4."""
     import torch
     from paper_1911_01492_gb300 import autograd as dga
     N, k = 32, 3
@@ -118,7 +119,7 @@ def test_solve_gradient_central_differences_32cubed_q3(dg):
     (0.5 * ((u - u_obs) ** 2).sum()).backward()
     g = lk.grad.clone()
     drng = np.random.default_rng(42)
-    eps = 1e-4
+    eps = 1e-3
     worst = 0.0
     for _ in range(20):
         d = torch.from_numpy(drng.standard_normal(m.n_dofs)).cuda()
