@@ -287,6 +287,37 @@ class SIPG:
                           shape=(Nc * n3, Nc * n3))
         return A.tocsr()
 
+    # -- diagonal (Jacobi preconditioner, Section 2.4's PCG with M = diag(A)) ---
+    def diagonal(self, K, cells=None):
+        """diag(A(K)) on the requested cells (all by default): a(phi_m, phi_m)
+        from the full 3D volume tables and the full face quadrature, with both
+        functions on the cell's own side of every face.  Shape (len(cells), n^3),
+        flattened when cells=None."""
+        Nc, n3, h, sigma = self.n_cells_total, self.n3, self.h, self.sigma
+        K = np.asarray(K, float).reshape(Nc, n3)
+        full = cells is None
+        cells = np.arange(Nc) if full else np.asarray(cells, dtype=np.int64)
+        kt = h * self.wq[None, :] * K[cells]
+        g2 = (self.grad ** 2).sum(axis=-1)                  # (q, m): |grad^ phi_m|^2
+        dg = kt @ g2
+        Kbar = self.kbar(K)
+        for d in range(3):
+            wf = h * self.face_w[d]
+            V0, V1 = self.face_val[(d, 0)], self.face_val[(d, 1)]
+            D0, D1 = self.face_der[(d, 0)], self.face_der[(d, 1)]
+            for upper in (True, False):
+                gamma, interior, _ = self.face_gamma(Kbar, cells, d, upper)
+                # own trace J and own share A of {d_n phi} (the whole d_n phi
+                # on the boundary); the face form gives sigma J^2 - 2 J A
+                if upper:
+                    J, A_int, A_bnd = V1, 0.5 * D1, D1
+                else:
+                    J, A_int, A_bnd = -V0, 0.5 * D0, D0
+                f_int = wf @ (sigma * J * J - 2.0 * J * A_int)
+                f_bnd = wf @ (sigma * J * J - 2.0 * J * A_bnd)
+                dg += gamma[:, None] * np.where(interior[:, None], f_int[None, :], f_bnd[None, :])
+        return dg.reshape(-1) if full else dg
+
     # -- coefficient gradient ---------------------------------------------------
     def face_form_unit(self, u, v):
         """b_F^{gamma=1}(u, v) for every face side: array (Nc, 6) in the order
@@ -402,15 +433,17 @@ class SIPG:
 # Conjugate gradients (Section 2.4, Algorithm PCG, with M = I).
 # ----------------------------------------------------------------------------
 
-def cg(apply, b, x0=None, rtol=1e-10, maxit=100000, max_restarts=5):
-    """Unpreconditioned CG following the PCG algorithm of Section 2.4 (M = I).
+def cg(apply, b, x0=None, rtol=1e-10, maxit=100000, max_restarts=5, minv=None):
+    """CG following the PCG algorithm of Section 2.4.
 
+    minv: None (M = I) or an array d with M^-1 r = d * r (a diagonal M).
     Stops when the recursively updated ||r|| <= rtol ||b||; then recomputes
     b - A x and restarts from x while that true residual is still above rtol.
     Returns (x, total iterations, true relative residual, residual history).
     """
     b = np.asarray(b, float)
     x = np.zeros_like(b) if x0 is None else np.array(x0, float)
+    precond = (lambda r: r) if minv is None else (lambda r: np.asarray(minv) * r)
     nb = float(np.linalg.norm(b))
     if nb == 0.0:
         return np.zeros_like(b), 0, 0.0, []
@@ -418,8 +451,8 @@ def cg(apply, b, x0=None, rtol=1e-10, maxit=100000, max_restarts=5):
     hist = []
     for _ in range(max_restarts + 1):
         r = b - apply(x)
-        p = r.copy()                       # p_1 = M r_0
-        rho = float(r @ p)                 # rho_1 = <p_1, r_0>
+        p = precond(r)                     # p_1 = M r_0 (M^-1 in the usual notation)
+        rho = float(p @ r)                 # rho_1 = <p_1, r_0>
         while it < maxit:
             q = apply(p)                   # q_i = A p_i
             alpha = float(p @ q)           # alpha_i = <p_i, q_i>
@@ -428,7 +461,7 @@ def cg(apply, b, x0=None, rtol=1e-10, maxit=100000, max_restarts=5):
             x = x + (rho / alpha) * p
             r = r - (rho / alpha) * q
             it += 1
-            z = r                          # z_{i+1} = M r_i
+            z = precond(r)                 # z_{i+1} = M r_i
             rnorm = float(np.linalg.norm(r))
             hist.append(rnorm / nb)
             if rnorm <= rtol * nb:

@@ -403,6 +403,49 @@ def test_cg_matches_direct_solve():
     assert hist[-1] <= 1e-12
 
 
+def test_pcg_with_diagonal_matches_direct_solve_in_fewer_iterations():
+    D = SIPG(3, 3)
+    K = inputs.lognormal_coefficient(3, 3, seed=43, corr_len=0.1 * 64 / 3)
+    A = D.assemble(K).toarray()
+    b = inputs.constant_load_vector(3, 3)
+    x0, it0, _, _ = cg(lambda z: A @ z, b, rtol=1e-11)
+    x1, it1, rel, _ = cg(lambda z: A @ z, b, rtol=1e-11, minv=1.0 / np.diag(A))
+    xd = np.linalg.solve(A, b)
+    assert rel <= 1e-11
+    assert np.abs(x1 - xd).max() <= 1e-11 * np.linalg.cond(A) * np.abs(xd).max()
+    assert it1 < it0
+
+
+@pytest.mark.parametrize("N,k,seed", [(1, 3, 1), (2, 2, 2), (3, 1, 3), (2, 4, 4)])
+def test_diagonal_equals_assembled_diagonal(N, k, seed):
+    """The oracle's diag(A) (one function on its own side of each face) equals
+    the diagonal of the CSR matrix assembled from the two-sided face blocks."""
+    D = SIPG(N, k)
+    K = inputs.lognormal_coefficient(N, k, seed=seed, corr_len=0.1 * 64 / N)
+    dref = D.assemble(K).diagonal()
+    d = D.diagonal(K)
+    assert np.abs(d - dref).max() <= 1e-13 * np.abs(dref).max()
+    cells = np.array([0, N ** 3 - 1, (N ** 3) // 2])
+    # same formula on a subset of cells (BLAS blocking may change the rounding)
+    assert np.abs(D.diagonal(K, cells=cells) - d.reshape(N ** 3, -1)[cells]).max() <= 1e-14 * np.abs(d).max()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8])
+def test_diagonal_one_cell_unit_coefficient_closed_form(k):
+    """One unit cube, K = 1, all six faces on the boundary.  Along each axis
+    the orthonormal Legendre L_t has int_0^1 (L_t')^2 = 2 (2t+1) t (t+1),
+    L_t(s)^2 = 2t+1 and L_t(s) dL_t/dn_out(s) = (2t+1) t (t+1) at both ends, so
+    a(phi, phi) = sum over t in (i, j, l) of 2 (2t+1) (sigma - t (t+1))."""
+    D = SIPG(1, k)
+    n = k + 1
+    d = D.diagonal(np.ones(n ** 3))
+    sigma = 2.0 * n * n
+    for m in range(n ** 3):
+        t = (m % n, (m // n) % n, m // (n * n))
+        exact = sum(2.0 * (2 * a + 1) * (sigma - a * (a + 1)) for a in t)
+        assert abs(d[m] - exact) <= 1e-12 * exact, (m, d[m], exact)
+
+
 def test_cg_zero_rhs_and_breakdown():
     x, it, rel, _ = cg(lambda z: z, np.zeros(5))
     assert it == 0 and np.all(x == 0)
