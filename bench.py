@@ -34,9 +34,10 @@ BATCH_LEVELS = [(128, 16, 2), (96, 24, 3), (32, 32, 4)]   # (samples, n_cells, d
 METRIC = "SIPG-DG apply GDOF/s (FP64)"
 NOMINAL_FP64_TFLOPS = 1.25   # GB300 FP64 rate: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
 # DRAM bytes (read + write) per DOF of one pass-2 launch (k_cell_lo<4,double>),
-# from an ncu capture of the 40^3 Q3 case, scaled by DOFs to the benchmark's
-# launch; None until captured for the current kernel.
-K_CELL_TRAFFIC_PER_DOF = None
+# from an ncu capture of the 40^3 Q3 case (508.5 MB read + 28.8 MB written for
+# 4,096,000 DOFs), scaled by DOFs to the benchmark's launch; set to None when
+# the kernel changes until it is captured again.
+K_CELL_TRAFFIC_PER_DOF = (508.5e6 + 28.8e6) / 4096000
 
 
 def flops_per_dof(n: int):
@@ -256,12 +257,17 @@ def run_cg(world):
     N, k = CG_WORKLOAD["n_cells"], CG_WORKLOAD["degree"]
     K = inputs.lognormal_coefficient(N, k, seed=CG_WORKLOAD["K_seed"])
     m = dg.Mesh(N, k)
-    m.set_coefficient(torch.from_numpy(K).cuda())
+    Kd = torch.from_numpy(K).cuda()
+    m.set_coefficient(Kd)
     b = torch.from_numpy(inputs.constant_load_vector(N, k)).cuda()
     out = {"workload": f"{N}^3 Q{k} SIPG-DG, lognormal K (seed 4), f = 1, "
                        f"{m.n_dofs} DOFs, to rel. residual {CG_WORKLOAD['rtol']:g} "
-                       "recomputed in FP64"}
-    for name, mode in (("mixed_ir", dg.DG_CG_MIXED_IR), ("fp64", dg.DG_CG_FP64)):
+                       "recomputed in FP64; Jacobi times include forming diag(A)"}
+    for name, mode in (("mixed_ir", dg.DG_CG_MIXED_IR), ("fp64", dg.DG_CG_FP64),
+                       ("mixed_ir_jacobi", dg.DG_CG_MIXED_IR | dg.DG_CG_PRECOND_JACOBI),
+                       ("fp64_jacobi", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_JACOBI)):
+        if mode & dg.DG_CG_PRECOND_JACOBI:
+            m.set_coefficient(Kd)  # drops the cached diagonal: the solve forms it
         x = torch.zeros_like(b)
         torch.cuda.synchronize()
         barrier(world)
@@ -272,6 +278,9 @@ def run_cg(world):
                      "rel_residual": st["rel_residual"], "status": st["status"]}
     if out["fp64"]["status"] == 0 and out["mixed_ir"]["status"] == 0:
         out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed_ir"]["seconds"]
+    if out["fp64_jacobi"]["status"] == 0 and out["mixed_ir_jacobi"]["status"] == 0:
+        out["speedup_mixed_vs_fp64_jacobi"] = (out["fp64_jacobi"]["seconds"]
+                                               / out["mixed_ir_jacobi"]["seconds"])
     m.close()
     return out
 
@@ -328,12 +337,12 @@ def _timed_sequential(meshes, bs, sizes, picked):
     return {"samples": len(picked), "seconds": t, "gdof_per_s": work / t / 1e9}
 
 
-def run_batched(world, rank, sequential_samples: int = 4, full: bool = False):
+def run_batched(world, rank, sequential_samples: int = 1, full: bool = False):
     """Batched lock-step CG (FP64, rtol 1e-8) on the 256-sample workload.
 
-    Always: the 128 small samples (16^3 Q2) in one batched solve against the
-    same samples one per dg_cg_solve call, and one-per-call rates of every
-    level.  With full = True also the whole 256-sample batch (several minutes).
+    Always: the 128 small samples (16^3 Q2) in one batched solve against 16 of
+    them solved one per dg_cg_solve call, and one-per-call rates of the larger
+    levels.  With full = True also the whole 256-sample batch (minutes).
     """
     out = {"workload": "256 lognormal-K samples: 128 x 16^3 Q2, 96 x 24^3 Q3, 32 x 32^3 Q4 "
                        "(230,162,432 DOFs), FP64 CG to 1e-8; seeds 1000 + sample"}
@@ -341,7 +350,7 @@ def run_batched(world, rank, sequential_samples: int = 4, full: bool = False):
     meshes, bs, xs, sizes = _batch_meshes(small)
     out["small_level_batched"] = _timed_batched(meshes, bs, xs, sizes, world)
     out["small_level_one_per_call"] = _timed_sequential(
-        meshes, bs, sizes, list(range(min(len(meshes), 4 * sequential_samples))))
+        meshes, bs, sizes, list(range(min(len(meshes), 16))))
     out["small_level_speedup"] = (out["small_level_batched"]["gdof_per_s"]
                                   / out["small_level_one_per_call"]["gdof_per_s"])
     for m in meshes:
@@ -374,7 +383,9 @@ def run_cg_probe(iters: int):
     m = dg.Mesh(N, k)
     m.set_coefficient(torch.from_numpy(inputs.lognormal_coefficient(N, k, seed=CG_WORKLOAD["K_seed"])).cuda())
     b = torch.from_numpy(inputs.constant_load_vector(N, k)).cuda()
-    for name, mode in (("mixed_ir", dg.DG_CG_MIXED_IR), ("fp64", dg.DG_CG_FP64)):
+    for name, mode in (("mixed_ir", dg.DG_CG_MIXED_IR), ("fp64", dg.DG_CG_FP64),
+                       ("mixed_ir_jacobi", dg.DG_CG_MIXED_IR | dg.DG_CG_PRECOND_JACOBI),
+                       ("fp64_jacobi", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_JACOBI)):
         x = torch.zeros_like(b)
         _, st = m.cg_solve(b, x, rtol=1e-12, maxit=iters, mode=mode, raise_on_error=False)
         print(json.dumps({"mode": name, "iterations": st["iterations"],
@@ -393,8 +404,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--batched", action="store_true",
                     help="also run the 256-sample batched CG workload")
-    ap.add_argument("--batched-sequential", type=int, default=4,
-                    help="samples per level re-solved one per call for the comparison")
+    ap.add_argument("--batched-sequential", type=int, default=1,
+                    help="samples of each larger level solved one per call for reference")
     ap.add_argument("--cg-probe", type=int, default=0, metavar="ITERS",
                     help="only run ITERS iterations of each CG mode on the CG workload "
                          "(for kernel profiles) and exit")

@@ -47,6 +47,7 @@ enum {
 
 enum { DG_FP64 = 0, DG_FP32 = 1 };            /* operator precision            */
 enum { DG_CG_FP64 = 0, DG_CG_MIXED_IR = 1, DG_CG_MIXED_IR_RESTART = 2 };  /* dg_cg_solve modes */
+enum { DG_CG_PRECOND_JACOBI = 256 };  /* OR into a mode: PCG with M = diag(A) */
 
 typedef struct dg_mesh dg_mesh;
 
@@ -97,8 +98,12 @@ int dg_apply(const dg_mesh* mesh, const void* x, void* y, int prec, void* stream
  * sequence of contractions; arguments as dg_apply. */
 int dg_apply_adjoint(const dg_mesh* mesh, const void* ybar, void* xbar, int prec, void* stream);
 
-/* Same as dg_apply but x and y are HOST buffers (pinned or pageable): copies x
- * to the device, applies, copies y back.  Blocks until y is written. */
+/* Same as dg_apply but x and y are HOST buffers (pinned or pageable).  The
+ * mesh is cut into at most 8 slabs of z-layers: x is copied in slab by slab on
+ * a copy stream, pass 1 of slab s and pass 2 of slab s-1 run on `stream` as
+ * soon as their inputs have arrived, and y is copied back slab by slab on a
+ * second copy stream, so that with pinned buffers both copies overlap the
+ * kernels.  Blocks until y is written.  Not recorded by dg_timing_enable. */
 int dg_apply_host(const dg_mesh* mesh, const void* x_host, void* y_host, int prec, void* stream);
 
 /* g[c*n^3 + q] = d(v^T A(K) u) / d log K_{c,q}  (FP64 device pointers, g
@@ -119,11 +124,24 @@ int dg_coeff_grad(const dg_mesh* mesh, const double* u, const double* v, double*
  * mode DG_CG_MIXED_IR_RESTART: classical iterative refinement: FP64 outer
  *   residual and update, each correction solved from zero by FP32 CG to a 10x
  *   residual reduction.
+ * mode | DG_CG_PRECOND_JACOBI: any of the above as PCG with M = diag(A)
+ *   (Section 2.4's PCG algorithm); the diagonal is formed on the first such
+ *   solve after dg_set_coefficient (one kernel, see dg_diagonal).
  * Stops when ||b - A x|| <= rtol ||b|| recomputed in FP64.  Blocking.
  * Returns NOT_CONVERGED at maxit (x holds the last iterate), BREAKDOWN on
  * <p, Ap> <= 0 or non-finite scalars.  st may be NULL. */
 int dg_cg_solve(const dg_mesh* mesh, const double* b, double* x, double rtol, int maxit,
                 int mode, dg_cg_stats* st, void* stream);
+
+/* d = diag(A(K)) (FP64 device pointer, n_dofs values in the layout of x,
+ * overwritten): the diagonal the Jacobi preconditioner uses (Section 2.4's
+ * PCG with M = diag(A)).  Entry (c, m) is a(phi_{c,m}, phi_{c,m}) of the
+ * bilinear form of Section 4.1: the volume term by sum factorisation with
+ * squared 1D tables, the face terms in closed form (orthonormal basis, exact
+ * Gauss rule on the face).  Cached until the next dg_set_coefficient.
+ * Blocking.  Errors: INVALID_ARG (NULL mesh or d, no coefficient), OOM, CUDA,
+ * BREAKDOWN (a diagonal entry <= 0 or non-finite). */
+int dg_diagonal(const dg_mesh* mesh, double* d, void* stream);
 
 /* Solve count independent systems A_s x_s = b_s (meshes may differ in size and
  * degree; FP64) with CG run in lock-step: every iteration of all unfinished
@@ -135,7 +153,7 @@ int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, const double* c
                         double* const* x, double rtol, int maxit, dg_cg_stats* st, void* stream);
 
 /* Kernel timing for measurement tools (no paper counterpart).  While enabled,
- * each dg_apply / dg_apply_adjoint / dg_apply_host on this mesh records CUDA
+ * each dg_apply / dg_apply_adjoint on this mesh records CUDA
  * events on its stream before pass 1 (traces), between the passes and after
  * pass 2 (cell kernel), for at most max_applies applications.  dg_timing_read
  * waits for those events, returns the number of recorded applications and the

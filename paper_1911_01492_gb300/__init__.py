@@ -26,6 +26,7 @@ DG_FP32 = 1
 DG_CG_FP64 = 0
 DG_CG_MIXED_IR = 1
 DG_CG_MIXED_IR_RESTART = 2
+DG_CG_PRECOND_JACOBI = 256
 
 ERROR_NAMES = {
     DG_ERR_INVALID_ARG: "DG_ERR_INVALID_ARG",
@@ -57,6 +58,7 @@ _SIGS = {
                                            ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                            ctypes.c_double, ctypes.c_int, _VP, _VP]),
     "dg_apply_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP]),
+    "dg_diagonal": (ctypes.c_int, [_VP, _VP, _VP]),
     "dg_timing_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "dg_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_double),
@@ -213,6 +215,15 @@ class Mesh:
                "dg_coeff_grad")
         return g
 
+    def diagonal(self, d=None, stream=None):
+        """diag(A(K)) as a CUDA float64 tensor (the Jacobi preconditioner's diagonal)."""
+        import torch
+        if d is None:
+            d = torch.empty(self.n_dofs, dtype=torch.float64, device="cuda")
+        _check(library().dg_diagonal(self._h, _ptr(d, _f64(), self.n_dofs, "d"),
+                                     _stream(stream)), "dg_diagonal")
+        return d
+
     # -- measurement -------------------------------------------------------------
     def timing_enable(self, max_applies: int):
         """Record CUDA events around both passes of the next max_applies applies."""
@@ -227,9 +238,16 @@ class Mesh:
 
     # -- solvers ---------------------------------------------------------------
     def cg_solve(self, b, x=None, rtol: float = 1e-10, maxit: int = 100000,
-                 mode: int = DG_CG_FP64, stream=None, raise_on_error: bool = True):
-        """Solve A x = b (blocking).  Returns (x, stats dict)."""
+                 mode: int = DG_CG_FP64, stream=None, raise_on_error: bool = True,
+                 precond: str | None = None):
+        """Solve A x = b (blocking).  precond: None or "jacobi" (PCG with
+        M = diag(A); same as OR-ing DG_CG_PRECOND_JACOBI into mode).
+        Returns (x, stats dict)."""
         import torch
+        if precond not in (None, "jacobi"):
+            raise ValueError(f"unknown preconditioner {precond!r}")
+        if precond == "jacobi":
+            mode |= DG_CG_PRECOND_JACOBI
         if x is None:
             x = torch.zeros_like(b)
         st = CGStats()

@@ -18,6 +18,16 @@ int dg_launch_trace_f64(const dg_mesh* m, const double* x, double* U, double* X,
   return DG_OK;
 }
 
+int dg_launch_pass_f64(const dg_mesh* m, int pass, const double* x, double* y, long long cbeg,
+                       long long cend, cudaStream_t s) {
+  cudaError_t e = dgk::dispatch_n<double, dgk::PassF>(m->n, m, pass, x, y, m->U64, m->X64,
+                                                      m->TR64, (const double*)m->kt64,
+                                                      (const double*)m->fw64, cbeg, cend, m->N,
+                                                      &m->tab64, s);
+  if (e != cudaSuccess) return dg_cuda_fail(e, "apply pass (fp64) launch");
+  return DG_OK;
+}
+
 int dg_prepare_apply_f64(int n) {
   cudaError_t e = dgk::dispatch_n<double, dgk::PrepareF>(n);
   if (e != cudaSuccess) return dg_cuda_fail(e, "apply (fp64) kernel attributes");

@@ -399,12 +399,13 @@ __device__ __forceinline__ void trace_cells(const T* __restrict__ x, T* __restri
 template <int N, typename T>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_trace(const T* __restrict__ x, T* __restrict__ U, T* __restrict__ Xm, T* __restrict__ TR,
-        long long ncells, const int* __restrict__ skip, const __grid_constant__ DGTab<T> tab) {
+        long long cbeg, long long cend, const int* __restrict__ skip,
+        const __grid_constant__ DGTab<T> tab) {
   constexpr int C = Cfg<N>::CPB;
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const long long c0 = (long long)blockIdx.x * C;
-  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
+  const long long c0 = cbeg + (long long)blockIdx.x * C;
+  const int nblk = (int)((cend - c0) < C ? (cend - c0) : C);
   trace_cells<N, T>(x, U, Xm, TR, c0, nblk, tab, reinterpret_cast<T*>(smem_raw));
 }
 
@@ -438,9 +439,25 @@ __device__ __forceinline__ void cell_core(const FS& fs, T* __restrict__ y, long 
   const int p = t2 % N, q = t2 / N;
   const bool active = lc < nblk;
   const long long c = c0 + lc;
-  const int cx = (int)(c % Nc);
-  const int cy = (int)((c / Nc) % Nc);
-  const int cz = (int)(c / ((long long)Nc * Nc));
+  // Cell coordinates: the block's first cell once (thread 0, one division),
+  // then step forward to this thread's cell; 64-bit division per thread would
+  // cost more instructions than the FP32 arithmetic of a line.
+  __shared__ int sbase[3];
+  if (threadIdx.x == 0) {
+    const unsigned cu = (unsigned)c0, n = (unsigned)Nc;
+    sbase[0] = (int)(cu % n);
+    sbase[1] = (int)((cu / n) % n);
+    sbase[2] = (int)(cu / n / n);
+  }
+  __syncthreads();
+  int cx = sbase[0] + lc, cy = sbase[1], cz = sbase[2];
+  while (cx >= Nc) {
+    cx -= Nc;
+    if (++cy == Nc) {
+      cy = 0;
+      ++cz;
+    }
+  }
   const long long sy = Nc, sz = (long long)Nc * Nc;
   const int o = lc * N3;
   const int pt = p + N * q;
@@ -608,13 +625,14 @@ __device__ __forceinline__ void cell_cells(const T* __restrict__ U, const T* __r
 template <int N, typename T>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_cell(const T* __restrict__ U, const T* __restrict__ Xm, const T* __restrict__ TR,
-       const T* __restrict__ kt, const T* __restrict__ FW, T* __restrict__ y, long long ncells,
-       int Nc, const int* __restrict__ skip, const __grid_constant__ DGTab<T> tab) {
+       const T* __restrict__ kt, const T* __restrict__ FW, T* __restrict__ y, long long cbeg,
+       long long cend, int Nc, const int* __restrict__ skip,
+       const __grid_constant__ DGTab<T> tab) {
   constexpr int C = Cfg<N>::CPB;
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const long long c0 = (long long)blockIdx.x * C;
-  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
+  const long long c0 = cbeg + (long long)blockIdx.x * C;
+  const int nblk = (int)((cend - c0) < C ? (cend - c0) : C);
   cell_cells<N, T>(U, Xm, TR, kt, FW, y, c0, nblk, Nc, tab, reinterpret_cast<T*>(smem_raw));
 }
 
@@ -623,13 +641,13 @@ template <int N, typename T>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_cell_lo(const T* __restrict__ U, const T* __restrict__ Xm, const T* __restrict__ TR,
           const T* __restrict__ lineop, const T* __restrict__ FW, T* __restrict__ y,
-          long long ncells, int Nc, const int* __restrict__ skip,
+          long long cbeg, long long cend, int Nc, const int* __restrict__ skip,
           const __grid_constant__ DGTab<T> tab) {
   constexpr int C = Cfg<N>::CPB;
   if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const long long c0 = (long long)blockIdx.x * C;
-  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
+  const long long c0 = cbeg + (long long)blockIdx.x * C;
+  const int nblk = (int)((cend - c0) < C ? (cend - c0) : C);
   cell_cells<N, T, true>(U, Xm, TR, nullptr, FW, y, c0, nblk, Nc, tab,
                          reinterpret_cast<T*>(smem_raw), lineop);
 }
@@ -710,14 +728,37 @@ cudaError_t launch_apply_n(const dg_mesh* m, const T* x, T* y, T* U, T* X, T* TR
   const unsigned blocks = (unsigned)((ncells + Cfg<N>::CPB - 1) / Cfg<N>::CPB);
   const size_t s1 = trace_smem<N, T>(), s2 = cell_smem<N, T>();
   dg_timing_mark(m, 0, s);
-  k_trace<N, T><<<blocks, Cfg<N>::THREADS, s1, s>>>(x, U, X, TR, ncells, skip, tab);
+  k_trace<N, T><<<blocks, Cfg<N>::THREADS, s1, s>>>(x, U, X, TR, 0, ncells, skip, tab);
   dg_timing_mark(m, 1, s);
   if (sizeof(T) == 8 && m != nullptr && m->lineop64 != nullptr)
     k_cell_lo<N, T><<<blocks, Cfg<N>::THREADS, s2, s>>>(U, X, TR, (const T*)m->lineop64, fw, y,
-                                                        ncells, Nc, skip, tab);
+                                                        0, ncells, Nc, skip, tab);
   else
-    k_cell<N, T><<<blocks, Cfg<N>::THREADS, s2, s>>>(U, X, TR, kt, fw, y, ncells, Nc, skip, tab);
+    k_cell<N, T><<<blocks, Cfg<N>::THREADS, s2, s>>>(U, X, TR, kt, fw, y, 0, ncells, Nc, skip,
+                                                     tab);
   dg_timing_mark(m, 2, s);
+  return cudaGetLastError();
+}
+
+// One pass over the cells [cbeg, cend) (pipelined host-buffer apply).
+// Pass 1 reads x and writes U, X, TR of those cells only; pass 2 reads the
+// traces of their face neighbours, so it may run on a range only after pass 1
+// has run on every neighbour of the range.
+template <int N, typename T>
+cudaError_t launch_pass_n(const dg_mesh* m, int pass, const T* x, T* y, T* U, T* X, T* TR,
+                          const T* kt, const T* fw, long long cbeg, long long cend, int Nc,
+                          const DGTab<T>& tab, cudaStream_t s) {
+  if (cend <= cbeg) return cudaSuccess;
+  const unsigned blocks = (unsigned)((cend - cbeg + Cfg<N>::CPB - 1) / Cfg<N>::CPB);
+  if (pass == 1)
+    k_trace<N, T><<<blocks, Cfg<N>::THREADS, trace_smem<N, T>(), s>>>(x, U, X, TR, cbeg, cend,
+                                                                       nullptr, tab);
+  else if (sizeof(T) == 8 && m->lineop64 != nullptr)
+    k_cell_lo<N, T><<<blocks, Cfg<N>::THREADS, cell_smem<N, T>(), s>>>(
+        U, X, TR, (const T*)m->lineop64, fw, y, cbeg, cend, Nc, nullptr, tab);
+  else
+    k_cell<N, T><<<blocks, Cfg<N>::THREADS, cell_smem<N, T>(), s>>>(U, X, TR, kt, fw, y, cbeg,
+                                                                     cend, Nc, nullptr, tab);
   return cudaGetLastError();
 }
 
@@ -725,8 +766,8 @@ template <int N, typename T>
 cudaError_t launch_trace_n(const T* x, T* U, T* X, T* TR, long long ncells, const DGTab<T>& tab,
                            cudaStream_t s) {
   const unsigned blocks = (unsigned)((ncells + Cfg<N>::CPB - 1) / Cfg<N>::CPB);
-  k_trace<N, T><<<blocks, Cfg<N>::THREADS, trace_smem<N, T>(), s>>>(x, U, X, TR, ncells, nullptr,
-                                                                     tab);
+  k_trace<N, T><<<blocks, Cfg<N>::THREADS, trace_smem<N, T>(), s>>>(x, U, X, TR, 0, ncells,
+                                                                     nullptr, tab);
   return cudaGetLastError();
 }
 
@@ -752,6 +793,16 @@ struct ApplyF {
                          const T* fw, long long ncells, int Nc, const int* skip,
                          const DGTab<T>* tab, cudaStream_t s) {
     return launch_apply_n<N, T>(m, x, y, U, X, TR, kt, fw, ncells, Nc, skip, *tab, s);
+  }
+};
+
+template <int N>
+struct PassF {
+  template <typename T>
+  static cudaError_t run(const dg_mesh* m, int pass, const T* x, T* y, T* U, T* X, T* TR,
+                         const T* kt, const T* fw, long long cbeg, long long cend, int Nc,
+                         const DGTab<T>* tab, cudaStream_t s) {
+    return launch_pass_n<N, T>(m, pass, x, y, U, X, TR, kt, fw, cbeg, cend, Nc, *tab, s);
   }
 };
 

@@ -1,7 +1,8 @@
-// Conjugate gradients on the device (Section 2.4, the PCG algorithm with M = I):
-//   q = A p,  alpha = rho / <p, q>,  x += alpha p,  r -= alpha q,
-//   rho' = <r, r>  (the convergence norm, merged into the update as in
-//   Section 2.4's merged reduction),  p = r + (rho'/rho) p.
+// Conjugate gradients on the device (Section 2.4, the PCG algorithm; M = I, or
+// M = diag(A) with DG_CG_PRECOND_JACOBI):
+//   q = A p,  alpha = rho / <p, q>,  x += alpha p,  r -= alpha q,  z = M^-1 r,
+//   rho' = <z, r> and the convergence norm <r, r> in the same pass (merged
+//   into the update as in Section 2.4's merged reduction),  p = z + (rho'/rho) p.
 // Scalars live on the device (DGCGState); every kernel checks `done` first, so
 // a CUDA graph of a fixed number of iterations can be replayed until the host
 // sees convergence without overshooting.  Reductions are deterministic: a fixed
@@ -145,6 +146,7 @@ __device__ double AccF::block_total() {
 template <int K, typename A>
 __device__ bool last_block_sums(A (&part)[K], double* partials, unsigned int* ticket,
                                 double (&tot)[K]) {
+  static_assert(K <= DG_RED_SUMS, "partials holds DG_RED_SUMS x DG_RED_BLOCKS doubles");
   __shared__ bool is_last;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -174,27 +176,31 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (n); \
        i += (long long)gridDim.x * blockDim.x)
 
-// r = b - q, p = r; rho = <r,r>, bnorm2 = <b,b>; tol2 = rtol^2 bnorm2.
+// r = b - q, p = z = M^-1 r (M = diag(A) when dinv is given, else I);
+// rho = <z, r>, rr = <r, r>, bnorm2 = <b, b>; tol2 = rtol^2 bnorm2.
 template <typename T>
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_init(const T* __restrict__ b, const T* __restrict__ q, T* __restrict__ r, T* __restrict__ p,
-       long long n, double rtol, double* partials, DGCGState* st) {
+       const T* __restrict__ dinv, long long n, double rtol, double* partials, DGCGState* st) {
   using A = typename AccOf<T>::type;
-  A ar[4], ab[4];
+  A ar[4], ab[4], az[4];
   grid_stride4(n, [&](long long i, int j) {
     const T ri = b[i] - q[i];
     r[i] = ri;
-    p[i] = ri;
+    const T zi = dinv ? dinv[i] * ri : ri;
+    p[i] = zi;
     ar[j].add_prod(ri, ri);
     ab[j].add_prod(b[i], b[i]);
+    az[j].add_prod(zi, ri);
   });
-  A acc[2] = {merge4(ar), merge4(ab)};
-  double tot[2];
-  if (last_block_sums<2>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
-    st->rho = tot[0];
+  A acc[3] = {merge4(ar), merge4(ab), merge4(az)};
+  double tot[3];
+  if (last_block_sums<3>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
+    st->rr = tot[0];
+    st->rho = tot[2];
     st->bnorm2 = tot[1];
     st->tol2 = rtol * rtol * tot[1];
-    st->breakdown = !(finite(tot[0]) && finite(tot[1]));
+    st->breakdown = !(finite(tot[0]) && finite(tot[1]) && finite(tot[2]));
     st->done = st->breakdown || tot[0] <= st->tol2 || st->iters >= st->maxit;
     st->ru_skip = 1;
   }
@@ -223,54 +229,64 @@ k_dot_pq(const T* __restrict__ p, const T* __restrict__ q, long long n, double* 
   }
 }
 
-// x += alpha p, r -= alpha q, rho' = <r, r>.
-// MIXED = false: convergence test on rho', beta, rho = rho'.
-// MIXED = true: rho' goes to rho_new for the direction update, and an FP64
-// refinement is requested (ru_skip = 0, sticky until the refinement runs) when
-// rho' has dropped below delta2 * rmax2 or below tol2, or at the iteration
+// x += alpha p, r -= alpha q; rr' = <r, r> (convergence norm), rho' = <z, r>
+// with z = M^-1 r (= rr' without M).
+// MIXED = false: convergence test on rr', beta = rho'/rho, rho = rho'.
+// MIXED = true: rho' goes to rho_new and beta is formed for the direction
+// update; an FP64 refinement is requested (ru_skip = 0, sticky until it runs)
+// when rr' has dropped below delta2 * rmax2 or below tol2, or at the iteration
 // cap; at the cap the FP32 iteration stops.
 template <typename T, bool MIXED>
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-            const T* __restrict__ q, long long n, double* partials, DGCGState* st) {
+            const T* __restrict__ q, const T* __restrict__ dinv, long long n, double* partials,
+            DGCGState* st) {
   if (st->done || (MIXED && st->iters >= st->maxit)) return;
   const T a = (T)st->alpha;
   using A = typename AccOf<T>::type;
-  A a4[4];
+  A a4[4], z4[4];
   grid_stride4(n, [&](long long i, int j) {
     x[i] = fma(a, p[i], x[i]);
     const T ri = fma(-a, q[i], r[i]);
     r[i] = ri;
     a4[j].add_prod(ri, ri);
+    if (dinv) z4[j].add_prod(dinv[i] * ri, ri);
   });
-  A acc[1] = {merge4(a4)};
-  double tot[1];
-  if (last_block_sums<1>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
+  A acc[2] = {merge4(a4), merge4(z4)};
+  double tot[2];
+  if (last_block_sums<2>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
     const double rr = tot[0];
+    const double zr = dinv ? tot[1] : rr;
     st->iters += 1;
-    if (!finite(rr)) {
+    if (!finite(rr) || !finite(zr)) {
       st->breakdown = 1;
       st->done = 1;
       st->ru_skip = 1;
     } else if (!MIXED) {
-      st->beta = rr / st->rho;
-      st->rho = rr;
+      st->beta = zr / st->rho;
+      st->rho = zr;
+      st->rr = rr;
       if (rr <= st->tol2 || st->iters >= st->maxit) st->done = 1;
     } else {
-      st->rho_new = rr;
+      st->rho_new = zr;
+      st->rr = rr;
+      st->beta = zr / st->rho;  // next direction update (k_dir32)
       if (rr <= st->delta2 * st->rmax2 || rr <= st->tol2 || st->iters >= st->maxit)
         st->ru_skip = 0;
     }
   }
 }
 
-// p = r + beta p
+// p = z + beta p, z = M^-1 r
 template <typename T>
 __global__ void __launch_bounds__(DG_RED_THREADS)
-k_update_p(T* __restrict__ p, const T* __restrict__ r, long long n, const DGCGState* st) {
+k_update_p(T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ dinv, long long n,
+           const DGCGState* st) {
   if (st->done) return;
   const T be = (T)st->beta;
-  grid_stride4(n, [&](long long i, int) { p[i] = fma(be, p[i], r[i]); });
+  grid_stride4(n, [&](long long i, int) {
+    p[i] = fma(be, p[i], dinv ? dinv[i] * r[i] : r[i]);
+  });
 }
 
 // refinement step 1 (mixed): x64 += d32, d32 = 0.
@@ -293,26 +309,31 @@ constexpr int kMaxStall = 30;
 // on stagnating refinements.
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_refine_r(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
-           float* __restrict__ r32, long long n, double* partials, DGCGState* st) {
+           float* __restrict__ r32, const double* __restrict__ dinv, long long n,
+           double* partials, DGCGState* st) {
   if (st->ru_skip) return;
-  AccD a4[4];
+  AccD a4[4], z4[4];
   grid_stride4(n, [&](long long i, int j) {
     const double ri = b[i] - q[i];
     r[i] = ri;
     r32[i] = (float)ri;
     a4[j].add_prod(ri, ri);
+    if (dinv) z4[j].add_prod(dinv[i] * ri, ri);
   });
-  AccD acc[1] = {merge4(a4)};
-  double tot[1];
-  if (last_block_sums<1>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
+  AccD acc[2] = {merge4(a4), merge4(z4)};
+  double tot[2];
+  if (last_block_sums<2>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
     const double rr = tot[0];
+    const double zr = dinv ? tot[1] : rr;
     st->n_refine += 1;
     st->restart = rr > 0.25 * st->rmax2;  // true residual fell by less than 2x
     st->stall = st->restart ? st->stall + 1 : 0;
-    st->rho_new = rr;
+    st->rho_new = zr;
+    st->rr = rr;
+    st->beta = st->restart ? 0.0 : zr / st->rho;  // direction update after replacement
     st->rmax2 = rr;
     st->ru_skip = 1;
-    if (!finite(rr)) {
+    if (!finite(rr) || !finite(zr)) {
       st->breakdown = 1;
       st->done = 1;
     } else if (rr <= st->tol2 || st->iters >= st->maxit || st->stall >= kMaxStall) {
@@ -364,15 +385,15 @@ double now_s() {
 
 // One iteration of plain CG on FP64 or FP32 vectors.
 template <typename T>
-int launch_iteration(dg_mesh* m, T* x, T* r, T* p, T* q, cudaStream_t s) {
+int launch_iteration(dg_mesh* m, T* x, T* r, T* p, T* q, const T* dinv, cudaStream_t s) {
   int rc = (sizeof(T) == 8)
                ? dg_launch_apply_f64(m, (const double*)p, (double*)q, &m->state->done, s)
                : dg_launch_apply_f32(m, (const float*)p, (float*)q, &m->state->done, s);
   if (rc) return rc;
   const long long n = m->ndofs;
   k_dot_pq<T><<<RED_LAUNCH>>>(p, q, n, m->partials, m->state);
-  k_update_xr<T, false><<<RED_LAUNCH>>>(x, r, p, q, n, m->partials, m->state);
-  k_update_p<T><<<RED_LAUNCH>>>(p, r, n, m->state);
+  k_update_xr<T, false><<<RED_LAUNCH>>>(x, r, p, q, dinv, n, m->partials, m->state);
+  k_update_p<T><<<RED_LAUNCH>>>(p, r, dinv, n, m->state);
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -381,23 +402,23 @@ int launch_iteration(dg_mesh* m, T* x, T* r, T* p, T* q, cudaStream_t s) {
 // (fused kernels of dg_mixed32.cu), then d += alpha p, r -= alpha q.  The FP64
 // refinement is not in the captured iteration: it runs between graph replays
 // when an iteration has requested it (refine_mixed).
-int launch_iteration_mixed(dg_mesh* m, cudaStream_t s) {
+int launch_iteration_mixed(dg_mesh* m, const float* dinv, cudaStream_t s) {
   const long long n = m->ndofs;
-  int rc = dg_launch_mixed32_dir_cell(m, s);
+  int rc = dg_launch_mixed32_dir_cell(m, dinv, s);
   if (rc) return rc;
-  k_update_xr<float, true><<<RED_LAUNCH>>>(m->d32, m->r32, m->p32, m->q32, n, m->partials,
+  k_update_xr<float, true><<<RED_LAUNCH>>>(m->d32, m->r32, m->p32, m->q32, dinv, n, m->partials,
                                            m->state);
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
 
 // FP64 refinement: x += d, r = b - A x (FP64), r32 = (float) r.
-int refine_mixed(dg_mesh* m, const double* b, double* x, cudaStream_t s) {
+int refine_mixed(dg_mesh* m, const double* b, double* x, const double* dinv, cudaStream_t s) {
   const long long n = m->ndofs;
   k_refine_x<<<RED_LAUNCH>>>(x, m->d32, n, m->state);
   int rc = dg_launch_apply_f64(m, x, m->q64, nullptr, s);
   if (rc) return rc;
-  k_refine_r<<<RED_LAUNCH>>>(b, m->q64, m->r64, m->r32, n, m->partials, m->state);
+  k_refine_r<<<RED_LAUNCH>>>(b, m->q64, m->r64, m->r32, dinv, n, m->partials, m->state);
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -468,7 +489,8 @@ int zero_solution(dg_mesh* m, double* x, dg_cg_stats* st, cudaStream_t s) {
 }
 
 int cg_fp64(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_cg_stats* st,
-            cudaStream_t s) {
+            bool jacobi, cudaStream_t s) {
+  const double* dinv = jacobi ? m->dinv64 : nullptr;
   const int max_restarts = 5;
   int iters = 0, restarts = 0;
   double res2 = 0, b2 = 0;
@@ -480,16 +502,16 @@ int cg_fp64(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_c
     if (rc) return rc;
     rc = dg_launch_apply_f64(m, x, m->q64, nullptr, s);
     if (rc) return rc;
-    k_init<double><<<RED_LAUNCH>>>(b, m->q64, m->r64, m->p64, m->ndofs, rtol, m->partials,
-                                   m->state);
+    k_init<double><<<RED_LAUNCH>>>(b, m->q64, m->r64, m->p64, dinv, m->ndofs, rtol,
+                                   m->partials, m->state);
     DG_CUDA(cudaGetLastError());
     rc = run_graph(m, s, chunk_for(m), [&] {
-      return launch_iteration<double>(m, x, m->r64, m->p64, m->q64, s);
+      return launch_iteration<double>(m, x, m->r64, m->p64, m->q64, dinv, s);
     });
     if (rc) return rc;
     const DGCGState hs = *m->state_host;
     iters = hs.iters;
-    if (st) st->rel_residual_rec = hs.bnorm2 > 0 ? std::sqrt(hs.rho / hs.bnorm2) : 0.0;
+    if (st) st->rel_residual_rec = hs.bnorm2 > 0 ? std::sqrt(hs.rr / hs.bnorm2) : 0.0;
     rc = true_residual(m, b, x, s, &res2, &b2);
     if (rc) return rc;
     const double rel = std::sqrt(res2 / b2);
@@ -512,7 +534,9 @@ int cg_fp64(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_c
 
 // FP32 CG recurrence with FP64 residual refinement (search direction kept).
 int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_cg_stats* st,
-             cudaStream_t s) {
+             bool jacobi, cudaStream_t s) {
+  const double* dinv = jacobi ? m->dinv64 : nullptr;
+  const float* dinv32 = jacobi ? m->dinv32 : nullptr;
   const double delta = 0.1;
   const long long n = m->ndofs;
   double res2 = 0, b2 = 0;
@@ -525,7 +549,7 @@ int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_
   // correction, so r32 = p32 = (float) r64.
   const unsigned vblocks = (unsigned)(m->sm_count * 8);
   k_scale_to_f32<<<vblocks, 256, 0, s>>>(m->r64, m->q32, m->d32, n, 1.0);
-  k_init<float><<<RED_LAUNCH>>>(m->q32, m->d32, m->r32, m->p32, n, rtol, m->partials,
+  k_init<float><<<RED_LAUNCH>>>(m->q32, m->d32, m->r32, m->p32, dinv32, n, rtol, m->partials,
                                 m->state);
   DG_CUDA(cudaGetLastError());
   // FP64 tolerance and reference norm from the FP64 residual
@@ -541,6 +565,7 @@ int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_
     h.ru_skip = 1;
     h.rho_new = h.rho;  // first direction update: p = r (restart)
     h.restart = 1;
+    h.beta = 0.0;
     *m->state_host = h;
     DG_CUDA(cudaMemcpyAsync(m->state, m->state_host, sizeof(DGCGState), cudaMemcpyHostToDevice,
                             s));
@@ -550,7 +575,8 @@ int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     DG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < chunk_for(m) && rc == DG_OK; ++i) rc = launch_iteration_mixed(m, s);
+    for (int i = 0; i < chunk_for(m) && rc == DG_OK; ++i)
+      rc = launch_iteration_mixed(m, dinv32, s);
     cudaError_t ec = cudaStreamEndCapture(s, &graph);
     if (rc) {
       if (graph) cudaGraphDestroy(graph);
@@ -566,7 +592,7 @@ int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_
       if (ec != cudaSuccess) break;
       if (m->state_host->done) break;
       if (m->state_host->ru_skip == 0) {
-        rc = refine_mixed(m, b, x, s);
+        rc = refine_mixed(m, b, x, dinv, s);
         if (rc) break;
         continue;
       }
@@ -585,7 +611,7 @@ int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_
     st->iterations = hs.iters;
     st->outer_iterations = hs.n_refine;
     st->rel_residual = rel;
-    st->rel_residual_rec = std::sqrt(hs.rho_new / b2);
+    st->rel_residual_rec = std::sqrt(hs.rr / b2);
   }
   if (hs.breakdown)
     return dg_fail(DG_ERR_BREAKDOWN, "dg_cg_solve(mixed): breakdown at iteration %d", hs.iters);
@@ -599,7 +625,8 @@ int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_
 
 // Classical refinement: restart an FP32 CG from zero for every correction.
 int cg_mixed_restart(dg_mesh* m, const double* b, double* x, double rtol, int maxit,
-                     dg_cg_stats* st, cudaStream_t s) {
+                     dg_cg_stats* st, bool jacobi, cudaStream_t s) {
+  const float* dinv32 = jacobi ? m->dinv32 : nullptr;
   const int max_outer = 60;
   const double inner_tol = 0.1;  // relative reduction per refinement step
   const long long n = m->ndofs;
@@ -629,11 +656,11 @@ int cg_mixed_restart(dg_mesh* m, const double* b, double* x, double rtol, int ma
     DG_CUDA(cudaGetLastError());
     rc = set_state(m, maxit - inner_total, 0, s);
     if (rc) return rc;
-    k_init<float><<<RED_LAUNCH>>>(m->q32, m->d32, m->r32, m->p32, n, inner_tol, m->partials,
-                                  m->state);
+    k_init<float><<<RED_LAUNCH>>>(m->q32, m->d32, m->r32, m->p32, dinv32, n, inner_tol,
+                                  m->partials, m->state);
     DG_CUDA(cudaGetLastError());
     rc = run_graph(m, s, chunk_for(m), [&] {
-      return launch_iteration<float>(m, m->d32, m->r32, m->p32, m->q32, s);
+      return launch_iteration<float>(m, m->d32, m->r32, m->p32, m->q32, dinv32, s);
     });
     if (rc) return rc;
     const DGCGState hs = *m->state_host;
@@ -656,7 +683,9 @@ extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double
   if (!(rtol > 0.0) || !(rtol < 1.0))
     return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: rtol=%g outside (0, 1)", rtol);
   if (maxit < 1) return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: maxit=%d < 1", maxit);
-  if (mode != DG_CG_FP64 && mode != DG_CG_MIXED_IR && mode != DG_CG_MIXED_IR_RESTART)
+  const bool jacobi = (mode & DG_CG_PRECOND_JACOBI) != 0;
+  const int base = mode & ~DG_CG_PRECOND_JACOBI;
+  if (base != DG_CG_FP64 && base != DG_CG_MIXED_IR && base != DG_CG_MIXED_IR_RESTART)
     return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: unknown mode %d", mode);
   dg_mesh* m = const_cast<dg_mesh*>(mc);
   int rc = dg_ensure_solver_ws(m);
@@ -667,12 +696,15 @@ extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double
   DG_CUDA(cudaStreamWaitEvent(m->solve_stream, m->ev, 0));
   if (st) *st = dg_cg_stats{};
   cudaStream_t s = m->solve_stream;
-  if (mode == DG_CG_FP64)
-    rc = cg_fp64(m, b, x, rtol, maxit, st, s);
-  else if (mode == DG_CG_MIXED_IR)
-    rc = cg_mixed(m, b, x, rtol, maxit, st, s);
-  else
-    rc = cg_mixed_restart(m, b, x, rtol, maxit, st, s);
+  if (jacobi) rc = dg_ensure_diagonal(m, s);
+  if (rc == DG_OK) {
+    if (base == DG_CG_FP64)
+      rc = cg_fp64(m, b, x, rtol, maxit, st, jacobi, s);
+    else if (base == DG_CG_MIXED_IR)
+      rc = cg_mixed(m, b, x, rtol, maxit, st, jacobi, s);
+    else
+      rc = cg_mixed_restart(m, b, x, rtol, maxit, st, jacobi, s);
+  }
   cudaError_t e = cudaStreamSynchronize(s);
   if (rc == DG_OK && e != cudaSuccess) rc = dg_cuda_fail(e, "dg_cg_solve: synchronize");
   if (st) {

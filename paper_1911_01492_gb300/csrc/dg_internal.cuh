@@ -31,7 +31,8 @@ void dg_build_tables(int n, double sigma, DGTab<double>* t64, DGTab<float>* t32)
 
 // CG scalar state kept on the device (one per solve / per batched sample).
 struct DGCGState {
-  double rho;       // <r, r> of the current residual
+  double rho;       // <z, r> of the current residual (z = M^-1 r; = <r, r> without M)
+  double rr;        // <r, r> of the current residual (the convergence norm)
   double pq;        // <p, A p>
   double alpha;     // rho / pq
   double beta;      // rho_new / rho
@@ -52,6 +53,9 @@ struct DGCGState {
   int restart;      // 1: the next direction update restarts with p = r (mixed mode)
   int stall;        // consecutive refinements that fell short of a 2x reduction
 };
+
+// z-slabs of the pipelined host-buffer apply (at most)
+#define DG_HOST_SLABS 8
 
 struct dg_mesh {
   int N;            // cells per direction
@@ -76,6 +80,11 @@ struct dg_mesh {
   double* fw64;     // face-point weights W/2 and derivative weight  [c][6][2][n^2]
   double* lineop64; // per-line volume operators (FP64)  [c][3][n^2][n(n+1)/2]
   float* fw32;
+  // Jacobi preconditioner: 1 / diag(A), formed on the first preconditioned solve
+  double* diag64;
+  double* dinv64;
+  float* dinv32;
+  bool has_diag;
   double* kbar;     // Kbar_c                          [c]
   int* dflag;       // device-side error flag of the setup kernels
 
@@ -84,13 +93,16 @@ struct dg_mesh {
   float *U32, *X32, *TR32;
   // second set for the coefficient gradient (traces of v), lazily allocated
   double *U64b, *X64b, *TR64b;
-  // host staging for dg_apply_host
+  // host staging for dg_apply_host: device copies of x and y, a copy-in and a
+  // copy-out stream and per-slab events of the pipelined copy/compute
   void *hx_dev, *hy_dev;
+  cudaStream_t hstream[2];
+  cudaEvent_t hev[2 * DG_HOST_SLABS + 1];
 
   // solver workspaces, lazily allocated
   double *r64, *p64, *q64, *t64;
   float *d32, *r32, *p32, *q32;
-  double* partials;       // reduction partials (DG_RED_BLOCKS doubles x 2)
+  double* partials;       // reduction partials (DG_RED_BLOCKS doubles x DG_RED_SUMS)
   double* partials_cells; // one partial per cell block (fused FP32 mixed kernels)
   DGCGState* state;       // device CG state
   DGCGState* state_host;  // pinned mirror
@@ -111,6 +123,7 @@ void dg_timing_mark(const dg_mesh* m, int slot, cudaStream_t s);
 // Deterministic two-level reductions use this fixed grid.
 #define DG_RED_BLOCKS 1216  // 8 x 152 SMs
 #define DG_RED_THREADS 256
+#define DG_RED_SUMS 4     // most sums one reduction kernel may form (partials size)
 
 // error reporting (dg_mesh.cu)
 int dg_fail(int code, const char* fmt, ...);
@@ -122,6 +135,11 @@ int dg_cuda_fail(cudaError_t e, const char* what);
   } while (0)
 
 // launchers (dg_apply_f64.cu / dg_apply_f32.cu)
+// one pass (1: traces, 2: cell terms) over the cells [cbeg, cend)
+int dg_launch_pass_f64(const dg_mesh* m, int pass, const double* x, double* y, long long cbeg,
+                       long long cend, cudaStream_t s);
+int dg_launch_pass_f32(const dg_mesh* m, int pass, const float* x, float* y, long long cbeg,
+                       long long cend, cudaStream_t s);
 int dg_launch_apply_f64(const dg_mesh* m, const double* x, double* y, const int* skip,
                         cudaStream_t s);
 int dg_launch_apply_f32(const dg_mesh* m, const float* x, float* y, const int* skip,
@@ -131,13 +149,15 @@ int dg_launch_trace_f64(const dg_mesh* m, const double* x, double* U, double* X,
                         cudaStream_t s);
 int dg_launch_coeff_grad(const dg_mesh* m, double* g, cudaStream_t s);
 // fused FP32 kernels of the mixed CG iteration (dg_mixed32.cu)
-int dg_launch_mixed32_dir_cell(const dg_mesh* m, cudaStream_t s);
+int dg_launch_mixed32_dir_cell(const dg_mesh* m, const float* dinv, cudaStream_t s);
 long long dg_mixed32_blocks(int n, long long ncells);
 // one-time kernel attributes (dynamic shared memory) for points-per-direction n
 int dg_prepare_apply_f64(int n);
 int dg_prepare_apply_f32(int n);
 int dg_prepare_grad(int n);
 
+// 1 / diag(A) for the Jacobi preconditioner (dg_precond.cu); forms it if needed
+int dg_ensure_diagonal(dg_mesh* m, cudaStream_t s);
 // workspace helpers (dg_mesh.cu)
 int dg_ensure_solver_ws(dg_mesh* m);
 int dg_ensure_grad_ws(dg_mesh* m);

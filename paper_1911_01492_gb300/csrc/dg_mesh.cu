@@ -96,7 +96,7 @@ static cudaError_t dmalloc(P** p, size_t count) {
 }
 
 static void free_all(dg_mesh* m) {
-  void* ptrs[] = {m->kt64, m->kt32, m->gh64, m->gh32, m->dgam, m->kbar, m->dflag, m->fw64, m->fw32, m->lineop64,
+  void* ptrs[] = {m->kt64, m->kt32, m->gh64, m->gh32, m->dgam, m->kbar, m->dflag, m->fw64, m->fw32, m->lineop64, m->diag64, m->dinv64, m->dinv32,
                   m->U64,  m->X64,  m->TR64, m->U32,  m->X32,  m->TR32, m->U64b,
                   m->X64b, m->TR64b, m->hx_dev, m->hy_dev, m->r64, m->p64, m->q64,
                   m->t64,  m->d32,  m->r32, m->p32, m->q32, m->partials, m->state,
@@ -110,6 +110,10 @@ static void free_all(dg_mesh* m) {
   }
   if (m->solve_stream) cudaStreamDestroy(m->solve_stream);
   if (m->ev) cudaEventDestroy(m->ev);
+  for (cudaStream_t hs : m->hstream)
+    if (hs) cudaStreamDestroy(hs);
+  for (cudaEvent_t he : m->hev)
+    if (he) cudaEventDestroy(he);
 }
 
 extern "C" int dg_create_mesh(int n_cells, int degree, dg_mesh** out) {
@@ -210,7 +214,7 @@ int dg_ensure_solver_ws(dg_mesh* m) {
   DG_CUDA(dmalloc(&m->r32, nd));
   DG_CUDA(dmalloc(&m->p32, nd));
   DG_CUDA(dmalloc(&m->q32, nd));
-  DG_CUDA(dmalloc(&m->partials, 2 * DG_RED_BLOCKS));
+  DG_CUDA(dmalloc(&m->partials, DG_RED_SUMS * DG_RED_BLOCKS));
   DG_CUDA(dmalloc(&m->partials_cells, (size_t)dg_mixed32_blocks(m->n, m->ncells)));
   DG_CUDA(cudaMallocHost((void**)&m->state_host, sizeof(DGCGState)));
   DG_CUDA(cudaStreamCreateWithFlags(&m->solve_stream, cudaStreamNonBlocking));
@@ -228,6 +232,7 @@ extern "C" int dg_set_coefficient(dg_mesh* m, const double* K, void* stream) {
     return dg_fail(DG_ERR_INVALID_ARG, "dg_set_coefficient: NULL mesh or K");
   cudaStream_t s = (cudaStream_t)stream;
   m->has_coef = false;
+  m->has_diag = false;
   DG_CUDA(cudaMemsetAsync(m->dflag, 0, sizeof(int), s));
   {
     const long long threads = m->ncells * 32;
@@ -290,23 +295,82 @@ extern "C" int dg_apply_adjoint(const dg_mesh* m, const void* ybar, void* xbar, 
   return dg_launch_apply_f32(m, (const float*)ybar, (float*)xbar, nullptr, (cudaStream_t)stream);
 }
 
+// Host-buffer apply, pipelined over z-slabs of cells so that both copies
+// overlap the kernels.  Three streams: copy-in (H2D of x slab by slab), the
+// caller's stream (pass 1 of slab s, then pass 2 of slab s-1, whose upper
+// neighbours are the first layer of slab s), copy-out (D2H of y slab by slab
+// as pass 2 finishes it).  Every event is recorded before any wait on it is
+// enqueued.
+static int ensure_host_pipeline(dg_mesh* m) {
+  if (m->hx_dev == nullptr) {
+    DG_CUDA(cudaMalloc(&m->hx_dev, (size_t)m->ndofs * sizeof(double)));
+    DG_CUDA(cudaMalloc(&m->hy_dev, (size_t)m->ndofs * sizeof(double)));
+  }
+  for (cudaStream_t& hs : m->hstream)
+    if (hs == nullptr) DG_CUDA(cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking));
+  for (cudaEvent_t& he : m->hev)
+    if (he == nullptr) DG_CUDA(cudaEventCreateWithFlags(&he, cudaEventDisableTiming));
+  return DG_OK;
+}
+
 extern "C" int dg_apply_host(const dg_mesh* mc, const void* x_host, void* y_host, int prec,
                              void* stream) {
   int rc = check_apply_args(mc, x_host, y_host, prec, "dg_apply_host");
   if (rc) return rc;
   dg_mesh* m = const_cast<dg_mesh*>(mc);
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = (size_t)m->ndofs * (prec == DG_FP64 ? sizeof(double) : sizeof(float));
-  if (m->hx_dev == nullptr) {
-    DG_CUDA(cudaMalloc(&m->hx_dev, (size_t)m->ndofs * sizeof(double)));
-    DG_CUDA(cudaMalloc(&m->hy_dev, (size_t)m->ndofs * sizeof(double)));
-  }
-  DG_CUDA(cudaMemcpyAsync(m->hx_dev, x_host, bytes, cudaMemcpyHostToDevice, s));
-  rc = (prec == DG_FP64)
-           ? dg_launch_apply_f64(m, (const double*)m->hx_dev, (double*)m->hy_dev, nullptr, s)
-           : dg_launch_apply_f32(m, (const float*)m->hx_dev, (float*)m->hy_dev, nullptr, s);
+  rc = ensure_host_pipeline(m);
   if (rc) return rc;
-  DG_CUDA(cudaMemcpyAsync(y_host, m->hy_dev, bytes, cudaMemcpyDeviceToHost, s));
+  const size_t esz = prec == DG_FP64 ? sizeof(double) : sizeof(float);
+  const long long layer = (long long)m->N * m->N;  // cells per z-layer
+  const int nslab_max = m->N < DG_HOST_SLABS ? m->N : DG_HOST_SLABS;
+  const int lps = (m->N + nslab_max - 1) / nslab_max;  // layers per slab
+  const int nslab = (m->N + lps - 1) / lps;
+  const long long n3 = (long long)m->n * m->n * m->n;
+  auto cells = [&](int sl) { return (long long)(sl * lps < m->N ? sl * lps : m->N) * layer; };
+  cudaStream_t cin = m->hstream[0], cout = m->hstream[1];
+  cudaEvent_t* ev_in = m->hev;                   // H2D of slab s done
+  cudaEvent_t* ev_out = m->hev + DG_HOST_SLABS;  // pass 2 of slab s done
+  cudaEvent_t ev_start = m->hev[2 * DG_HOST_SLABS];
+  // order after the caller's earlier work on its stream
+  DG_CUDA(cudaEventRecord(ev_start, s));
+  DG_CUDA(cudaStreamWaitEvent(cin, ev_start, 0));
+  DG_CUDA(cudaStreamWaitEvent(cout, ev_start, 0));
+  char* xd = (char*)m->hx_dev;
+  char* yd = (char*)m->hy_dev;
+  for (int sl = 0; sl < nslab; ++sl) {
+    const size_t off = (size_t)(cells(sl) * n3) * esz;
+    const size_t bytes = (size_t)((cells(sl + 1) - cells(sl)) * n3) * esz;
+    DG_CUDA(cudaMemcpyAsync(xd + off, (const char*)x_host + off, bytes, cudaMemcpyHostToDevice,
+                            cin));
+    DG_CUDA(cudaEventRecord(ev_in[sl], cin));
+  }
+  auto pass = [&](int p, int sl) {
+    return prec == DG_FP64
+               ? dg_launch_pass_f64(m, p, (const double*)xd, (double*)yd, cells(sl),
+                                    cells(sl + 1), s)
+               : dg_launch_pass_f32(m, p, (const float*)xd, (float*)yd, cells(sl),
+                                    cells(sl + 1), s);
+  };
+  for (int sl = 0; sl <= nslab; ++sl) {
+    if (sl < nslab) {
+      DG_CUDA(cudaStreamWaitEvent(s, ev_in[sl], 0));
+      rc = pass(1, sl);
+      if (rc) return rc;
+    }
+    if (sl >= 1) {
+      rc = pass(2, sl - 1);
+      if (rc) return rc;
+      DG_CUDA(cudaEventRecord(ev_out[sl - 1], s));
+    }
+  }
+  for (int sl = 0; sl < nslab; ++sl) {
+    const size_t off = (size_t)(cells(sl) * n3) * esz;
+    const size_t bytes = (size_t)((cells(sl + 1) - cells(sl)) * n3) * esz;
+    DG_CUDA(cudaStreamWaitEvent(cout, ev_out[sl], 0));
+    DG_CUDA(cudaMemcpyAsync((char*)y_host + off, yd + off, bytes, cudaMemcpyDeviceToHost, cout));
+  }
+  DG_CUDA(cudaStreamSynchronize(cout));
   DG_CUDA(cudaStreamSynchronize(s));
   return DG_OK;
 }

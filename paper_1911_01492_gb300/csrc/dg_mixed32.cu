@@ -3,7 +3,8 @@
 // FP32 arithmetic is ~75x cheaper than FP64 on GB300, so the FP32 operator is
 // bound by memory traffic, not arithmetic.  These kernels trade arithmetic for
 // bytes and fold the CG vector work into the operator passes:
-//   k_dir32:  p = r + beta p (beta from the device CG state, 0 on a restart),
+//   k_dir32:  p = r + beta p (beta from the device CG state, 0 on a restart;
+//             formed once by k_update_xr / k_refine_r, not per thread),
 //             then pass 1 of p writing only the face traces (no U, X);
 //   k_cell32: reloads p, recomputes its nodal values, x-modal values and own
 //             face traces in shared memory, reads the neighbours' traces,
@@ -13,6 +14,11 @@
 //             finish sets alpha = rho / <p, q>.
 // Per DOF this moves ~35 B for the operator (instead of ~66 B in the generic
 // two-pass FP32 path) and removes the separate direction and dot kernels.
+// Measured at 48^3 Q4 (13.8 M DOFs): k_dir32 63 us + k_cell32 191 us per
+// iteration; the same fusion built on stored U and X (generic pass 2) took
+// 86 + 185 us, so recomputing in shared memory is kept.  Both are bound by
+// instruction issue (~8 warp instructions per DOF), not by FP32 arithmetic or
+// bytes.
 #include "dg_apply_impl.cuh"
 
 // rho = rho_new and clear the restart flag, after k_dir32 has read them.
@@ -33,18 +39,18 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& t) 
 template <int N>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_dir32(const float* __restrict__ r, float* __restrict__ p, float* __restrict__ TR,
-        long long ncells, const DGCGState* __restrict__ st,
+        const float* __restrict__ dinv, long long ncells, const DGCGState* __restrict__ st,
         const __grid_constant__ DGTab<float> tab) {
   constexpr int C = Cfg<N>::CPB, N3 = N * N * N;
   if (st->done || st->iters >= st->maxit) return;
-  const float beta = st->restart ? 0.0f : (float)(st->rho_new / st->rho);
+  const float beta = (float)st->beta;  // set once by the kernel that formed rho_new
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* s = reinterpret_cast<float*>(smem_raw);
   const long long c0 = (long long)blockIdx.x * C;
   const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
   for (int t = threadIdx.x; t < nblk * N3; t += blockDim.x) {
     const long long i = c0 * N3 + t;
-    const float v = fmaf(beta, p[i], r[i]);
+    const float v = fmaf(beta, p[i], dinv ? dinv[i] * r[i] : r[i]);  // p = M^-1 r + beta p
     p[i] = v;
     s[t] = v;
   }
@@ -129,15 +135,16 @@ k_cell32(const float* __restrict__ p, const float* __restrict__ TR, const float*
   (void)N2;
 }
 
+
+
 template <int N>
 struct Mixed32F {
   template <typename T>
-  static cudaError_t run(const dg_mesh* m, cudaStream_t s) {
+  static cudaError_t run(const dg_mesh* m, const float* dinv, cudaStream_t s) {
     constexpr int C = Cfg<N>::CPB, N3 = N * N * N;
     const unsigned blocks = (unsigned)((m->ncells + C - 1) / C);
-    k_dir32<N><<<blocks, Cfg<N>::THREADS, sizeof(float) * C * N3, s>>>(m->r32, m->p32, m->TR32,
-                                                                        m->ncells, m->state,
-                                                                        m->tab32);
+    k_dir32<N><<<blocks, Cfg<N>::THREADS, sizeof(float) * C * N3, s>>>(
+        m->r32, m->p32, m->TR32, dinv, m->ncells, m->state, m->tab32);
     k_commit_rho_after_dir<<<1, 1, 0, s>>>(m->state);
     const size_t sm2 = sizeof(float) * (4 * C * N3 + C * 12 * N * N);
     k_cell32<N><<<blocks, Cfg<N>::THREADS, sm2, s>>>(m->p32, m->TR32, m->kt32, m->gh32, m->q32,
@@ -149,8 +156,8 @@ struct Mixed32F {
 
 }  // namespace dgk
 
-int dg_launch_mixed32_dir_cell(const dg_mesh* m, cudaStream_t s) {
-  cudaError_t e = dgk::dispatch_n<float, dgk::Mixed32F>(m->n, m, s);
+int dg_launch_mixed32_dir_cell(const dg_mesh* m, const float* dinv, cudaStream_t s) {
+  cudaError_t e = dgk::dispatch_n<float, dgk::Mixed32F>(m->n, m, dinv, s);
   if (e != cudaSuccess) return dg_cuda_fail(e, "mixed-precision FP32 kernels launch");
   return DG_OK;
 }

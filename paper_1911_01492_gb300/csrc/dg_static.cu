@@ -108,9 +108,9 @@ struct StaticApplyF {
     using dgk::Cfg;
     const unsigned blocks = (unsigned)((ncells + Cfg<N>::CPB - 1) / Cfg<N>::CPB);
     dgk::k_trace<N, double><<<blocks, Cfg<N>::THREADS, dgk::trace_smem<N, double>(), s>>>(
-        x, U, X, TR, ncells, nullptr, *tab);
+        x, U, X, TR, 0, ncells, nullptr, *tab);
     dgk::k_cell<N, double><<<blocks, Cfg<N>::THREADS, dgk::cell_smem<N, double>(), s>>>(
-        U, X, TR, kt, fw, y, ncells, Nc, nullptr, *tab);
+        U, X, TR, kt, fw, y, 0, ncells, Nc, nullptr, *tab);
     return cudaGetLastError();
   }
 };

@@ -122,13 +122,30 @@ def test_coeff_grad_matches_oracle(dg, N, k):
     assert relmax(g, gref) <= TOL64
 
 
-def test_host_apply_matches_device_apply(dg):
+@pytest.mark.parametrize("N,k,dtype,pinned", [
+    (4, 3, "f64", True),    # 4 slabs of one z-layer
+    (9, 2, "f64", True),    # 5 slabs of 2 layers, the last one ragged (1 layer)
+    (1, 2, "f64", False),   # one cell, one slab, pageable buffers
+    (17, 1, "f32", True),   # 6 slabs of 3 layers, ragged, FP32
+    (5, 4, "f32", False),
+])
+def test_host_apply_matches_device_apply(dg, N, k, dtype, pinned):
+    """The slab-pipelined host-buffer apply gives the device apply bit for bit
+    (the same kernels on cell ranges), twice in a row on the same buffers."""
     import torch
-    m, K, x = make_problem(dg, 4, 3)
-    xh = torch.from_numpy(x).pin_memory()
-    yh = m.apply_host(xh)
+    m, K, x = make_problem(dg, N, k)
+    xt = torch.from_numpy(x)
+    if dtype == "f32":
+        xt = xt.float()
+    xh = xt.pin_memory() if pinned else xt.clone()
+    yh = torch.empty_like(xh)
+    if pinned:
+        yh = yh.pin_memory()
     yd = m.apply(xh.cuda()).cpu()
-    assert torch.equal(yh, yd)
+    for _ in range(2):
+        yh.fill_(float("nan"))
+        m.apply_host(xh, yh)
+        assert torch.equal(yh, yd)
 
 
 @pytest.mark.slow

@@ -151,3 +151,62 @@ def test_cg_reports_indefinite_coarse_mesh(dg):
     for mode in (0, 1):
         x, st = m.cg_solve(b, rtol=1e-10, maxit=3000, mode=mode, raise_on_error=False)
         assert st["status"] in (dg.DG_ERR_BREAKDOWN, dg.DG_ERR_NOT_CONVERGED), st
+
+
+@pytest.mark.parametrize("N,k", [(1, 2), (3, 2), (2, 3), (3, 4), (4, 1), (2, 8), (7, 3), (5, 5)])
+def test_diagonal_matches_oracle(dg, N, k):
+    """dg_diagonal against the oracle's a(phi, phi) by full quadrature: one
+    cell (boundary faces only), every block shape of the diagonal kernel
+    (8 cells per block at Q1 down to 1 at Q8) and ragged last blocks."""
+    import torch
+    D = SIPG(N, k)
+    K = small_mesh_field(N, k, 17)
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(K).cuda())
+    d = m.diagonal().cpu().numpy()
+    dref = D.diagonal(K)
+    assert np.abs(d - dref).max() <= 1e-12 * np.abs(dref).max()
+    # re-set coefficient: the cached diagonal must follow it
+    m.set_coefficient(torch.from_numpy(2.0 * K).cuda())
+    d2 = m.diagonal().cpu().numpy()
+    assert np.abs(d2 - 2.0 * dref).max() <= 2e-12 * np.abs(dref).max()
+
+
+@pytest.mark.slow
+def test_diagonal_full_size_sampled_cells(dg):
+    """48^3 Q4 lognormal K, the CG workload: sampled cells (corners, edges,
+    interior, random) against the oracle's diagonal of those cells."""
+    import torch
+    N, k = 48, 4
+    K = inputs.lognormal_coefficient(N, k, seed=4)
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(K).cuda())
+    d = m.diagonal().cpu().numpy().reshape(N ** 3, -1)
+    rng = np.random.default_rng(11)
+    cells = np.concatenate([[0, N - 1, N * N - 1, N ** 3 - 1, N ** 3 // 2 + N // 2],
+                            rng.choice(N ** 3, 59, replace=False)])
+    dref = SIPG(N, k).diagonal(K, cells=cells)
+    assert np.abs(d[cells] - dref).max() <= 1e-12 * np.abs(dref).max()
+    m.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_jacobi_pcg_residual_checked_by_oracle(dg, mode):
+    import torch
+    N, k = 4, 3
+    D = SIPG(N, k)
+    K = small_mesh_field(N, k, 5)
+    b = inputs.constant_load_vector(N, k)
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(K).cuda())
+    bd = torch.from_numpy(b).cuda()
+    x, st = m.cg_solve(bd, rtol=1e-10, mode=mode, precond="jacobi")
+    assert st["status"] == 0
+    assert oracle_rel_residual(D, K, b, x.cpu().numpy()) <= 1.05e-10
+    _, st0 = m.cg_solve(bd, rtol=1e-10, mode=mode)
+    assert st["iterations"] < st0["iterations"]
+    # the oracle's PCG with the same diagonal needs a similar number of iterations
+    if mode == 0:
+        _, it_ref, _, _ = __import__("oracle").cg(lambda z: D.apply(K, z), b, rtol=1e-10,
+                                                   minv=1.0 / D.assemble(K).diagonal())
+        assert abs(st["iterations"] - it_ref) <= max(3, it_ref // 10)
