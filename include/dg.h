@@ -99,11 +99,12 @@ int dg_apply(const dg_mesh* mesh, const void* x, void* y, int prec, void* stream
 int dg_apply_adjoint(const dg_mesh* mesh, const void* ybar, void* xbar, int prec, void* stream);
 
 /* Same as dg_apply but x and y are HOST buffers (pinned or pageable).  The
- * mesh is cut into at most 8 slabs of z-layers: x is copied in slab by slab on
- * a copy stream, pass 1 of slab s and pass 2 of slab s-1 run on `stream` as
- * soon as their inputs have arrived, and y is copied back slab by slab on a
- * second copy stream, so that with pinned buffers both copies overlap the
- * kernels.  Blocks until y is written.  Not recorded by dg_timing_enable. */
+ * mesh is cut into at most 16 slabs of z-layers: x is copied in slab by slab
+ * on a copy stream, pass 1 of each slab runs on an internal stream as soon as
+ * its x has arrived, pass 2 of slab s runs on `stream` once pass 1 has covered
+ * slab s+1, and y is copied back slab by slab on a second copy stream, so that
+ * with pinned buffers both copies overlap the kernels.  Blocks until y is
+ * written.  Not recorded by dg_timing_enable. */
 int dg_apply_host(const dg_mesh* mesh, const void* x_host, void* y_host, int prec, void* stream);
 
 /* g[c*n^3 + q] = d(v^T A(K) u) / d log K_{c,q}  (FP64 device pointers, g

@@ -55,7 +55,7 @@ struct DGCGState {
 };
 
 // z-slabs of the pipelined host-buffer apply (at most)
-#define DG_HOST_SLABS 8
+#define DG_HOST_SLABS 16
 
 struct dg_mesh {
   int N;            // cells per direction
@@ -93,11 +93,11 @@ struct dg_mesh {
   float *U32, *X32, *TR32;
   // second set for the coefficient gradient (traces of v), lazily allocated
   double *U64b, *X64b, *TR64b;
-  // host staging for dg_apply_host: device copies of x and y, a copy-in and a
-  // copy-out stream and per-slab events of the pipelined copy/compute
+  // host staging for dg_apply_host: device copies of x and y, copy-in,
+  // copy-out and pass-1 streams and per-slab events of the pipeline
   void *hx_dev, *hy_dev;
-  cudaStream_t hstream[2];
-  cudaEvent_t hev[2 * DG_HOST_SLABS + 1];
+  cudaStream_t hstream[3];
+  cudaEvent_t hev[3 * DG_HOST_SLABS + 1];
 
   // solver workspaces, lazily allocated
   double *r64, *p64, *q64, *t64;

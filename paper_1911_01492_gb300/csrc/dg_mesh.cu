@@ -296,11 +296,15 @@ extern "C" int dg_apply_adjoint(const dg_mesh* m, const void* ybar, void* xbar, 
 }
 
 // Host-buffer apply, pipelined over z-slabs of cells so that both copies
-// overlap the kernels.  Three streams: copy-in (H2D of x slab by slab), the
-// caller's stream (pass 1 of slab s, then pass 2 of slab s-1, whose upper
-// neighbours are the first layer of slab s), copy-out (D2H of y slab by slab
-// as pass 2 finishes it).  Every event is recorded before any wait on it is
-// enqueued.
+// overlap the kernels.  Four streams:
+//   copy-in   H2D of x, slab by slab;
+//   pass 1    pass 1 of slab s once its x has arrived (runs ahead of pass 2);
+//   caller's  pass 2 of slab s once pass 1 has covered slab s+1 (the upper
+//             neighbours of slab s are the first layer of slab s+1);
+//   copy-out  D2H of y of slab s once pass 2 has written it.
+// Pass 1 and pass 2 of different slabs may run at the same time, which fills
+// the last partial wave of each launch.  Every event is recorded before any
+// wait on it is enqueued.
 static int ensure_host_pipeline(dg_mesh* m) {
   if (m->hx_dev == nullptr) {
     DG_CUDA(cudaMalloc(&m->hx_dev, (size_t)m->ndofs * sizeof(double)));
@@ -328,45 +332,52 @@ extern "C" int dg_apply_host(const dg_mesh* mc, const void* x_host, void* y_host
   const int nslab = (m->N + lps - 1) / lps;
   const long long n3 = (long long)m->n * m->n * m->n;
   auto cells = [&](int sl) { return (long long)(sl * lps < m->N ? sl * lps : m->N) * layer; };
-  cudaStream_t cin = m->hstream[0], cout = m->hstream[1];
-  cudaEvent_t* ev_in = m->hev;                   // H2D of slab s done
-  cudaEvent_t* ev_out = m->hev + DG_HOST_SLABS;  // pass 2 of slab s done
-  cudaEvent_t ev_start = m->hev[2 * DG_HOST_SLABS];
+  cudaStream_t cin = m->hstream[0], cout = m->hstream[1], p1 = m->hstream[2];
+  cudaEvent_t* ev_in = m->hev;                       // H2D of slab s done
+  cudaEvent_t* ev_p1 = m->hev + DG_HOST_SLABS;       // pass 1 of slab s done
+  cudaEvent_t* ev_out = m->hev + 2 * DG_HOST_SLABS;  // pass 2 of slab s done
+  cudaEvent_t ev_start = m->hev[3 * DG_HOST_SLABS];
   // order after the caller's earlier work on its stream
   DG_CUDA(cudaEventRecord(ev_start, s));
   DG_CUDA(cudaStreamWaitEvent(cin, ev_start, 0));
+  DG_CUDA(cudaStreamWaitEvent(p1, ev_start, 0));
   DG_CUDA(cudaStreamWaitEvent(cout, ev_start, 0));
   char* xd = (char*)m->hx_dev;
   char* yd = (char*)m->hy_dev;
+  auto span = [&](int sl, size_t* off, size_t* bytes) {
+    *off = (size_t)(cells(sl) * n3) * esz;
+    *bytes = (size_t)((cells(sl + 1) - cells(sl)) * n3) * esz;
+  };
+  auto pass = [&](int p, int sl, cudaStream_t st) {
+    return prec == DG_FP64
+               ? dg_launch_pass_f64(m, p, (const double*)xd, (double*)yd, cells(sl),
+                                    cells(sl + 1), st)
+               : dg_launch_pass_f32(m, p, (const float*)xd, (float*)yd, cells(sl),
+                                    cells(sl + 1), st);
+  };
   for (int sl = 0; sl < nslab; ++sl) {
-    const size_t off = (size_t)(cells(sl) * n3) * esz;
-    const size_t bytes = (size_t)((cells(sl + 1) - cells(sl)) * n3) * esz;
+    size_t off, bytes;
+    span(sl, &off, &bytes);
     DG_CUDA(cudaMemcpyAsync(xd + off, (const char*)x_host + off, bytes, cudaMemcpyHostToDevice,
                             cin));
     DG_CUDA(cudaEventRecord(ev_in[sl], cin));
   }
-  auto pass = [&](int p, int sl) {
-    return prec == DG_FP64
-               ? dg_launch_pass_f64(m, p, (const double*)xd, (double*)yd, cells(sl),
-                                    cells(sl + 1), s)
-               : dg_launch_pass_f32(m, p, (const float*)xd, (float*)yd, cells(sl),
-                                    cells(sl + 1), s);
-  };
-  for (int sl = 0; sl <= nslab; ++sl) {
-    if (sl < nslab) {
-      DG_CUDA(cudaStreamWaitEvent(s, ev_in[sl], 0));
-      rc = pass(1, sl);
-      if (rc) return rc;
-    }
-    if (sl >= 1) {
-      rc = pass(2, sl - 1);
-      if (rc) return rc;
-      DG_CUDA(cudaEventRecord(ev_out[sl - 1], s));
-    }
+  for (int sl = 0; sl < nslab; ++sl) {
+    DG_CUDA(cudaStreamWaitEvent(p1, ev_in[sl], 0));
+    rc = pass(1, sl, p1);
+    if (rc) return rc;
+    DG_CUDA(cudaEventRecord(ev_p1[sl], p1));
   }
   for (int sl = 0; sl < nslab; ++sl) {
-    const size_t off = (size_t)(cells(sl) * n3) * esz;
-    const size_t bytes = (size_t)((cells(sl + 1) - cells(sl)) * n3) * esz;
+    // pass 1 of slabs sl - 1, sl, sl + 1 (in stream order on p1)
+    DG_CUDA(cudaStreamWaitEvent(s, ev_p1[sl + 1 < nslab ? sl + 1 : sl], 0));
+    rc = pass(2, sl, s);
+    if (rc) return rc;
+    DG_CUDA(cudaEventRecord(ev_out[sl], s));
+  }
+  for (int sl = 0; sl < nslab; ++sl) {
+    size_t off, bytes;
+    span(sl, &off, &bytes);
     DG_CUDA(cudaStreamWaitEvent(cout, ev_out[sl], 0));
     DG_CUDA(cudaMemcpyAsync((char*)y_host + off, yd + off, bytes, cudaMemcpyDeviceToHost, cout));
   }
