@@ -176,9 +176,12 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (n); \
        i += (long long)gridDim.x * blockDim.x)
 
-// r = b - q, p = z = M^-1 r (M = diag(A) when dinv is given, else I);
+// r = b - q, p = z = M^-1 r (PC: M = diag(A), dinv = 1/diag; else M = I);
 // rho = <z, r>, rr = <r, r>, bnorm2 = <b, b>; tol2 = rtol^2 bnorm2.
-template <typename T>
+// The preconditioner is a template parameter so that the M = I kernels carry
+// no per-element branch (a runtime test kept the compiler from batching the
+// loads of the unrolled grid-stride loop and cost ~40 % of the bandwidth).
+template <typename T, bool PC>
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_init(const T* __restrict__ b, const T* __restrict__ q, T* __restrict__ r, T* __restrict__ p,
        const T* __restrict__ dinv, long long n, double rtol, double* partials, DGCGState* st) {
@@ -187,7 +190,8 @@ k_init(const T* __restrict__ b, const T* __restrict__ q, T* __restrict__ r, T* _
   grid_stride4(n, [&](long long i, int j) {
     const T ri = b[i] - q[i];
     r[i] = ri;
-    const T zi = dinv ? dinv[i] * ri : ri;
+    T zi = ri;
+    if constexpr (PC) zi = dinv[i] * ri;
     p[i] = zi;
     ar[j].add_prod(ri, ri);
     ab[j].add_prod(b[i], b[i]);
@@ -206,15 +210,60 @@ k_init(const T* __restrict__ b, const T* __restrict__ q, T* __restrict__ r, T* _
   }
 }
 
+// 16-byte vectors for the vector kernels below (all operands 16-byte aligned).
+template <typename T> struct V16;
+template <> struct V16<float> {
+  using type = float4;
+  static constexpr int W = 4;
+  __device__ static void split(const float4& v, float (&a)[4]) {
+    a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+  }
+  __device__ static float4 join(const float (&a)[4]) { return make_float4(a[0], a[1], a[2], a[3]); }
+};
+template <> struct V16<double> {
+  using type = double2;
+  static constexpr int W = 2;
+  __device__ static void split(const double2& v, double (&a)[2]) { a[0] = v.x; a[1] = v.y; }
+  __device__ static double2 join(const double (&a)[2]) { return make_double2(a[0], a[1]); }
+};
+
 // pq = <p, q>, alpha = rho / pq.
-template <typename T>
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_dot_pq(const T* __restrict__ p, const T* __restrict__ q, long long n, double* partials,
          DGCGState* st) {
   if (st->done) return;
   using A = typename AccOf<T>::type;
   A a4[4];
-  grid_stride4(n, [&](long long i, int j) { a4[j].add_prod(p[i], q[i]); });
+  const long long S = (long long)gridDim.x * blockDim.x;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long tail = 0;
+  if constexpr (VEC) {
+    using VT = V16<T>;
+    using V = typename VT::type;
+    constexpr int W = VT::W;
+    const long long nv = n / W;
+    const V* pv = reinterpret_cast<const V*>(p);
+    const V* qv = reinterpret_cast<const V*>(q);
+    for (long long iv = tid; iv < nv; iv += 2 * S) {
+      const bool two = iv + S < nv;
+      T ps[2][W], qs[2][W];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (u == 1 && !two) break;
+        VT::split(pv[iv + u * S], ps[u]);
+        VT::split(qv[iv + u * S], qs[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (u == 1 && !two) break;
+#pragma unroll
+        for (int c = 0; c < W; ++c) a4[(u * W + c) & 3].add_prod(ps[u][c], qs[u][c]);
+      }
+    }
+    tail = nv * W;
+  }
+  for (long long i = tail + tid; i < n; i += S) a4[0].add_prod(p[i], q[i]);
   A acc[1] = {merge4(a4)};
   double tot[1];
   if (last_block_sums<1>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
@@ -236,7 +285,7 @@ k_dot_pq(const T* __restrict__ p, const T* __restrict__ q, long long n, double* 
 // update; an FP64 refinement is requested (ru_skip = 0, sticky until it runs)
 // when rr' has dropped below delta2 * rmax2 or below tol2, or at the iteration
 // cap; at the cap the FP32 iteration stops.
-template <typename T, bool MIXED>
+template <typename T, bool MIXED, bool PC, bool VEC>
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
             const T* __restrict__ q, const T* __restrict__ dinv, long long n, double* partials,
@@ -245,18 +294,67 @@ k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
   const T a = (T)st->alpha;
   using A = typename AccOf<T>::type;
   A a4[4], z4[4];
-  grid_stride4(n, [&](long long i, int j) {
+  const long long S = (long long)gridDim.x * blockDim.x;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long tail = 0;  // first element left to the scalar loop
+  if constexpr (VEC) {
+    // U 16-byte vectors of every operand per step, all loaded before any
+    // store (U = 2 without M; 1 with M, which has five operands and two
+    // compensated sums and would otherwise need over 100 registers).
+    using VT = V16<T>;
+    using V = typename VT::type;
+    constexpr int W = VT::W, U = PC ? 1 : 2;
+    const long long nv = n / W;
+    V* xv = reinterpret_cast<V*>(x);
+    V* rv = reinterpret_cast<V*>(r);
+    const V* pv = reinterpret_cast<const V*>(p);
+    const V* qv = reinterpret_cast<const V*>(q);
+    const V* dv = reinterpret_cast<const V*>(dinv);
+    for (long long iv = tid; iv < nv; iv += U * S) {
+      const bool two = iv + S < nv;
+      T xs[U][W], rs[U][W], ps[U][W], qs[U][W], ds[U][W];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (u == 1 && !two) break;
+        const long long k = iv + u * S;
+        VT::split(xv[k], xs[u]);
+        VT::split(rv[k], rs[u]);
+        VT::split(pv[k], ps[u]);
+        VT::split(qv[k], qs[u]);
+        if constexpr (PC) VT::split(dv[k], ds[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (u == 1 && !two) break;
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+          const int j = (u * W + c) & 3;
+          xs[u][c] = fma(a, ps[u][c], xs[u][c]);
+          rs[u][c] = fma(-a, qs[u][c], rs[u][c]);
+          a4[j].add_prod(rs[u][c], rs[u][c]);
+          if constexpr (PC) z4[j].add_prod(ds[u][c] * rs[u][c], rs[u][c]);
+        }
+        xv[iv + u * S] = VT::join(xs[u]);
+        rv[iv + u * S] = VT::join(rs[u]);
+      }
+    }
+    tail = nv * W;
+  }
+  for (long long i = tail + tid; i < n; i += S) {
     x[i] = fma(a, p[i], x[i]);
     const T ri = fma(-a, q[i], r[i]);
     r[i] = ri;
-    a4[j].add_prod(ri, ri);
-    if (dinv) z4[j].add_prod(dinv[i] * ri, ri);
-  });
-  A acc[2] = {merge4(a4), merge4(z4)};
-  double tot[2];
-  if (last_block_sums<2>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
+    a4[0].add_prod(ri, ri);
+    if constexpr (PC) z4[0].add_prod(dinv[i] * ri, ri);
+  }
+  constexpr int K = PC ? 2 : 1;
+  A acc[K];
+  acc[0] = merge4(a4);
+  if constexpr (PC) acc[K - 1] = merge4(z4);
+  double tot[K];
+  if (last_block_sums<K>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
     const double rr = tot[0];
-    const double zr = dinv ? tot[1] : rr;
+    const double zr = tot[K - 1];  // = rr without M
     st->iters += 1;
     if (!finite(rr) || !finite(zr)) {
       st->breakdown = 1;
@@ -278,15 +376,52 @@ k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
 }
 
 // p = z + beta p, z = M^-1 r
-template <typename T>
+template <typename T, bool PC, bool VEC>
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_update_p(T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ dinv, long long n,
            const DGCGState* st) {
   if (st->done) return;
   const T be = (T)st->beta;
-  grid_stride4(n, [&](long long i, int) {
-    p[i] = fma(be, p[i], dinv ? dinv[i] * r[i] : r[i]);
-  });
+  const long long S = (long long)gridDim.x * blockDim.x;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long tail = 0;
+  if constexpr (VEC) {
+    using VT = V16<T>;
+    using V = typename VT::type;
+    constexpr int W = VT::W;
+    const long long nv = n / W;
+    V* pv = reinterpret_cast<V*>(p);
+    const V* rv = reinterpret_cast<const V*>(r);
+    const V* dv = reinterpret_cast<const V*>(dinv);
+    for (long long iv = tid; iv < nv; iv += 2 * S) {
+      const bool two = iv + S < nv;
+      T ps[2][W], rs[2][W], ds[2][W];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (u == 1 && !two) break;
+        VT::split(pv[iv + u * S], ps[u]);
+        VT::split(rv[iv + u * S], rs[u]);
+        if constexpr (PC) VT::split(dv[iv + u * S], ds[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (u == 1 && !two) break;
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+          T z = rs[u][c];
+          if constexpr (PC) z = ds[u][c] * z;
+          ps[u][c] = fma(be, ps[u][c], z);
+        }
+        pv[iv + u * S] = VT::join(ps[u]);
+      }
+    }
+    tail = nv * W;
+  }
+  for (long long i = tail + tid; i < n; i += S) {
+    T zi = r[i];
+    if constexpr (PC) zi = dinv[i] * zi;
+    p[i] = fma(be, p[i], zi);
+  }
 }
 
 // refinement step 1 (mixed): x64 += d32, d32 = 0.
@@ -307,6 +442,7 @@ constexpr int kMaxStall = 30;
 // refinement step 2 (mixed), after q = A64 x: r64 = b - q, r32 = (float) r64,
 // rho_new = rmax2 = ||r64||^2; converged when <= tol2; cap on iterations and
 // on stagnating refinements.
+template <bool PC>
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_refine_r(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
            float* __restrict__ r32, const double* __restrict__ dinv, long long n,
@@ -318,13 +454,16 @@ k_refine_r(const double* __restrict__ b, const double* __restrict__ q, double* _
     r[i] = ri;
     r32[i] = (float)ri;
     a4[j].add_prod(ri, ri);
-    if (dinv) z4[j].add_prod(dinv[i] * ri, ri);
+    if constexpr (PC) z4[j].add_prod(dinv[i] * ri, ri);
   });
-  AccD acc[2] = {merge4(a4), merge4(z4)};
-  double tot[2];
-  if (last_block_sums<2>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
+  constexpr int K = PC ? 2 : 1;
+  AccD acc[K];
+  acc[0] = merge4(a4);
+  if constexpr (PC) acc[K - 1] = merge4(z4);
+  double tot[K];
+  if (last_block_sums<K>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
     const double rr = tot[0];
-    const double zr = dinv ? tot[1] : rr;
+    const double zr = tot[K - 1];  // = rr without M
     st->n_refine += 1;
     st->restart = rr > 0.25 * st->rmax2;  // true residual fell by less than 2x
     st->stall = st->restart ? st->stall + 1 : 0;
@@ -383,6 +522,8 @@ double now_s() {
 
 #define RED_LAUNCH DG_RED_BLOCKS, DG_RED_THREADS, 0, s
 
+bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
 // One iteration of plain CG on FP64 or FP32 vectors.
 template <typename T>
 int launch_iteration(dg_mesh* m, T* x, T* r, T* p, T* q, const T* dinv, cudaStream_t s) {
@@ -391,9 +532,30 @@ int launch_iteration(dg_mesh* m, T* x, T* r, T* p, T* q, const T* dinv, cudaStre
                : dg_launch_apply_f32(m, (const float*)p, (float*)q, &m->state->done, s);
   if (rc) return rc;
   const long long n = m->ndofs;
-  k_dot_pq<T><<<RED_LAUNCH>>>(p, q, n, m->partials, m->state);
-  k_update_xr<T, false><<<RED_LAUNCH>>>(x, r, p, q, dinv, n, m->partials, m->state);
-  k_update_p<T><<<RED_LAUNCH>>>(p, r, dinv, n, m->state);
+  // 16-byte vector kernels when every operand allows it (x is the caller's)
+  const bool vec = aligned16(x) && aligned16(r) && aligned16(p) && aligned16(q) &&
+                   aligned16(dinv);
+  if (vec)
+    k_dot_pq<T, true><<<RED_LAUNCH>>>(p, q, n, m->partials, m->state);
+  else
+    k_dot_pq<T, false><<<RED_LAUNCH>>>(p, q, n, m->partials, m->state);
+  if (dinv && vec) {
+    k_update_xr<T, false, true, true><<<RED_LAUNCH>>>(x, r, p, q, dinv, n, m->partials,
+                                                      m->state);
+    k_update_p<T, true, true><<<RED_LAUNCH>>>(p, r, dinv, n, m->state);
+  } else if (dinv) {
+    k_update_xr<T, false, true, false><<<RED_LAUNCH>>>(x, r, p, q, dinv, n, m->partials,
+                                                       m->state);
+    k_update_p<T, true, false><<<RED_LAUNCH>>>(p, r, dinv, n, m->state);
+  } else if (vec) {
+    k_update_xr<T, false, false, true><<<RED_LAUNCH>>>(x, r, p, q, dinv, n, m->partials,
+                                                       m->state);
+    k_update_p<T, false, true><<<RED_LAUNCH>>>(p, r, dinv, n, m->state);
+  } else {
+    k_update_xr<T, false, false, false><<<RED_LAUNCH>>>(x, r, p, q, dinv, n, m->partials,
+                                                        m->state);
+    k_update_p<T, false, false><<<RED_LAUNCH>>>(p, r, dinv, n, m->state);
+  }
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -406,8 +568,13 @@ int launch_iteration_mixed(dg_mesh* m, const float* dinv, cudaStream_t s) {
   const long long n = m->ndofs;
   int rc = dg_launch_mixed32_dir_cell(m, dinv, s);
   if (rc) return rc;
-  k_update_xr<float, true><<<RED_LAUNCH>>>(m->d32, m->r32, m->p32, m->q32, dinv, n, m->partials,
-                                           m->state);
+  // all operands are the mesh's own allocations (256-byte aligned)
+  if (dinv)
+    k_update_xr<float, true, true, true><<<RED_LAUNCH>>>(m->d32, m->r32, m->p32, m->q32, dinv,
+                                                         n, m->partials, m->state);
+  else
+    k_update_xr<float, true, false, true><<<RED_LAUNCH>>>(m->d32, m->r32, m->p32, m->q32, dinv,
+                                                          n, m->partials, m->state);
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -418,7 +585,10 @@ int refine_mixed(dg_mesh* m, const double* b, double* x, const double* dinv, cud
   k_refine_x<<<RED_LAUNCH>>>(x, m->d32, n, m->state);
   int rc = dg_launch_apply_f64(m, x, m->q64, nullptr, s);
   if (rc) return rc;
-  k_refine_r<<<RED_LAUNCH>>>(b, m->q64, m->r64, m->r32, dinv, n, m->partials, m->state);
+  if (dinv)
+    k_refine_r<true><<<RED_LAUNCH>>>(b, m->q64, m->r64, m->r32, dinv, n, m->partials, m->state);
+  else
+    k_refine_r<false><<<RED_LAUNCH>>>(b, m->q64, m->r64, m->r32, dinv, n, m->partials, m->state);
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }
@@ -502,8 +672,12 @@ int cg_fp64(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_c
     if (rc) return rc;
     rc = dg_launch_apply_f64(m, x, m->q64, nullptr, s);
     if (rc) return rc;
-    k_init<double><<<RED_LAUNCH>>>(b, m->q64, m->r64, m->p64, dinv, m->ndofs, rtol,
-                                   m->partials, m->state);
+    if (dinv)
+      k_init<double, true><<<RED_LAUNCH>>>(b, m->q64, m->r64, m->p64, dinv, m->ndofs, rtol,
+                                           m->partials, m->state);
+    else
+      k_init<double, false><<<RED_LAUNCH>>>(b, m->q64, m->r64, m->p64, dinv, m->ndofs, rtol,
+                                            m->partials, m->state);
     DG_CUDA(cudaGetLastError());
     rc = run_graph(m, s, chunk_for(m), [&] {
       return launch_iteration<double>(m, x, m->r64, m->p64, m->q64, dinv, s);
@@ -549,8 +723,12 @@ int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_
   // correction, so r32 = p32 = (float) r64.
   const unsigned vblocks = (unsigned)(m->sm_count * 8);
   k_scale_to_f32<<<vblocks, 256, 0, s>>>(m->r64, m->q32, m->d32, n, 1.0);
-  k_init<float><<<RED_LAUNCH>>>(m->q32, m->d32, m->r32, m->p32, dinv32, n, rtol, m->partials,
-                                m->state);
+  if (dinv32)
+    k_init<float, true><<<RED_LAUNCH>>>(m->q32, m->d32, m->r32, m->p32, dinv32, n, rtol,
+                                        m->partials, m->state);
+  else
+    k_init<float, false><<<RED_LAUNCH>>>(m->q32, m->d32, m->r32, m->p32, dinv32, n, rtol,
+                                         m->partials, m->state);
   DG_CUDA(cudaGetLastError());
   // FP64 tolerance and reference norm from the FP64 residual
   DG_CUDA(cudaMemcpyAsync(m->state_host, m->state, sizeof(DGCGState), cudaMemcpyDeviceToHost, s));
@@ -656,8 +834,12 @@ int cg_mixed_restart(dg_mesh* m, const double* b, double* x, double rtol, int ma
     DG_CUDA(cudaGetLastError());
     rc = set_state(m, maxit - inner_total, 0, s);
     if (rc) return rc;
-    k_init<float><<<RED_LAUNCH>>>(m->q32, m->d32, m->r32, m->p32, dinv32, n, inner_tol,
-                                  m->partials, m->state);
+    if (dinv32)
+      k_init<float, true><<<RED_LAUNCH>>>(m->q32, m->d32, m->r32, m->p32, dinv32, n, inner_tol,
+                                          m->partials, m->state);
+    else
+      k_init<float, false><<<RED_LAUNCH>>>(m->q32, m->d32, m->r32, m->p32, dinv32, n,
+                                           inner_tol, m->partials, m->state);
     DG_CUDA(cudaGetLastError());
     rc = run_graph(m, s, chunk_for(m), [&] {
       return launch_iteration<float>(m, m->d32, m->r32, m->p32, m->q32, dinv32, s);

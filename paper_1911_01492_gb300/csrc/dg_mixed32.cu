@@ -11,7 +11,8 @@
 //             forms the face weights from h*gamma on the fly, computes
 //             q = A p, and folds <p, q> (FP64-accurate: exact products summed
 //             in compensated float-float) into its epilogue; the last block to
-//             finish sets alpha = rho / <p, q>.
+//             finish commits rho = rho_new (formed with beta by the kernel
+//             that updated r) and sets alpha = rho / <p, q>.
 // Per DOF this moves ~35 B for the operator (instead of ~66 B in the generic
 // two-pass FP32 path) and removes the separate direction and dot kernels.
 // Measured at 48^3 Q4 (13.8 M DOFs): k_dir32 63 us + k_cell32 191 us per
@@ -21,13 +22,6 @@
 // bytes.
 #include "dg_apply_impl.cuh"
 
-// rho = rho_new and clear the restart flag, after k_dir32 has read them.
-__global__ void k_commit_rho_after_dir(DGCGState* st) {
-  if (st->done || st->iters >= st->maxit) return;
-  st->rho = st->rho_new;
-  st->restart = 0;
-}
-
 namespace dgk {
 
 __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& t) {
@@ -36,7 +30,7 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& t) 
   t = (a - (s - bb)) + (b - bb);
 }
 
-template <int N>
+template <int N, bool PC>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_dir32(const float* __restrict__ r, float* __restrict__ p, float* __restrict__ TR,
         const float* __restrict__ dinv, long long ncells, const DGCGState* __restrict__ st,
@@ -50,7 +44,9 @@ k_dir32(const float* __restrict__ r, float* __restrict__ p, float* __restrict__ 
   const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
   for (int t = threadIdx.x; t < nblk * N3; t += blockDim.x) {
     const long long i = c0 * N3 + t;
-    const float v = fmaf(beta, p[i], dinv ? dinv[i] * r[i] : r[i]);  // p = M^-1 r + beta p
+    float z = r[i];
+    if constexpr (PC) z = dinv[i] * z;  // z = M^-1 r
+    const float v = fmaf(beta, p[i], z);  // p = z + beta p
     p[i] = v;
     s[t] = v;
   }
@@ -128,7 +124,10 @@ k_cell32(const float* __restrict__ p, const float* __restrict__ TR, const float*
       st->done = 1;
       st->ru_skip = 1;
     } else {
-      st->alpha = st->rho / tot;
+      const double rho = st->rho_new;  // k_dir32 has used beta; commit the new rho
+      st->rho = rho;
+      st->restart = 0;
+      st->alpha = rho / tot;
     }
     st->ticket = 0u;
   }
@@ -143,9 +142,12 @@ struct Mixed32F {
   static cudaError_t run(const dg_mesh* m, const float* dinv, cudaStream_t s) {
     constexpr int C = Cfg<N>::CPB, N3 = N * N * N;
     const unsigned blocks = (unsigned)((m->ncells + C - 1) / C);
-    k_dir32<N><<<blocks, Cfg<N>::THREADS, sizeof(float) * C * N3, s>>>(
-        m->r32, m->p32, m->TR32, dinv, m->ncells, m->state, m->tab32);
-    k_commit_rho_after_dir<<<1, 1, 0, s>>>(m->state);
+    if (dinv)
+      k_dir32<N, true><<<blocks, Cfg<N>::THREADS, sizeof(float) * C * N3, s>>>(
+          m->r32, m->p32, m->TR32, dinv, m->ncells, m->state, m->tab32);
+    else
+      k_dir32<N, false><<<blocks, Cfg<N>::THREADS, sizeof(float) * C * N3, s>>>(
+          m->r32, m->p32, m->TR32, dinv, m->ncells, m->state, m->tab32);
     const size_t sm2 = sizeof(float) * (4 * C * N3 + C * 12 * N * N);
     k_cell32<N><<<blocks, Cfg<N>::THREADS, sm2, s>>>(m->p32, m->TR32, m->kt32, m->gh32, m->q32,
                                                      m->ncells, m->N, m->partials_cells,

@@ -210,3 +210,27 @@ def test_jacobi_pcg_residual_checked_by_oracle(dg, mode):
         _, it_ref, _, _ = __import__("oracle").cg(lambda z: D.apply(K, z), b, rtol=1e-10,
                                                    minv=1.0 / D.assemble(K).diagonal())
         assert abs(st["iterations"] - it_ref) <= max(3, it_ref // 10)
+
+
+@pytest.mark.parametrize("precond", [None, "jacobi"])
+def test_cg_fp64_unaligned_solution_vector(dg, precond):
+    """x as a view 8 bytes past a 16-byte boundary takes the scalar update
+    kernels; 5^3 Q2 has an odd DOF count, so the vector kernels' scalar tail
+    runs in the aligned case.  Both reach the same iterate."""
+    import torch
+    N, k = 5, 2
+    D = SIPG(N, k)
+    K = small_mesh_field(N, k, 6)
+    b = inputs.constant_load_vector(N, k)
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(K).cuda())
+    bd = torch.from_numpy(b).cuda()
+    xa, sta = m.cg_solve(bd, torch.zeros_like(bd), rtol=1e-10, precond=precond)
+    big = torch.zeros(m.n_dofs + 1, dtype=torch.float64, device="cuda")
+    xu = big[1:]
+    assert xu.data_ptr() % 16 == 8
+    _, stu = m.cg_solve(bd, xu, rtol=1e-10, precond=precond)
+    assert stu["status"] == 0 and sta["status"] == 0
+    assert oracle_rel_residual(D, K, b, xu.cpu().numpy()) <= 1.05e-10
+    assert abs(stu["iterations"] - sta["iterations"]) <= 2
+    assert float((xu - xa).norm() / xa.norm()) <= 1e-8
