@@ -233,9 +233,13 @@ template <typename T>
 struct FaceGlobal {
   const T* TR;
   const T* FW;
+  struct Pre {};  // nothing prefetched: the FP64 kernels hide load latency behind the FP64 pipe
+  template <int N>
+  __device__ __forceinline__ void prefetch(Pre&, long long, int, const bool (&)[6],
+                                           const long long (&)[6]) const {}
   template <int N, bool UPPER>
-  __device__ __forceinline__ void get(long long c, int lc, int f, bool in, long long cn, int fn,
-                                      int pt, T& cv, T& cdm) const {
+  __device__ __forceinline__ void get(const Pre&, long long c, int lc, int f, bool in,
+                                      long long cn, int fn, int pt, T& cv, T& cdm) const {
     (void)lc;
     face_point<N, UPPER>(TR, FW, c, f, in, cn, fn, pt, cv, cdm);
   }
@@ -244,21 +248,42 @@ struct FaceGlobal {
 // FaceLocal: own traces from shared memory (computed in the same kernel),
 // neighbour traces from the pass-1 buffer, weights from h*gamma per face
 // (W/2 = h gamma w_s w_t / 2; the derivative weight doubles on the boundary).
+// The global loads (neighbour traces, h*gamma) of all six faces are issued
+// together by prefetch() when the cell phase starts, so their latency overlaps
+// the volume work instead of stalling each direction's face step.
 template <typename T>
 struct FaceLocal {
   const T* TR;
   const T* str;
   const T* gh;
   const DGTab<T>* tab;
+  struct Pre {
+    T un[6], gn[6], g[6];
+  };
+  // in[f], cn[f]: whether face f is interior and its neighbour cell; the
+  // neighbour's face is f ^ 1 (x- <-> x+, ...).
+  template <int N>
+  __device__ __forceinline__ void prefetch(Pre& pre, long long c, int pt, const bool (&in)[6],
+                                           const long long (&cn)[6]) const {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      pre.un[f] = T(0);
+      pre.gn[f] = T(0);
+      if (in[f]) load_trace<N>(TR, cn[f], f ^ 1, pt, pre.un[f], pre.gn[f]);
+      pre.g[f] = gh[c * 6 + f];
+    }
+  }
   template <int N, bool UPPER>
-  __device__ __forceinline__ void get(long long c, int lc, int f, bool in, long long cn, int fn,
-                                      int pt, T& cv, T& cdm) const {
+  __device__ __forceinline__ void get(const Pre& pre, long long c, int lc, int f, bool in,
+                                      long long cn, int fn, int pt, T& cv, T& cdm) const {
     constexpr int N2 = N * N;
+    (void)c;
+    (void)cn;
+    (void)fn;
     const T* own = str + lc * (12 * N2) + (2 * f) * N2 + pt;
     const T uo = own[0], go = own[N2];
-    T un = T(0), gn = go;
-    if (in) load_trace<N>(TR, cn, fn, pt, un, gn);
-    const T wh = T(0.5) * gh[c * 6 + f] * tab->w[pt % N] * tab->w[pt / N];
+    const T un = pre.un[f], gn = in ? pre.gn[f] : go;
+    const T wh = T(0.5) * pre.g[f] * tab->w[pt % N] * tab->w[pt / N];
     flux<N, UPPER>(uo, go, un, gn, wh, in ? wh : wh + wh, cv, cdm);
   }
 };
@@ -461,6 +486,11 @@ __device__ __forceinline__ void cell_core(const FS& fs, T* __restrict__ y, long 
   const long long sy = Nc, sz = (long long)Nc * Nc;
   const int o = lc * N3;
   const int pt = p + N * q;
+  // face f = x-, x+, y-, y+, z-, z+: interior?  neighbour cell
+  const bool in6[6] = {cx > 0, cx < Nc - 1, cy > 0, cy < Nc - 1, cz > 0, cz < Nc - 1};
+  const long long cn6[6] = {c - 1, c + 1, c - sy, c + sy, c - sz, c + sz};
+  typename FS::Pre pre;
+  if (active) fs.template prefetch<N>(pre, c, pt, in6, cn6);
 
   // z-lines then y-lines: collocation derivative, Kt, transpose, face terms
 #pragma unroll
@@ -509,8 +539,8 @@ __device__ __forceinline__ void cell_core(const FS& fs, T* __restrict__ y, long 
       const bool inl = (dir == 0) ? (cz > 0) : (cy > 0);
       const long long st = (dir == 0) ? sz : sy;
       T cv1, cd1, cv0, cd0;
-      fs.template get<N, true>(c, lc, fu, inu, c + st, fl, pt, cv1, cd1);
-      fs.template get<N, false>(c, lc, fl, inl, c - st, fu, pt, cv0, cd0);
+      fs.template get<N, true>(pre, c, lc, fu, inu, c + st, fl, pt, cv1, cd1);
+      fs.template get<N, false>(pre, c, lc, fl, inl, c - st, fu, pt, cv0, cd0);
 #pragma unroll
       for (int e = 0; e < N; ++e) {
         T acc = fma(tab.l1[e], cv1, r[e]);
@@ -551,8 +581,8 @@ __device__ __forceinline__ void cell_core(const FS& fs, T* __restrict__ y, long 
       bt_bdt<N>(tab, rr, kg, R);
     }
     T cv1, cd1, cv0, cd0;
-    fs.template get<N, true>(c, lc, 1, cx < Nc - 1, c + 1, 0, pt, cv1, cd1);
-    fs.template get<N, false>(c, lc, 0, cx > 0, c - 1, 1, pt, cv0, cd0);
+    fs.template get<N, true>(pre, c, lc, 1, cx < Nc - 1, c + 1, 0, pt, cv1, cd1);
+    fs.template get<N, false>(pre, c, lc, 0, cx > 0, c - 1, 1, pt, cv0, cd0);
     // modal test functions: value a_i at 1, (-1)^i a_i at 0; derivative -d_i cd
     // at 1, -(-1)^(i+1) d_i cd at 0 (a_0 = 1, d_0 = 0)
     const T sp = cv1 + cv0, sm = cv1 - cv0;

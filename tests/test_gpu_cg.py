@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
 
-from oracle import SIPG
+from oracle import SIPG, cg
 from paper_1911_01492_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -49,6 +49,10 @@ def test_cg_fp64_manufactured_8cubed_q2(dg):
     assert np.linalg.norm(x - xd) <= 1e-10 * 2.3e3 * 10 * np.linalg.norm(xd)
     # the discrete solution approximates u to O(h^3)
     assert D.l2_error(x, u_exact) < 2e-3
+
+
+def relmax(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
 
 
 def small_mesh_field(N, k, seed):
@@ -234,3 +238,26 @@ def test_cg_fp64_unaligned_solution_vector(dg, precond):
     assert oracle_rel_residual(D, K, b, xu.cpu().numpy()) <= 1.05e-10
     assert abs(stu["iterations"] - sta["iterations"]) <= 2
     assert float((xu - xa).norm() / xa.norm()) <= 1e-8
+
+
+@pytest.mark.parametrize("N,k", [(3, 2), (4, 3), (3, 4), (2, 6), (2, 8)])
+@pytest.mark.parametrize("mode,precond", [(0, None), (0, "jacobi"), (1, None), (1, "jacobi")])
+def test_cg_first_iterates_match_oracle_recurrence(dg, N, k, mode, precond):
+    """Three CG iterations from x = 0 for a random right-hand side: x_3 is a
+    polynomial of degree two in A applied to b (M^-1 A with Jacobi), so a
+    wrong entry of the operator shows up element by element.  The mixed mode
+    runs the fused FP32 iteration kernels (tolerance 1e-4, from FP32
+    rounding); the FP64 mode the FP64 apply (1e-10)."""
+    import torch
+    D = SIPG(N, k)
+    K = small_mesh_field(N, k, 21)
+    b = inputs.uniform_vector(N, k, 22)
+    minv = 1.0 / D.diagonal(K) if precond else None
+    xref, _, _, _ = cg(lambda v: D.apply(K, v), b, rtol=1e-14, maxit=3, minv=minv)
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(K).cuda())
+    x, st = m.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-14, maxit=3, mode=mode,
+                       precond=precond, raise_on_error=False)
+    assert st["iterations"] == 3, st
+    tol = 1e-10 if mode == 0 else 1e-4
+    assert relmax(x.cpu().numpy(), xref) <= tol
