@@ -34,10 +34,10 @@ BATCH_LEVELS = [(128, 16, 2), (96, 24, 3), (32, 32, 4)]   # (samples, n_cells, d
 METRIC = "SIPG-DG apply GDOF/s (FP64)"
 NOMINAL_FP64_TFLOPS = 1.25   # GB300 FP64 rate: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
 # DRAM bytes (read + write) per DOF of one pass-2 launch (k_cell_lo<4,double>),
-# from an ncu capture of the 40^3 Q3 case (508.5 MB read + 28.8 MB written for
+# from an ncu capture of the 40^3 Q3 case (462.9 MB read + 27.4 MB written for
 # 4,096,000 DOFs), scaled by DOFs to the benchmark's launch; set to None when
 # the kernel changes until it is captured again.
-K_CELL_TRAFFIC_PER_DOF = (508.5e6 + 28.8e6) / 4096000
+K_CELL_TRAFFIC_PER_DOF = (462.859264e6 + 27.433984e6) / 4096000
 
 
 def flops_per_dof(n: int):

@@ -245,6 +245,42 @@ struct FaceGlobal {
   }
 };
 
+// FaceNbr: only the neighbour part of an interior face's flux; the own-side
+// part (and the whole boundary form) is inside the line operators.  With the
+// neighbour trace (un, gn) and W/2 = Wh (equal to the derivative weight
+// inside), the upper face gives cv = -Wh (2 sigma un + gn), cdm = -Wh un and
+// the lower face cv = Wh (gn - 2 sigma un), cdm = Wh un: three operations
+// and three loads per face point instead of five and six.
+template <typename T>
+struct FaceNbr {
+  const T* TR;
+  const T* FW;
+  struct Pre {};
+  template <int N>
+  __device__ __forceinline__ void prefetch(Pre&, long long, int, const bool (&)[6],
+                                           const long long (&)[6]) const {}
+  template <int N, bool UPPER>
+  __device__ __forceinline__ void get(const Pre&, long long c, int lc, int f, bool in,
+                                      long long cn, int fn, int pt, T& cv, T& cdm) const {
+    constexpr int N2 = N * N;
+    constexpr T S2 = T(4 * N * N);
+    (void)lc;
+    cv = T(0);
+    cdm = T(0);
+    if (!in) return;
+    T un, gn;
+    load_trace<N>(TR, cn, fn, pt, un, gn);
+    const T wh = FW[c * (12 * N2) + (2 * f) * N2 + pt];
+    if (UPPER) {
+      cv = -wh * fma(S2, un, gn);
+      cdm = -wh * un;
+    } else {
+      cv = wh * fma(-S2, un, gn);
+      cdm = wh * un;
+    }
+  }
+};
+
 // FaceLocal: own traces from shared memory (computed in the same kernel),
 // neighbour traces from the pass-1 buffer, weights from h*gamma per face
 // (W/2 = h gamma w_s w_t / 2; the derivative weight doubles on the boundary).
@@ -450,9 +486,11 @@ __host__ __device__ constexpr int packed(int i, int j) {
   return i <= j ? i * N - i * (i - 1) / 2 + (j - i) : j * N - j * (j - 1) / 2 + (i - j);
 }
 
-// LINEOP = true: the volume term of a line is one precomputed symmetric
-// operator per line (lineop: [c][x,y,z][line][packed n(n+1)/2], see
-// k_line_ops) instead of D^T diag(Kt) D (y, z) and L'^T diag(Kt) L' (x).
+// LINEOP = true: the volume term of a line and the own-side terms of its two
+// face points are one precomputed symmetric operator per line (lineop:
+// [c][x,y,z][line][packed n(n+1)/2], see k_line_ops) instead of
+// D^T diag(Kt) D (y, z) and L'^T diag(Kt) L' (x); the face policy then adds
+// only the neighbour part of interior faces (FaceNbr).
 template <int N, typename T, typename FS, bool LINEOP = false>
 __device__ __forceinline__ void cell_core(const FS& fs, T* __restrict__ y, long long c0,
                                           int nblk, int Nc, const DGTab<T>& tab, T* su, T* sx,
@@ -648,8 +686,14 @@ __device__ __forceinline__ void cell_cells(const T* __restrict__ U, const T* __r
     }
   }
   __syncthreads();
-  const FaceGlobal<T> fs{TR, FW};
-  cell_core<N, T, FaceGlobal<T>, LINEOP>(fs, y, c0, nblk, Nc, tab, su, sx, sr, sk, lineop);
+  if constexpr (LINEOP) {
+    // the line operators hold the volume term and the own-side face terms
+    const FaceNbr<T> fs{TR, FW};
+    cell_core<N, T, FaceNbr<T>, true>(fs, y, c0, nblk, Nc, tab, su, sx, sr, sk, lineop);
+  } else {
+    const FaceGlobal<T> fs{TR, FW};
+    cell_core<N, T, FaceGlobal<T>, false>(fs, y, c0, nblk, Nc, tab, su, sx, sr, sk, lineop);
+  }
 }
 
 template <int N, typename T>
@@ -682,14 +726,18 @@ k_cell_lo(const T* __restrict__ U, const T* __restrict__ Xm, const T* __restrict
                          reinterpret_cast<T*>(smem_raw), lineop);
 }
 
-// Line operators from Kt = h w K (one thread per cell, direction and line):
+// Line operators from Kt = h w K and h gamma (one thread per cell, direction
+// and line):
 //   x-line (b, e):  M[i][j] = sum_a L_i'(xi_a) Kt(a, b, e) L_j'(xi_a)   (acts on x-modes)
 //   y-line (a, e):  M[i][j] = sum_f D[f][i] Kt(a, f, e) D[f][j]         (acts on nodal values)
 //   z-line (a, b):  M[i][j] = sum_f D[f][i] Kt(a, b, f) D[f][j]
-// stored as lineop[((c*3 + dir)*n^2 + line)*n(n+1)/2 + packed(i, j)].
+// plus the own-side part of the flux at the line's two face points, so that
+// pass 2 only adds the neighbour part of interior faces (FaceNbr).
+// Stored as lineop[((c*3 + dir)*n^2 + line)*n(n+1)/2 + packed(i, j)].
 template <int N>
-__global__ void k_line_ops(const double* __restrict__ kt, double* __restrict__ lineop,
-                           long long ncells, const __grid_constant__ DGTab<double> tab) {
+__global__ void k_line_ops(const double* __restrict__ kt, const double* __restrict__ gh,
+                           double* __restrict__ lineop, long long ncells, int Nc,
+                           const __grid_constant__ DGTab<double> tab) {
   constexpr int N2 = N * N, N3 = N * N * N, NP = N * (N + 1) / 2;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ncells * 3 * N2) return;
@@ -719,6 +767,31 @@ __global__ void k_line_ops(const double* __restrict__ kt, double* __restrict__ l
         acc = fma(gi * k[f], gj, acc);
       }
       M[packed<N>(i, j)] = acc;
+    }
+  }
+  // Own-side face terms of the line's two faces (both trial and test function
+  // on this cell's side).  At the face point of this line, with v the test
+  // values and d the test derivatives (d/dxi) at the face (modal a, L' on
+  // x-lines; Lagrange l, l' on y- and z-lines), the flux adds
+  //   Wh (2 sigma v v^T -+ c (v d^T + d v^T)),  Wh = h gamma_F w_s w_t / 2,
+  // "-" on the upper face, "+" on the lower one, c = 1 inside and 2 on the
+  // boundary (where the whole one-sided form is own-side).
+  const long long crd = dir == 0 ? c % Nc : dir == 1 ? (c / Nc) % Nc : c / ((long long)Nc * Nc);
+  const double w2 = tab.w[p] * tab.w[q];
+  const double whl = 0.5 * gh[c * 6 + 2 * dir] * w2, whu = 0.5 * gh[c * 6 + 2 * dir + 1] * w2;
+  const double cl = crd > 0 ? 1.0 : 2.0, cu = crd < Nc - 1 ? 1.0 : 2.0;
+  constexpr double S2 = 4.0 * N * N;  // 2 sigma, sigma = 2 (k+1)^2
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const double v0i = dir == 0 ? tab.a0[i] : tab.l0[i], d0i = dir == 0 ? tab.d0[i] : tab.dl0[i];
+    const double v1i = dir == 0 ? tab.a1[i] : tab.l1[i], d1i = dir == 0 ? tab.d1[i] : tab.dl1[i];
+#pragma unroll
+    for (int j = i; j < N; ++j) {
+      const double v0j = dir == 0 ? tab.a0[j] : tab.l0[j], d0j = dir == 0 ? tab.d0[j] : tab.dl0[j];
+      const double v1j = dir == 0 ? tab.a1[j] : tab.l1[j], d1j = dir == 0 ? tab.d1[j] : tab.dl1[j];
+      const double fl = whl * (S2 * v0i * v0j + cl * (v0i * d0j + d0i * v0j));
+      const double fu = whu * (S2 * v1i * v1j - cu * (v1i * d1j + d1i * v1j));
+      M[packed<N>(i, j)] += fl + fu;
     }
   }
 }
@@ -868,10 +941,11 @@ namespace dgk {
 template <int N>
 struct LineOpsF {
   template <typename T>
-  static cudaError_t run(const double* kt, double* lineop, long long ncells,
-                         const DGTab<double>* tab, cudaStream_t s) {
+  static cudaError_t run(const double* kt, const double* gh, double* lineop, long long ncells,
+                         int Nc, const DGTab<double>* tab, cudaStream_t s) {
     const long long threads = ncells * 3 * N * N;
-    k_line_ops<N><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(kt, lineop, ncells, *tab);
+    k_line_ops<N><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(kt, gh, lineop, ncells, Nc,
+                                                                    *tab);
     return cudaGetLastError();
   }
 };

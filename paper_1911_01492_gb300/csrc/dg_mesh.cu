@@ -248,7 +248,8 @@ extern "C" int dg_set_coefficient(dg_mesh* m, const double* K, void* stream) {
     dgk::k_face_weights<float><<<blocks, 256, 0, s>>>(m->gh64, m->fw32, m->N, m->n, m->tab64);
     DG_CUDA(cudaGetLastError());
     cudaError_t e = dgk::dispatch_n<double, dgk::LineOpsF>(m->n, (const double*)m->kt64,
-                                                           m->lineop64, m->ncells,
+                                                           (const double*)m->gh64, m->lineop64,
+                                                           m->ncells, m->N,
                                                            (const DGTab<double>*)&m->tab64, s);
     if (e != cudaSuccess) return dg_cuda_fail(e, "dg_set_coefficient: line operators");
   }

@@ -86,13 +86,15 @@ def test_solve_gradient_matches_oracle_on_4cubed(dg, k):
 
 @pytest.mark.slow
 def test_solve_gradient_central_differences_32cubed_q3(dg):
-    """32^3 Q3 lognormal K: gradient by adjoint CG against central finite
-    differences along 20 seeded directions.  Solves go to a relative residual
-    of 1e-10 recomputed in FP64: 1e-12 is below what FP64 CG can attain on this
+    """32^3 Q3 lognormal K: gradient by adjoint CG against finite differences
+    along 20 seeded directions.  Solves go to a relative residual of 1e-10
+    recomputed in FP64: 1e-12 is below what FP64 CG can attain on this
     operator (its true residual floors near 5e-11, about u_64 times the
-    condition number).  At that accuracy the solution error is ~1e-7 relative,
-    so eps = 1e-3 (truncation error O(eps^2)) keeps the quotient's error near
-    5e-5; eps = 1e-4 would let the solve error reach ~5e-4."""
+    condition number).  The solve error then enters a difference quotient
+    divided by eps, so the quotient is the fourth-order central one,
+    (-L(2e) + 8 L(e) - 8 L(-e) + L(-2e)) / (12 e), at eps = 1e-2: truncation
+    O(eps^4) ~ 1e-8 and the solve error ~10x smaller than in a second-order
+    quotient at eps = 1e-3 (whose worst direction sat at ~1e-4)."""
     import torch
     from paper_1911_01492_gb300 import autograd as dga
     N, k = 32, 3
@@ -119,11 +121,12 @@ def test_solve_gradient_central_differences_32cubed_q3(dg):
     (0.5 * ((u - u_obs) ** 2).sum()).backward()
     g = lk.grad.clone()
     drng = np.random.default_rng(42)
-    eps = 1e-3
+    eps = 1e-2
     worst = 0.0
     for _ in range(20):
         d = torch.from_numpy(drng.standard_normal(m.n_dofs)).cuda()
-        fd = (loss(logK + eps * d) - loss(logK - eps * d)) / (2 * eps)
+        fd = (-loss(logK + 2 * eps * d) + 8 * loss(logK + eps * d) - 8 * loss(logK - eps * d)
+              + loss(logK - 2 * eps * d)) / (12 * eps)
         an = float(torch.dot(g, d))
         worst = max(worst, abs(fd - an) / abs(an))
     assert worst <= 1e-4, worst
