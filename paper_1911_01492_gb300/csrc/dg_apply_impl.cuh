@@ -294,19 +294,21 @@ struct FaceLocal {
   const T* gh;
   const DGTab<T>* tab;
   struct Pre {
-    T un[6], gn[6], g[6];
+    T un[6], gn[6], wh[6];  // neighbour trace; W/2 = h gamma w_s w_t / 2 per face
   };
   // in[f], cn[f]: whether face f is interior and its neighbour cell; the
   // neighbour's face is f ^ 1 (x- <-> x+, ...).
   template <int N>
   __device__ __forceinline__ void prefetch(Pre& pre, long long c, int pt, const bool (&in)[6],
                                            const long long (&cn)[6]) const {
+    // the line's face point has the same Gauss weights on all six faces
+    const T hw2 = T(0.5) * tab->w[pt % N] * tab->w[pt / N];
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       pre.un[f] = T(0);
       pre.gn[f] = T(0);
       if (in[f]) load_trace<N>(TR, cn[f], f ^ 1, pt, pre.un[f], pre.gn[f]);
-      pre.g[f] = gh[c * 6 + f];
+      pre.wh[f] = hw2 * gh[c * 6 + f];
     }
   }
   template <int N, bool UPPER>
@@ -319,7 +321,7 @@ struct FaceLocal {
     const T* own = str + lc * (12 * N2) + (2 * f) * N2 + pt;
     const T uo = own[0], go = own[N2];
     const T un = pre.un[f], gn = in ? pre.gn[f] : go;
-    const T wh = T(0.5) * pre.g[f] * tab->w[pt % N] * tab->w[pt / N];
+    const T wh = pre.wh[f];
     flux<N, UPPER>(uo, go, un, gn, wh, in ? wh : wh + wh, cv, cdm);
   }
 };

@@ -71,9 +71,18 @@ k_cell32(const float* __restrict__ p, const float* __restrict__ TR, const float*
   __shared__ bool is_last;
   const long long c0 = (long long)blockIdx.x * C;
   const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
-  for (int t = threadIdx.x; t < nblk * N3; t += blockDim.x) {
-    su[t] = p[c0 * N3 + t];
-    sk[t] = kt[c0 * N3 + t];
+  // NT = C n^2 threads cover the block's C n^3 values in N strides; each
+  // thread keeps its p values in registers for the <p, q> epilogue
+  float preg[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int t = threadIdx.x + k * NT;
+    preg[k] = 0.0f;
+    if (t < nblk * N3) {
+      preg[k] = p[c0 * N3 + t];
+      su[t] = preg[k];
+      sk[t] = kt[c0 * N3 + t];
+    }
   }
   __syncthreads();
   trace_core<N, float, 1>(nullptr, nullptr, nullptr, c0, nblk, tab, su, sx, str);
@@ -82,8 +91,11 @@ k_cell32(const float* __restrict__ p, const float* __restrict__ TR, const float*
   cell_core<N, float>(fs, q, c0, nblk, Nc, tab, su, sx, sr, sk);
   // <p, q> over the block's cells; q is still in sx after cell_core
   float hi = 0.0f, lo = 0.0f;
-  for (int t = threadIdx.x; t < nblk * N3; t += blockDim.x) {
-    const float a = p[c0 * N3 + t], b = sx[t];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int t = threadIdx.x + k * NT;
+    if (t >= nblk * N3) break;
+    const float a = preg[k], b = sx[t];
     const float pr = a * b;
     const float e = fmaf(a, b, -pr);
     float s1, t1;
