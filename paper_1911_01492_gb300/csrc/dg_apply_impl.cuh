@@ -757,19 +757,12 @@ __global__ void k_line_ops(const double* __restrict__ kt, const double* __restri
     k[f] = kt[c * N3 + qi];
   }
   double* M = lineop + (t)*NP;
+  // volume: M[i][j] = sum_f g_i(f) k_f g_j(f), with gk[i][f] = g_i(f) k_f formed once
+  double gk[N][N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
 #pragma unroll
-    for (int j = i; j < N; ++j) {
-      double acc = 0.0;
-#pragma unroll
-      for (int f = 0; f < N; ++f) {
-        const double gi = dir == 0 ? tab.Bd[f][i] : tab.D[f][i];
-        const double gj = dir == 0 ? tab.Bd[f][j] : tab.D[f][j];
-        acc = fma(gi * k[f], gj, acc);
-      }
-      M[packed<N>(i, j)] = acc;
-    }
+    for (int f = 0; f < N; ++f) gk[i][f] = (dir == 0 ? tab.Bd[f][i] : tab.D[f][i]) * k[f];
   }
   // Own-side face terms of the line's two faces (both trial and test function
   // on this cell's side).  At the face point of this line, with v the test
@@ -777,23 +770,39 @@ __global__ void k_line_ops(const double* __restrict__ kt, const double* __restri
   // x-lines; Lagrange l, l' on y- and z-lines), the flux adds
   //   Wh (2 sigma v v^T -+ c (v d^T + d v^T)),  Wh = h gamma_F w_s w_t / 2,
   // "-" on the upper face, "+" on the lower one, c = 1 inside and 2 on the
-  // boundary (where the whole one-sided form is own-side).
+  // boundary (where the whole one-sided form is own-side).  Entry (i, j) of
+  // each face term is v_i P_j + d_i Q_j with P = Wh (2 sigma v -+ c d) and
+  // Q = -+ Wh c v.
   const long long crd = dir == 0 ? c % Nc : dir == 1 ? (c / Nc) % Nc : c / ((long long)Nc * Nc);
   const double w2 = tab.w[p] * tab.w[q];
   const double whl = 0.5 * gh[c * 6 + 2 * dir] * w2, whu = 0.5 * gh[c * 6 + 2 * dir + 1] * w2;
-  const double cl = crd > 0 ? 1.0 : 2.0, cu = crd < Nc - 1 ? 1.0 : 2.0;
+  const double cl = (crd > 0 ? 1.0 : 2.0) * whl, cu = (crd < Nc - 1 ? 1.0 : 2.0) * whu;
   constexpr double S2 = 4.0 * N * N;  // 2 sigma, sigma = 2 (k+1)^2
+  double v0[N], d0[N], v1[N], d1[N], P0[N], Q0[N], P1[N], Q1[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    v0[j] = dir == 0 ? tab.a0[j] : tab.l0[j];
+    d0[j] = dir == 0 ? tab.d0[j] : tab.dl0[j];
+    v1[j] = dir == 0 ? tab.a1[j] : tab.l1[j];
+    d1[j] = dir == 0 ? tab.d1[j] : tab.dl1[j];
+    P0[j] = fma(whl * S2, v0[j], cl * d0[j]);
+    Q0[j] = cl * v0[j];
+    P1[j] = fma(whu * S2, v1[j], -cu * d1[j]);
+    Q1[j] = -cu * v1[j];
+  }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    const double v0i = dir == 0 ? tab.a0[i] : tab.l0[i], d0i = dir == 0 ? tab.d0[i] : tab.dl0[i];
-    const double v1i = dir == 0 ? tab.a1[i] : tab.l1[i], d1i = dir == 0 ? tab.d1[i] : tab.dl1[i];
 #pragma unroll
     for (int j = i; j < N; ++j) {
-      const double v0j = dir == 0 ? tab.a0[j] : tab.l0[j], d0j = dir == 0 ? tab.d0[j] : tab.dl0[j];
-      const double v1j = dir == 0 ? tab.a1[j] : tab.l1[j], d1j = dir == 0 ? tab.d1[j] : tab.dl1[j];
-      const double fl = whl * (S2 * v0i * v0j + cl * (v0i * d0j + d0i * v0j));
-      const double fu = whu * (S2 * v1i * v1j - cu * (v1i * d1j + d1i * v1j));
-      M[packed<N>(i, j)] += fl + fu;
+      double acc = 0.0;
+#pragma unroll
+      for (int f = 0; f < N; ++f)
+        acc = fma(gk[i][f], dir == 0 ? tab.Bd[f][j] : tab.D[f][j], acc);
+      acc = fma(v0[i], P0[j], acc);
+      acc = fma(d0[i], Q0[j], acc);
+      acc = fma(v1[i], P1[j], acc);
+      acc = fma(d1[i], Q1[j], acc);
+      M[packed<N>(i, j)] = acc;
     }
   }
 }
