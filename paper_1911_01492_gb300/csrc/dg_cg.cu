@@ -782,6 +782,10 @@ int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_
     DG_CUDA(ec);
   }
   const DGCGState hs = *m->state_host;
+  if (hs.timeout)
+    return dg_fail(DG_ERR_TIMEOUT,
+                   "dg_cg_solve(mixed): a bounded wait for a bulk copy in the FP32 direction "
+                   "kernel ran out at iteration %d", hs.iters);
   rc = true_residual(m, b, x, s, &res2, &b2);
   if (rc) return rc;
   const double rel = std::sqrt(res2 / b2);

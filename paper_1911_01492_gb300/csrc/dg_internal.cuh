@@ -52,6 +52,7 @@ struct DGCGState {
   int n_refine;     // FP64 residual refinements performed (mixed mode)
   int restart;      // 1: the next direction update restarts with p = r (mixed mode)
   int stall;        // consecutive refinements that fell short of a 2x reduction
+  int timeout;      // 1 if a kernel gave up a bounded wait (bulk-copy barrier)
 };
 
 // z-slabs of the pipelined host-buffer apply (at most)
@@ -108,6 +109,7 @@ struct dg_mesh {
   DGCGState* state_host;  // pinned mirror
   cudaStream_t solve_stream;
   cudaEvent_t ev;
+  int dir_bulk_grid[2];   // persistent grid of the bulk-copy direction kernel (M = I, Jacobi)
 
   // optional per-pass kernel timing (dg_timing_enable / dg_timing_read)
   cudaEvent_t* tev;       // 3 events per recorded application
@@ -151,6 +153,8 @@ int dg_launch_coeff_grad(const dg_mesh* m, double* g, cudaStream_t s);
 // fused FP32 kernels of the mixed CG iteration (dg_mixed32.cu)
 int dg_launch_mixed32_dir_cell(const dg_mesh* m, const float* dinv, cudaStream_t s);
 long long dg_mixed32_blocks(int n, long long ncells);
+// attributes and persistent grid of the mixed kernels (before any capture)
+int dg_prepare_mixed32(dg_mesh* m);
 // one-time kernel attributes (dynamic shared memory) for points-per-direction n
 int dg_prepare_apply_f64(int n);
 int dg_prepare_apply_f32(int n);

@@ -221,7 +221,7 @@ int dg_ensure_solver_ws(dg_mesh* m) {
   DG_CUDA(cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming));
   DG_CUDA(dmalloc(&m->state, 1));
   DG_CUDA(cudaMemset(m->state, 0, sizeof(DGCGState)));
-  return DG_OK;
+  return dg_prepare_mixed32(m);
 }
 
 // ---------------------------------------------------------------------------

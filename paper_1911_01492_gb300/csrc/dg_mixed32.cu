@@ -1,25 +1,29 @@
 // FP32 kernels of the mixed-precision CG iteration (DG_CG_MIXED_IR).
 //
 // FP32 arithmetic is ~75x cheaper than FP64 on GB300, so the FP32 operator is
-// bound by memory traffic, not arithmetic.  These kernels trade arithmetic for
-// bytes and fold the CG vector work into the operator passes:
-//   k_dir32:  p = r + beta p (beta from the device CG state, 0 on a restart;
-//             formed once by k_update_xr / k_refine_r, not per thread),
-//             then pass 1 of p writing only the face traces (no U, X);
+// bound by memory traffic and instruction issue, not arithmetic.  These
+// kernels trade arithmetic for bytes and fold the CG vector work into the
+// operator passes:
+//   k_dir32_bulk: p = z + beta p (z = M^-1 r; beta from the device CG state,
+//             0 on a restart, formed once by k_update_xr / k_refine_r), then
+//             pass 1 of p writing only the face traces (no U, X).  Its inputs
+//             are staged in shared memory by bulk copies (TMA engine),
+//             double-buffered over groups of cells in a persistent grid.
 //   k_cell32: reloads p, recomputes its nodal values, x-modal values and own
 //             face traces in shared memory, reads the neighbours' traces,
-//             forms the face weights from h*gamma on the fly, computes
-//             q = A p, and folds <p, q> (FP64-accurate: exact products summed
-//             in compensated float-float) into its epilogue; the last block to
-//             finish commits rho = rho_new (formed with beta by the kernel
-//             that updated r) and sets alpha = rho / <p, q>.
-// Per DOF this moves ~35 B for the operator (instead of ~66 B in the generic
+//             forms the face weights from h*gamma, computes q = A p, and folds
+//             <p, q> (FP64-accurate: exact products summed in compensated
+//             float-float) into its epilogue; the last block to finish commits
+//             rho = rho_new (formed with beta by the kernel that updated r) and
+//             sets alpha = rho / <p, q>.
+// Per DOF this moves ~38 B for the operator (instead of ~66 B in the generic
 // two-pass FP32 path) and removes the separate direction and dot kernels.
-// Measured at 48^3 Q4 (13.8 M DOFs): k_dir32 63 us + k_cell32 191 us per
-// iteration; the same fusion built on stored U and X (generic pass 2) took
-// 86 + 185 us, so recomputing in shared memory is kept.  Both are bound by
-// instruction issue (~8 warp instructions per DOF), not by FP32 arithmetic or
-// bytes.
+// Measured at 48^3 Q4 (13.8 M DOFs): k_dir32_bulk 58 us + k_cell32 168 us per
+// iteration.  The same fusion built on stored U and X (generic pass 2) was
+// slower, so recomputing in shared memory is kept.  k_cell32 is bound by
+// instruction issue and block barriers (~9 warp instructions per DOF).
+#include <cstdlib>
+
 #include "dg_apply_impl.cuh"
 
 namespace dgk {
@@ -30,28 +34,190 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& t) 
   t = (a - (s - bb)) + (b - bb);
 }
 
+// ---------------------------------------------------------------------------
+// Bulk copies (TMA engine, cp.async.bulk) completing on an mbarrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* ptr) {
+  return (unsigned)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// make the barrier initialisation visible to the async proxy
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this CTA's earlier generic-proxy shared-memory accesses before
+// later async-proxy (bulk copy) accesses
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  unsigned long long state;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+               : "=l"(state)
+               : "r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  (void)state;
+}
+// bytes (a multiple of 16) from global src to shared dst (both 16-byte
+// aligned); completion is signalled on bar as transaction bytes
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity to complete, at most `limit`
+// polls; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  long long limit) {
+  for (long long i = 0; i < limit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    __nanosleep(32);
+  }
+  return false;
+}
+
+// Direction kernel with the block's inputs staged by bulk copies,
+// double-buffered.  The cells are cut into groups of G = 4 CPB cells: G n^3
+// floats are a multiple of 16 bytes for every n, so each group of r, p (and
+// 1/diag) starts on a 16-byte boundary and is one bulk copy.  A block has one
+// thread per line of every cell of a group (G n^2 threads) and walks its
+// groups in a persistent grid: while it computes group g (p = z + beta p into
+// shared and global memory, then the face traces), one thread has already
+// started the copies of the block's next group into the other buffer.  With
+// CPB-cell blocks and two buffers each the residency fell to 5 blocks of 4
+// warps per SM and the kernel was no faster than plain loads; whole-group
+// blocks keep the SM full.  A ragged last group is loaded with plain loads.  Waits on the copy barriers
+// are bounded: on expiry the kernel sets st->timeout and st->done, waits
+// (bounded again) for its copies still in flight and returns.
+// stall_test != 0 (test hook) skips the first copy, so that the first wait
+// runs out with no copy in flight.
 template <int N, bool PC>
-__global__ void __launch_bounds__(Cfg<N>::THREADS)
-k_dir32(const float* __restrict__ r, float* __restrict__ p, float* __restrict__ TR,
-        const float* __restrict__ dinv, long long ncells, const DGCGState* __restrict__ st,
-        const __grid_constant__ DGTab<float> tab) {
-  constexpr int C = Cfg<N>::CPB, N3 = N * N * N;
+struct Dir32Bulk {
+  static constexpr int C = Cfg<N>::CPB, N3 = N * N * N, G = 4 * C;
+  static constexpr int NARR = PC ? 3 : 2;  // r, p (and 1/diag(A))
+  static constexpr int THREADS = G * N * N;  // one thread per line of every cell of a group
+  static constexpr unsigned GROUP_BYTES = (unsigned)(G * N3 * sizeof(float));
+  // 2 barriers, then NARR arrays x 2 buffers
+  static constexpr size_t SMEM = 16 + 2 * NARR * (size_t)GROUP_BYTES;
+  static_assert(GROUP_BYTES % 16 == 0, "bulk copies need 16-byte multiples");
+};
+
+template <int N, bool PC>
+__global__ void __launch_bounds__(Dir32Bulk<N, PC>::THREADS)
+k_dir32_bulk(const float* __restrict__ r, float* __restrict__ p, float* __restrict__ TR,
+             const float* __restrict__ dinv, long long ncells, DGCGState* st,
+             long long limit, int stall_test, const __grid_constant__ DGTab<float> tab) {
+  using B = Dir32Bulk<N, PC>;
+  constexpr int N3 = B::N3, G = B::G, NT = B::THREADS;
   if (st->done || st->iters >= st->maxit) return;
   const float beta = (float)st->beta;  // set once by the kernel that formed rho_new
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* s = reinterpret_cast<float*>(smem_raw);
-  const long long c0 = (long long)blockIdx.x * C;
-  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
-  for (int t = threadIdx.x; t < nblk * N3; t += blockDim.x) {
-    const long long i = c0 * N3 + t;
-    float z = r[i];
-    if constexpr (PC) z = dinv[i] * z;  // z = M^-1 r
-    const float v = fmaf(beta, p[i], z);  // p = z + beta p
-    p[i] = v;
-    s[t] = v;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);
+  float* buf = reinterpret_cast<float*>(smem_raw + 16);
+  float* const br[2] = {buf, buf + G * N3};
+  float* const bp[2] = {buf + 2 * G * N3, buf + 3 * G * N3};
+  float* const bd[2] = {buf + 4 * G * N3, buf + 5 * G * N3};  // PC only
+  const long long ngroups = (ncells + G - 1) / G;
+  const long long nfull = ncells / G;  // groups moved by bulk copies
+  auto issue = [&](long long g, int b) {  // thread 0 only
+    mbar_arrive_expect_tx(&bar[b], B::NARR * B::GROUP_BYTES);
+    bulk_g2s(br[b], r + g * G * N3, B::GROUP_BYTES, &bar[b]);
+    bulk_g2s(bp[b], p + g * G * N3, B::GROUP_BYTES, &bar[b]);
+    if constexpr (PC) bulk_g2s(bd[b], dinv + g * G * N3, B::GROUP_BYTES, &bar[b]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
   }
   __syncthreads();
-  trace_core<N, float, 2>(nullptr, nullptr, TR, c0, nblk, tab, s, nullptr, nullptr);
+  long long g = blockIdx.x;
+  bool issued[2] = {false, false};  // a copy into buffer b is in flight (thread 0's view)
+  if (threadIdx.x == 0 && g < nfull && !stall_test) {
+    issue(g, 0);
+    issued[0] = true;
+  }
+  bool failed = false;
+  int it = 0;
+  for (; g < ngroups; g += gridDim.x, ++it) {
+    const int b = it & 1;
+    const long long gn = g + gridDim.x;
+    if (threadIdx.x == 0 && gn < nfull) {
+      fence_proxy_async();  // the previous group's generic accesses to buffer b^1
+      issue(gn, b ^ 1);
+      issued[b ^ 1] = true;
+    }
+    const long long cg0 = g * G;
+    if (g < nfull) {
+      const bool ok = mbar_wait_bounded(&bar[b], (unsigned)((it >> 1) & 1), limit);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      if (threadIdx.x == 0) issued[b] = false;
+    } else {  // ragged last group
+      const int n = (int)(ncells - cg0) * N3;
+      for (int t = threadIdx.x; t < n; t += NT) {
+        br[b][t] = r[cg0 * N3 + t];
+        bp[b][t] = p[cg0 * N3 + t];
+        if constexpr (PC) bd[b][t] = dinv[cg0 * N3 + t];
+      }
+      __syncthreads();
+    }
+    {
+      const int nblk = (int)((ncells - cg0) < G ? (ncells - cg0) : G);
+      float* sp = bp[b];
+      const float* sr = br[b];
+      const float* sd = bd[b];
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int t = threadIdx.x + k * NT;
+        if (t < nblk * N3) {
+          float z = sr[t];
+          if constexpr (PC) z = sd[t] * z;  // z = M^-1 r
+          const float v = fmaf(beta, sp[t], z);  // p = z + beta p
+          sp[t] = v;
+          p[cg0 * N3 + t] = v;
+        }
+      }
+      __syncthreads();
+      trace_core<N, float, 2>(nullptr, nullptr, TR, cg0, nblk, tab, sp, nullptr, nullptr);
+      __syncthreads();
+    }
+  }
+  if (failed && threadIdx.x == 0) {
+    st->timeout = 1;
+    st->done = 1;
+    st->ru_skip = 1;
+    // copies of this block still in flight: wait for them, bounded again
+    for (int bb = 0; bb < 2; ++bb)
+      if (issued[bb]) mbar_wait_bounded(&bar[bb], (unsigned)(((it + (bb != (it & 1))) >> 1) & 1), limit);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_inval(&bar[0]);
+    mbar_inval(&bar[1]);
+  }
 }
 
 template <int N>
@@ -154,12 +320,21 @@ struct Mixed32F {
   static cudaError_t run(const dg_mesh* m, const float* dinv, cudaStream_t s) {
     constexpr int C = Cfg<N>::CPB, N3 = N * N * N;
     const unsigned blocks = (unsigned)((m->ncells + C - 1) / C);
-    if (dinv)
-      k_dir32<N, true><<<blocks, Cfg<N>::THREADS, sizeof(float) * C * N3, s>>>(
-          m->r32, m->p32, m->TR32, dinv, m->ncells, m->state, m->tab32);
+    // test hook (read when the iteration is captured): the direction kernel
+    // skips its first bulk copy and gives up its wait after a few polls
+    const char* env = getenv("DG_TEST_BULK_STALL");
+    const bool stall_now = env != nullptr && env[0] == '1';
+    const long long limit = stall_now ? (1LL << 12) : (1LL << 22);
+    const int pc = dinv != nullptr;
+    const unsigned gb = (unsigned)m->dir_bulk_grid[pc];
+    if (pc)
+      k_dir32_bulk<N, true><<<gb, Dir32Bulk<N, true>::THREADS, Dir32Bulk<N, true>::SMEM, s>>>(
+          m->r32, m->p32, m->TR32, dinv, m->ncells, m->state, limit, stall_now ? 1 : 0,
+          m->tab32);
     else
-      k_dir32<N, false><<<blocks, Cfg<N>::THREADS, sizeof(float) * C * N3, s>>>(
-          m->r32, m->p32, m->TR32, dinv, m->ncells, m->state, m->tab32);
+      k_dir32_bulk<N, false><<<gb, Dir32Bulk<N, false>::THREADS, Dir32Bulk<N, false>::SMEM, s>>>(
+          m->r32, m->p32, m->TR32, dinv, m->ncells, m->state, limit, stall_now ? 1 : 0,
+          m->tab32);
     const size_t sm2 = sizeof(float) * (4 * C * N3 + C * 12 * N * N);
     k_cell32<N><<<blocks, Cfg<N>::THREADS, sm2, s>>>(m->p32, m->TR32, m->kt32, m->gh32, m->q32,
                                                      m->ncells, m->N, m->partials_cells,
@@ -168,7 +343,38 @@ struct Mixed32F {
   }
 };
 
+// Kernel attributes and the persistent grid of the bulk-copy direction kernel
+// (host calls that must not run inside stream capture).
+template <int N>
+struct PrepareMixed32F {
+  template <typename T>
+  static cudaError_t run(dg_mesh* m) {
+    const long long ngroups = (m->ncells + Dir32Bulk<N, false>::G - 1) / Dir32Bulk<N, false>::G;
+    for (int pc = 0; pc < 2; ++pc) {
+      const void* fn = pc ? (const void*)k_dir32_bulk<N, true> : (const void*)k_dir32_bulk<N, false>;
+      const size_t smem = pc ? Dir32Bulk<N, true>::SMEM : Dir32Bulk<N, false>::SMEM;
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+      int occ = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, Dir32Bulk<N, false>::THREADS,
+                                                        smem);
+      if (e != cudaSuccess) return e;
+      if (occ < 1) return cudaErrorInvalidConfiguration;
+      const long long full = (long long)occ * m->sm_count;
+      m->dir_bulk_grid[pc] = (int)(ngroups < full ? ngroups : full);
+    }
+    return cudaSuccess;
+  }
+};
+
 }  // namespace dgk
+
+int dg_prepare_mixed32(dg_mesh* m) {
+  cudaError_t e = dgk::dispatch_n<float, dgk::PrepareMixed32F>(m->n, m);
+  if (e != cudaSuccess) return dg_cuda_fail(e, "mixed-precision FP32 kernel attributes");
+  return DG_OK;
+}
 
 int dg_launch_mixed32_dir_cell(const dg_mesh* m, const float* dinv, cudaStream_t s) {
   cudaError_t e = dgk::dispatch_n<float, dgk::Mixed32F>(m->n, m, dinv, s);

@@ -261,3 +261,25 @@ def test_cg_first_iterates_match_oracle_recurrence(dg, N, k, mode, precond):
     assert st["iterations"] == 3, st
     tol = 1e-10 if mode == 0 else 1e-4
     assert relmax(x.cpu().numpy(), xref) <= tol
+
+
+def test_bulk_copy_wait_timeout_is_reported_and_gpu_stays_usable(dg, monkeypatch):
+    """A test hook makes the mixed CG's direction kernel skip its first bulk
+    copy, so its bounded wait on the copy barrier runs out with no copy in
+    flight: the solve must return DG_ERR_TIMEOUT (no trap, no hang), and the
+    next solve on the same mesh must succeed."""
+    import torch
+    N, k = 4, 3
+    K = small_mesh_field(N, k, 5)
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(K).cuda())
+    b = torch.from_numpy(inputs.constant_load_vector(N, k)).cuda()
+    monkeypatch.setenv("DG_TEST_BULK_STALL", "1")
+    with pytest.raises(dg.DGError, match="TIMEOUT"):
+        m.cg_solve(b, rtol=1e-10, mode=dg.DG_CG_MIXED_IR)
+    monkeypatch.delenv("DG_TEST_BULK_STALL")
+    torch.cuda.synchronize()
+    x, st = m.cg_solve(b, rtol=1e-10, mode=dg.DG_CG_MIXED_IR)
+    assert st["status"] == 0
+    assert oracle_rel_residual(SIPG(N, k), K, inputs.constant_load_vector(N, k),
+                               x.cpu().numpy()) <= 1.05e-10
