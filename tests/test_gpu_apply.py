@@ -161,3 +161,19 @@ def test_full_size_64cubed_q3_sampled_cells(dg):
     cells = np.unique(np.concatenate([corners, rng.choice(N ** 3, 193, replace=False)]))
     yref = SIPG(N, k).apply(K, x, cells=cells)
     assert relmax(y[cells], yref) <= TOL64
+
+
+@pytest.mark.slow
+def test_full_size_64cubed_q3_fp32_sampled_cells(dg):
+    """The FP32 operator on the 64^3 Q3 lognormal workload (FP32 input), at
+    200 sampled cells against the FP64 oracle applied to the same FP32 input."""
+    import torch
+    N, k = 64, 3
+    m, K, x = make_problem(dg, N, k, kseed=2, xseed=3)
+    x32 = x.astype(np.float32)
+    y = m.apply(torch.from_numpy(x32).cuda()).cpu().numpy().astype(np.float64).reshape(N ** 3, -1)
+    rng = np.random.default_rng(1)
+    corners = [0, N - 1, N * (N - 1), N * N - 1, N ** 3 - 1, N ** 3 - N, N ** 3 - N * N]
+    cells = np.unique(np.concatenate([corners, rng.choice(N ** 3, 193, replace=False)]))
+    yref = SIPG(N, k).apply(K, x32.astype(np.float64), cells=cells)
+    assert relmax(y[cells], yref) <= TOL32

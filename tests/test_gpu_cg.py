@@ -283,3 +283,27 @@ def test_bulk_copy_wait_timeout_is_reported_and_gpu_stays_usable(dg, monkeypatch
     assert st["status"] == 0
     assert oracle_rel_residual(SIPG(N, k), K, inputs.constant_load_vector(N, k),
                                x.cpu().numpy()) <= 1.05e-10
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode,precond", [(0, None), (1, None), (1, "jacobi")])
+def test_cg_first_iterates_full_size_48cubed_q4(dg, mode, precond):
+    """The CG workload (48^3 Q4, lognormal K seed 4) in the benchmark's launch
+    configuration: three iterations from x = 0 for a random right-hand side,
+    every DOF against the oracle's recurrence.  The mixed mode runs the fused
+    FP32 kernels (bulk-copy direction kernel, persistent grid) at full size."""
+    import torch
+    N, k = 48, 4
+    K = inputs.lognormal_coefficient(N, k, seed=4)
+    b = inputs.uniform_vector(N, k, 23)
+    D = SIPG(N, k)
+    minv = 1.0 / D.diagonal(K) if precond else None
+    xref, _, _, _ = cg(lambda v: D.apply(K, v), b, rtol=1e-14, maxit=3, minv=minv)
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(K).cuda())
+    x, st = m.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-14, maxit=3, mode=mode,
+                       precond=precond, raise_on_error=False)
+    assert st["iterations"] == 3, st
+    tol = 1e-10 if mode == 0 else 1e-4
+    assert relmax(x.cpu().numpy(), xref) <= tol
+    m.close()
