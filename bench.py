@@ -304,7 +304,7 @@ def _batch_meshes(levels, seed0=1000):
     return meshes, bs, xs, sizes
 
 
-def _timed_batched(meshes, bs, xs, sizes, world):
+def _timed_batched(meshes, bs, xs, sizes, world, precond=None):
     import torch
     import paper_1911_01492_gb300 as dg
     for x in xs:
@@ -312,7 +312,8 @@ def _timed_batched(meshes, bs, xs, sizes, world):
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
-    stats = dg.cg_solve_batched(meshes, bs, xs, rtol=1e-8, maxit=200000, raise_on_error=False)
+    stats = dg.cg_solve_batched(meshes, bs, xs, rtol=1e-8, maxit=200000, raise_on_error=False,
+                                precond=precond)
     torch.cuda.synchronize()
     dt = max_over_ranks(time.perf_counter() - t0, world)
     work = sum(st["iterations"] * n for st, n in zip(stats, sizes))
@@ -342,7 +343,8 @@ def run_batched(world, rank, sequential_samples: int = 1, full: bool = False):
 
     Always: the 128 small samples (16^3 Q2) in one batched solve against 16 of
     them solved one per dg_cg_solve call, and one-per-call rates of the larger
-    levels.  With full = True also the whole 256-sample batch (minutes).
+    levels, and the small batch again with M = diag(A_s).  With full = True
+    also the whole 256-sample batch, without and with M (minutes).
     """
     out = {"workload": "256 lognormal-K samples: 128 x 16^3 Q2, 96 x 24^3 Q3, 32 x 32^3 Q4 "
                        "(230,162,432 DOFs), FP64 CG to 1e-8; seeds 1000 + sample"}
@@ -353,6 +355,9 @@ def run_batched(world, rank, sequential_samples: int = 1, full: bool = False):
         meshes, bs, sizes, list(range(min(len(meshes), 16))))
     out["small_level_speedup"] = (out["small_level_batched"]["gdof_per_s"]
                                   / out["small_level_one_per_call"]["gdof_per_s"])
+    # the same batch with M = diag(A_s); its time includes forming the diagonals
+    out["small_level_batched_jacobi"] = _timed_batched(meshes, bs, xs, sizes, world,
+                                                       precond="jacobi")
     for m in meshes:
         m.close()
     rates = {}
@@ -368,6 +373,8 @@ def run_batched(world, rank, sequential_samples: int = 1, full: bool = False):
     if full:
         meshes, bs, xs, sizes = _batch_meshes(BATCH_LEVELS)
         out["full_batch"] = _timed_batched(meshes, bs, xs, sizes, world)
+        out["full_batch_jacobi"] = _timed_batched(meshes, bs, xs, sizes, world,
+                                                  precond="jacobi")
         for m in meshes:
             m.close()
     return out

@@ -153,6 +153,15 @@ int dg_diagonal(const dg_mesh* mesh, double* d, void* stream);
 int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, const double* const* b,
                         double* const* x, double rtol, int maxit, dg_cg_stats* st, void* stream);
 
+/* dg_cg_solve_batched with a mode: DG_CG_FP64 (the same as
+ * dg_cg_solve_batched) or DG_CG_FP64 | DG_CG_PRECOND_JACOBI, every sample then
+ * running Section 2.4's PCG with M = diag(A_s) (formed per mesh as by
+ * dg_diagonal, cached until its next dg_set_coefficient).  Other modes:
+ * INVALID_ARG.  Everything else as dg_cg_solve_batched. */
+int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count, const double* const* b,
+                             double* const* x, double rtol, int maxit, int mode,
+                             dg_cg_stats* st, void* stream);
+
 /* Kernel timing for measurement tools (no paper counterpart).  While enabled,
  * each dg_apply / dg_apply_adjoint on this mesh records CUDA
  * events on its stream before pass 1 (traces), between the passes and after

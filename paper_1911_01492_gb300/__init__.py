@@ -57,6 +57,10 @@ _SIGS = {
     "dg_cg_solve_batched": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int,
                                            ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                            ctypes.c_double, ctypes.c_int, _VP, _VP]),
+    "dg_cg_solve_batched_mode": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int,
+                                                ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                                ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                _VP, _VP]),
     "dg_apply_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "dg_diagonal": (ctypes.c_int, [_VP, _VP, _VP]),
     "dg_timing_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -260,8 +264,12 @@ class Mesh:
 
 
 def cg_solve_batched(meshes, bs, xs, rtol: float = 1e-8, maxit: int = 100000, stream=None,
-                     raise_on_error: bool = True):
-    """Solve meshes[s] x[s] = b[s] for all s in one lock-step batched solve."""
+                     raise_on_error: bool = True, precond: str | None = None):
+    """Solve meshes[s] x[s] = b[s] for all s in one lock-step batched solve
+    (FP64).  precond: None or "jacobi" (PCG with M = diag(A_s))."""
+    if precond not in (None, "jacobi"):
+        raise ValueError(f"unknown preconditioner {precond!r}")
+    mode = DG_CG_FP64 | (DG_CG_PRECOND_JACOBI if precond == "jacobi" else 0)
     count = len(meshes)
     if not (len(bs) == len(xs) == count):
         raise ValueError("meshes, bs and xs must have the same length")
@@ -269,8 +277,8 @@ def cg_solve_batched(meshes, bs, xs, rtol: float = 1e-8, maxit: int = 100000, st
     B = (ctypes.c_void_p * count)(*[_ptr(b, _f64(), m.n_dofs, "b") for b, m in zip(bs, meshes)])
     X = (ctypes.c_void_p * count)(*[_ptr(x, _f64(), m.n_dofs, "x") for x, m in zip(xs, meshes)])
     st = (CGStats * count)()
-    rc = library().dg_cg_solve_batched(H, count, B, X, float(rtol), int(maxit),
-                                       ctypes.cast(st, ctypes.c_void_p), _stream(stream))
+    rc = library().dg_cg_solve_batched_mode(H, count, B, X, float(rtol), int(maxit), mode,
+                                            ctypes.cast(st, ctypes.c_void_p), _stream(stream))
     if raise_on_error:
         _check(rc, "dg_cg_solve_batched")
     return [s.as_dict() for s in st]

@@ -2,17 +2,18 @@
 // samples, mesh sizes and degrees, as in the multilevel Monte-Carlo setting of
 // Section 5) solved by lock-step CG in one persistent kernel.
 //
-// Each sample runs the CG of Section 2.4 (M = I) with its own scalars, like
+// Each sample runs the PCG of Section 2.4 (M = I, or M = diag(A) with
+// DG_CG_PRECOND_JACOBI) with its own scalars, like
 // the k independent solvers running in lock-step of the horizontal
 // vectorisation in Section 3.5.  The cells of all samples are cut into work
 // units (one block's worth of cells of one sample); every iteration of every
 // unfinished sample is executed by one persistent cooperative launch:
-//   A  p = r + beta p on the unit's cells, then pass 1 (nodal values, face
-//      traces) of p;
+//   A  p = z + beta p (z = M^-1 r) on the unit's cells, then pass 1 (nodal
+//      values, face traces) of p;
 //   B  pass 2 (volume + face terms) -> q, and the unit's partial <p, q>;
 //   C  per sample: alpha = rho / <p, q>  (partials summed in a fixed order);
-//   D  x += alpha p, r -= alpha q, the unit's partial <r, r>;
-//   E  per sample: rho' = <r, r>, convergence test, beta = rho' / rho;
+//   D  x += alpha p, r -= alpha q, the unit's partials <r, r> and <z, r>;
+//   E  per sample: rho' = <z, r>, convergence test on <r, r>, beta = rho'/rho;
 // separated by grid-wide barriers.  Each barrier spins a bounded number of
 // times; on expiry the kernel raises an error flag and returns, and the host
 // reports DG_ERR_TIMEOUT.  Work units of finished samples are skipped, so
@@ -48,6 +49,7 @@ struct SampleDev {
   const double* kt;
   const double* fw;
   const double* lineop;
+  const double* dinv;  // 1 / diag(A) for M = diag(A); nullptr for M = I
   long long ncells;
   int Nc;       // cells per direction
   int n;        // points per direction
@@ -56,6 +58,7 @@ struct SampleDev {
 
 struct BState {
   double rho, rho_new, alpha, beta, tol2, bnorm2, pq;
+  double rr;  // <r, r>, the convergence norm (rho = <z, r>)
   int done, breakdown, iters, maxit;
 };
 
@@ -150,8 +153,12 @@ kb_persistent(const SampleDev* __restrict__ S, int ns, const int2* __restrict__ 
       const int nblk = (int)((sd.ncells - c0) < cpu ? (sd.ncells - c0) : cpu);
       const long long n3 = (long long)sd.n * sd.n * sd.n;
       const double be = st[s].beta;
-      for (long long i = c0 * n3 + threadIdx.x; i < (c0 + nblk) * n3; i += BT)
-        sd.p[i] = fma(be, sd.p[i], sd.r[i]);
+      if (sd.dinv)
+        for (long long i = c0 * n3 + threadIdx.x; i < (c0 + nblk) * n3; i += BT)
+          sd.p[i] = fma(be, sd.p[i], sd.dinv[i] * sd.r[i]);
+      else
+        for (long long i = c0 * n3 + threadIdx.x; i < (c0 + nblk) * n3; i += BT)
+          sd.p[i] = fma(be, sd.p[i], sd.r[i]);
       __syncthreads();
       switch (sd.n) {
         case 2: unit_pass1<2>(sd, c0, nblk, smem); break;
@@ -182,14 +189,14 @@ kb_persistent(const SampleDev* __restrict__ S, int ns, const int2* __restrict__ 
       for (long long i = c0 * n3 + threadIdx.x; i < (c0 + nblk) * n3; i += BT)
         a = fma(sd.p[i], sd.q[i], a);
       a = block_sum(a, sred);
-      if (threadIdx.x == 0) part[2 * u] = a;
+      if (threadIdx.x == 0) part[3 * u] = a;
     }
     if (!grid_sync(ctl, nb, limit)) return;
     // C: alpha per sample
     for (int s = blockIdx.x; s < ns; s += nb) {
       if (st[s].done) continue;
       double a = 0.0;
-      for (int u = S[s].ubeg + threadIdx.x; u < S[s].uend; u += BT) a += part[2 * u];
+      for (int u = S[s].ubeg + threadIdx.x; u < S[s].uend; u += BT) a += part[3 * u];
       a = block_sum(a, sred);
       if (threadIdx.x == 0) {
         st[s].pq = a;
@@ -202,7 +209,7 @@ kb_persistent(const SampleDev* __restrict__ S, int ns, const int2* __restrict__ 
       }
     }
     if (!grid_sync(ctl, nb, limit)) return;
-    // D: x += alpha p, r -= alpha q, partial <r, r>
+    // D: x += alpha p, r -= alpha q, partials <r, r> and <z, r>
     for (int u = blockIdx.x; u < nu; u += nb) {
       const int s = units[u].x;
       if (st[s].done) continue;
@@ -212,32 +219,53 @@ kb_persistent(const SampleDev* __restrict__ S, int ns, const int2* __restrict__ 
       const int nblk = (int)((sd.ncells - c0) < cpu ? (sd.ncells - c0) : cpu);
       const long long n3 = (long long)sd.n * sd.n * sd.n;
       const double al = st[s].alpha;
-      double a = 0.0;
-      for (long long i = c0 * n3 + threadIdx.x; i < (c0 + nblk) * n3; i += BT) {
-        sd.x[i] = fma(al, sd.p[i], sd.x[i]);
-        const double ri = fma(-al, sd.q[i], sd.r[i]);
-        sd.r[i] = ri;
-        a = fma(ri, ri, a);
+      double a = 0.0, z = 0.0;
+      if (sd.dinv) {  // two loops: no per-element branch between the loads
+        for (long long i = c0 * n3 + threadIdx.x; i < (c0 + nblk) * n3; i += BT) {
+          sd.x[i] = fma(al, sd.p[i], sd.x[i]);
+          const double ri = fma(-al, sd.q[i], sd.r[i]);
+          sd.r[i] = ri;
+          a = fma(ri, ri, a);
+          z = fma(sd.dinv[i] * ri, ri, z);
+        }
+      } else {
+        for (long long i = c0 * n3 + threadIdx.x; i < (c0 + nblk) * n3; i += BT) {
+          sd.x[i] = fma(al, sd.p[i], sd.x[i]);
+          const double ri = fma(-al, sd.q[i], sd.r[i]);
+          sd.r[i] = ri;
+          a = fma(ri, ri, a);
+        }
       }
       a = block_sum(a, sred);
-      if (threadIdx.x == 0) part[2 * u + 1] = a;
+      if (sd.dinv) z = block_sum(z, sred);  // uniform: the block works on one unit
+      if (threadIdx.x == 0) {
+        part[3 * u + 1] = a;
+        part[3 * u + 2] = z;
+      }
     }
     if (!grid_sync(ctl, nb, limit)) return;
-    // E: rho', convergence, beta
+    // E: rho' = <z, r>, convergence on <r, r>, beta
     for (int s = blockIdx.x; s < ns; s += nb) {
       if (st[s].done) continue;
-      double a = 0.0;
-      for (int u = S[s].ubeg + threadIdx.x; u < S[s].uend; u += BT) a += part[2 * u + 1];
+      const bool pc = S[s].dinv != nullptr;
+      double a = 0.0, z = 0.0;
+      for (int u = S[s].ubeg + threadIdx.x; u < S[s].uend; u += BT) {
+        a += part[3 * u + 1];
+        if (pc) z += part[3 * u + 2];
+      }
       a = block_sum(a, sred);
+      if (pc) z = block_sum(z, sred);
       if (threadIdx.x == 0) {
         BState& b = st[s];
+        const double zr = pc ? z : a;
         b.iters += 1;
-        if (!isfinite(a)) {
+        if (!isfinite(a) || !isfinite(zr)) {
           b.breakdown = 1;
           b.done = 1;
         } else {
-          b.beta = a / b.rho;
-          b.rho = a;
+          b.beta = zr / b.rho;
+          b.rho = zr;
+          b.rr = a;
           if (a <= b.tol2 || b.iters >= b.maxit) b.done = 1;
         }
       }
@@ -256,32 +284,35 @@ kb_persistent(const SampleDev* __restrict__ S, int ns, const int2* __restrict__ 
   }
 }
 
-// Per-sample start: r = b - q (q = A x), p = r, rho = <r,r>, bnorm2 = <b,b>,
-// beta = 0.  One launch per sample; the last block publishes the sums.
+// Per-sample start: r = b - q (q = A x), p = z = M^-1 r (dinv, or M = I when
+// dinv is null), rho = <z, r>, rr = <r, r>, bnorm2 = <b, b>, beta = 0.  One
+// launch per sample; the last block publishes the sums.
 __global__ void __launch_bounds__(256)
 kb_init(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
-        double* __restrict__ p, long long n, double rtol, double* partials, unsigned* ticket,
-        BState* st, int maxit, int keep_iters) {
+        double* __restrict__ p, const double* __restrict__ dinv, long long n, double rtol,
+        double* partials, unsigned* ticket, BState* st, int maxit, int keep_iters) {
   __shared__ double sw[8];
   __shared__ bool last;
-  double rr = 0.0, bb = 0.0;
+  double rr = 0.0, bb = 0.0, zr = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const double ri = b[i] - q[i];
+    const double zi = dinv ? dinv[i] * ri : ri;
     r[i] = ri;
-    p[i] = ri;
+    p[i] = zi;
     rr = fma(ri, ri, rr);
     bb = fma(b[i], b[i], bb);
+    zr = fma(zi, ri, zr);
   }
-  double tot[2] = {rr, bb};
-  for (int k = 0; k < 2; ++k) {
+  double tot[3] = {rr, bb, zr};
+  for (int k = 0; k < 3; ++k) {
     double v = warp_sum(tot[k]);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
     __syncthreads();
     double t = 0.0;
     for (int i = 0; i < 8; ++i) t += sw[i];
-    if (threadIdx.x == 0) partials[2 * blockIdx.x + k] = t;
+    if (threadIdx.x == 0) partials[3 * blockIdx.x + k] = t;
   }
   __threadfence();
   __syncthreads();
@@ -290,19 +321,21 @@ kb_init(const double* __restrict__ b, const double* __restrict__ q, double* __re
   if (!last) return;
   __threadfence();
   if (threadIdx.x == 0) {
-    double a = 0.0, c = 0.0;
+    double a = 0.0, c = 0.0, z = 0.0;
     for (unsigned i = 0; i < gridDim.x; ++i) {
-      a += ((volatile double*)partials)[2 * i];
-      c += ((volatile double*)partials)[2 * i + 1];
+      a += ((volatile double*)partials)[3 * i];
+      c += ((volatile double*)partials)[3 * i + 1];
+      z += ((volatile double*)partials)[3 * i + 2];
     }
     BState s = {};
-    s.rho = a;
+    s.rho = z;
+    s.rr = a;
     s.bnorm2 = c;
     s.tol2 = rtol * rtol * c;
     s.beta = 0.0;
     s.maxit = maxit;
     s.iters = keep_iters;
-    s.breakdown = !(isfinite(a) && isfinite(c));
+    s.breakdown = !(isfinite(a) && isfinite(c) && isfinite(z));
     // b = 0: the solution is x = 0 (set by the host), nothing to iterate
     s.done = s.breakdown || c == 0.0 || a <= s.tol2 || keep_iters >= maxit;
     *st = s;
@@ -396,9 +429,14 @@ int launch_persistent(Batch& B, int ns, int blocks, int iters, long long limit, 
 
 }  // namespace
 
-extern "C" int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, const double* const* b,
-                                   double* const* x, double rtol, int maxit, dg_cg_stats* st,
-                                   void* stream) {
+extern "C" int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count,
+                                        const double* const* b, double* const* x, double rtol,
+                                        int maxit, int mode, dg_cg_stats* st, void* stream) {
+  if (mode != DG_CG_FP64 && mode != (DG_CG_FP64 | DG_CG_PRECOND_JACOBI))
+    return dg_fail(DG_ERR_INVALID_ARG,
+                   "dg_cg_solve_batched: mode %d; the batched solver runs DG_CG_FP64, with or "
+                   "without DG_CG_PRECOND_JACOBI", mode);
+  const bool jacobi = (mode & DG_CG_PRECOND_JACOBI) != 0;
   if (meshes == nullptr || b == nullptr || x == nullptr || count < 1)
     return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: NULL array or count < 1");
   if (!(rtol > 0.0) || !(rtol < 1.0))
@@ -442,6 +480,12 @@ extern "C" int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, cons
     d.kt = m->kt64;
     d.fw = m->fw64;
     d.lineop = m->lineop64;
+    d.dinv = nullptr;
+    if (jacobi) {
+      rc = dg_ensure_diagonal(m, m->solve_stream);
+      if (rc) return rc;
+      d.dinv = m->dinv64;
+    }
     d.ncells = m->ncells;
     d.Nc = m->N;
     d.n = m->n;
@@ -453,6 +497,7 @@ extern "C" int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, cons
     sig.push_back(m->N);
     sig.push_back(m->n);
   }
+  sig.push_back(mode);
   B.nunits = (int)hu.size();
   cudaStream_t us = (cudaStream_t)stream;
   // a private non-blocking stream (capture needs one); ordered after the caller's work
@@ -463,7 +508,7 @@ extern "C" int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, cons
   DG_CUDA(cudaMalloc(&B.d_samples, sizeof(SampleDev) * count));
   DG_CUDA(cudaMalloc(&B.d_units, sizeof(int2) * B.nunits));
   DG_CUDA(cudaMalloc(&B.d_state, sizeof(BState) * count));
-  DG_CUDA(cudaMalloc(&B.d_part, sizeof(double) * 2 * B.nunits));
+  DG_CUDA(cudaMalloc(&B.d_part, sizeof(double) * 3 * B.nunits));
   DG_CUDA(cudaMalloc(&B.d_ctl, sizeof(BCtl)));
   DG_CUDA(cudaMalloc(&B.d_aux, sizeof(double) * 2 * 1024));
   DG_CUDA(cudaMalloc(&B.d_ticket, sizeof(unsigned)));
@@ -513,8 +558,8 @@ extern "C" int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, cons
       dg_mesh* m = B.meshes[i];
       int rc = dg_launch_apply_f64(m, x[i], m->q64, nullptr, s);
       if (rc) return rc;
-      kb_init<<<256, 256, 0, s>>>(b[i], m->q64, m->r64, m->p64, m->ndofs, rtol, B.d_aux,
-                                  B.d_ticket, B.d_state + i, maxit, iters_total[i]);
+      kb_init<<<256, 256, 0, s>>>(b[i], m->q64, m->r64, m->p64, hs[i].dinv, m->ndofs, rtol,
+                                  B.d_aux, B.d_ticket, B.d_state + i, maxit, iters_total[i]);
       DG_CUDA(cudaGetLastError());
       ++nstart;
     }
@@ -672,4 +717,10 @@ extern "C" int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, cons
     }
   }
   return first_bad;
+}
+
+extern "C" int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, const double* const* b,
+                                   double* const* x, double rtol, int maxit, dg_cg_stats* st,
+                                   void* stream) {
+  return dg_cg_solve_batched_mode(meshes, count, b, x, rtol, maxit, DG_CG_FP64, st, stream);
 }
