@@ -39,6 +39,17 @@
 
 namespace dgk {
 
+// Per-cell stride (floats or doubles) of the own-trace array in shared memory
+// (12 n^2 values per cell, padded): with the padding, the warp's trace
+// accesses of consecutive cells fall into distinct banks (without it they are
+// 2-way conflicted for n = 3..5 and 4-way for n = 2).
+template <int N>
+constexpr int str_stride() {
+  constexpr int pad = N == 2 ? 4 : N == 3 ? 29 : N == 4 ? 16 : N == 5 ? 13 : N == 6 ? 20
+                    : N == 7 ? 5 : N == 8 ? 0 : 5;
+  return 12 * N * N + pad;
+}
+
 template <int N>
 struct Cfg {
   // cells per block, chosen so a block has ~128-256 threads
@@ -318,7 +329,7 @@ struct FaceLocal {
     (void)c;
     (void)cn;
     (void)fn;
-    const T* own = str + lc * (12 * N2) + (2 * f) * N2 + pt;
+    const T* own = str + lc * str_stride<N>() + (2 * f) * N2 + pt;
     const T uo = own[0], go = own[N2];
     const T un = pre.un[f], gn = in ? pre.gn[f] : go;
     const T wh = pre.wh[f];
@@ -373,7 +384,7 @@ __device__ __forceinline__ void trace_core(T* __restrict__ U, T* __restrict__ Xm
   }
   __syncthreads();
   // along x: thread owns (b = p, e = q); X is modal in x, nodal in y and z
-  T* tr = (MODE == 1) ? str + lc * (12 * N2) : TR + c * (12 * N2);
+  T* tr = (MODE == 1) ? str + lc * str_stride<N>() : TR + c * (12 * N2);
   if (active) {
     T X[N], u[N];
 #pragma unroll

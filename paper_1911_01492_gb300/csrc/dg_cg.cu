@@ -368,7 +368,7 @@ k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
     } else {
       st->rho_new = zr;
       st->rr = rr;
-      st->beta = zr / st->rho;  // next direction update (k_dir32)
+      st->beta = zr / st->rho;  // next direction update (k_dir32_bulk)
       if (rr <= st->delta2 * st->rmax2 || rr <= st->tol2 || st->iters >= st->maxit)
         st->ru_skip = 0;
     }

@@ -232,7 +232,7 @@ k_cell32(const float* __restrict__ p, const float* __restrict__ TR, const float*
   float* sx = su + C * N3;
   float* sr = sx + C * N3;
   float* sk = sr + C * N3;
-  float* str = sk + C * N3;  // C * 12 * N2 own face traces
+  float* str = sk + C * N3;  // C cells x str_stride<N>() own face traces (padded)
   __shared__ float rh[NT], rl[NT];
   __shared__ bool is_last;
   const long long c0 = (long long)blockIdx.x * C;
@@ -302,7 +302,7 @@ k_cell32(const float* __restrict__ p, const float* __restrict__ TR, const float*
       st->done = 1;
       st->ru_skip = 1;
     } else {
-      const double rho = st->rho_new;  // k_dir32 has used beta; commit the new rho
+      const double rho = st->rho_new;  // k_dir32_bulk has used beta; commit the new rho
       st->rho = rho;
       st->restart = 0;
       st->alpha = rho / tot;
@@ -335,7 +335,7 @@ struct Mixed32F {
       k_dir32_bulk<N, false><<<gb, Dir32Bulk<N, false>::THREADS, Dir32Bulk<N, false>::SMEM, s>>>(
           m->r32, m->p32, m->TR32, dinv, m->ncells, m->state, limit, stall_now ? 1 : 0,
           m->tab32);
-    const size_t sm2 = sizeof(float) * (4 * C * N3 + C * 12 * N * N);
+    const size_t sm2 = sizeof(float) * (4 * C * N3 + C * str_stride<N>());
     k_cell32<N><<<blocks, Cfg<N>::THREADS, sm2, s>>>(m->p32, m->TR32, m->kt32, m->gh32, m->q32,
                                                      m->ncells, m->N, m->partials_cells,
                                                      m->state, m->tab32);

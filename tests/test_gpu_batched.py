@@ -72,15 +72,17 @@ def test_batched_jacobi_matches_sequential_and_oracle(dg):
         assert float((x - xseq).norm() / xseq.norm()) <= 1e-6
 
 
-def test_batched_single_sample_and_zero_rhs(dg):
+@pytest.mark.parametrize("precond", [None, "jacobi"])
+def test_batched_single_sample_and_zero_rhs(dg, precond):
     import torch
     meshes, bs, xs, Ks = make_batch(dg, [(3, 2), (2, 3)], seed0=77)
     bs[1].zero_()
     xs[1].fill_(1.0)
-    stats = dg.cg_solve_batched(meshes, bs, xs, rtol=1e-10)
+    stats = dg.cg_solve_batched(meshes, bs, xs, rtol=1e-10, precond=precond)
     assert all(s["status"] == 0 for s in stats)
     assert torch.count_nonzero(xs[1]).item() == 0
-    one = dg.cg_solve_batched(meshes[:1], bs[:1], [torch.zeros_like(xs[0])], rtol=1e-10)
+    one = dg.cg_solve_batched(meshes[:1], bs[:1], [torch.zeros_like(xs[0])], rtol=1e-10,
+                              precond=precond)
     assert one[0]["status"] == 0
 
 

@@ -81,7 +81,8 @@ def test_cg_lognormal_residual_checked_by_oracle(dg, N, k, seed, mode):
         assert st["outer_iterations"] >= 1
 
 
-def test_cg_nonzero_initial_guess_and_zero_rhs(dg):
+@pytest.mark.parametrize("mode,precond", [(0, None), (0, "jacobi"), (1, None), (1, "jacobi")])
+def test_cg_nonzero_initial_guess_and_zero_rhs(dg, mode, precond):
     import torch
     N, k = 3, 3
     D = SIPG(N, k)
@@ -90,11 +91,13 @@ def test_cg_nonzero_initial_guess_and_zero_rhs(dg):
     m.set_coefficient(torch.from_numpy(K).cuda())
     b = inputs.uniform_vector(N, k, 10)
     x0 = torch.from_numpy(inputs.uniform_vector(N, k, 11)).cuda()
-    x, st = m.cg_solve(torch.from_numpy(b).cuda(), x=x0, rtol=1e-11)
-    assert oracle_rel_residual(D, K, b, x.cpu().numpy()) <= 1.05e-11
+    rtol = 1e-11 if mode == 0 else 1e-10
+    x, st = m.cg_solve(torch.from_numpy(b).cuda(), x=x0, rtol=rtol, mode=mode, precond=precond)
+    assert oracle_rel_residual(D, K, b, x.cpu().numpy()) <= 1.05 * rtol
     z = torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda")
-    x, st = m.cg_solve(z.clone(), x=torch.ones_like(z), rtol=1e-10)
+    x, st = m.cg_solve(z.clone(), x=torch.ones_like(z), rtol=1e-10, mode=mode, precond=precond)
     assert st["status"] == 0
+    assert torch.count_nonzero(x).item() == 0
 
 
 def test_cg_maxit_reports_not_converged(dg):
