@@ -16,7 +16,7 @@ from __future__ import annotations
 
 import torch
 
-from . import DG_CG_FP64, Mesh
+from . import DG_CG_FP64, DG_CG_PRECOND_JACOBI, Mesh
 
 
 def _ensure_coefficient(mesh: Mesh, logK: torch.Tensor):
@@ -73,6 +73,12 @@ def apply(x: torch.Tensor, logK: torch.Tensor, mesh: Mesh) -> torch.Tensor:
 
 
 def solve(b: torch.Tensor, logK: torch.Tensor, mesh: Mesh, rtol: float = 1e-12,
-          mode: int = DG_CG_FP64) -> torch.Tensor:
-    """u = A(exp(logK))^{-1} b by CG, differentiable in b and logK (adjoint CG)."""
+          mode: int = DG_CG_FP64, precond: str | None = None) -> torch.Tensor:
+    """u = A(exp(logK))^{-1} b by CG, differentiable in b and logK (adjoint CG).
+    mode and precond (None or "jacobi") select the solver of both the forward
+    and the adjoint solve, as in Mesh.cg_solve."""
+    if precond not in (None, "jacobi"):
+        raise ValueError(f"unknown preconditioner {precond!r}")
+    if precond == "jacobi":
+        mode |= DG_CG_PRECOND_JACOBI
     return SolveFn.apply(b, logK, mesh, rtol, mode)
