@@ -243,7 +243,11 @@ def test_cg_fp64_unaligned_solution_vector(dg, precond):
     assert float((xu - xa).norm() / xa.norm()) <= 1e-8
 
 
-@pytest.mark.parametrize("N,k", [(3, 2), (4, 3), (3, 4), (2, 6), (2, 8)])
+# Every degree with at least one full bulk-copy group of the mixed direction
+# kernel (4 x cells-per-block cells) and a ragged last group, plus meshes
+# smaller than one group (plain loads only).
+@pytest.mark.parametrize("N,k", [(6, 1), (4, 2), (4, 3), (3, 4), (3, 5), (3, 6), (3, 7), (2, 8),
+                                 (3, 2), (2, 6)])
 @pytest.mark.parametrize("mode,precond", [(0, None), (0, "jacobi"), (1, None), (1, "jacobi")])
 def test_cg_first_iterates_match_oracle_recurrence(dg, N, k, mode, precond):
     """Three CG iterations from x = 0 for a random right-hand side: x_3 is a
