@@ -39,17 +39,6 @@
 
 namespace dgk {
 
-// Per-cell stride (floats or doubles) of the own-trace array in shared memory
-// (12 n^2 values per cell, padded): with the padding, the warp's trace
-// accesses of consecutive cells fall into distinct banks (without it they are
-// 2-way conflicted for n = 3..5 and 4-way for n = 2).
-template <int N>
-constexpr int str_stride() {
-  constexpr int pad = N == 2 ? 4 : N == 3 ? 29 : N == 4 ? 16 : N == 5 ? 13 : N == 6 ? 20
-                    : N == 7 ? 5 : N == 8 ? 0 : 5;
-  return 12 * N * N + pad;
-}
-
 template <int N>
 struct Cfg {
   // cells per block, chosen so a block has ~128-256 threads
@@ -244,13 +233,15 @@ template <typename T>
 struct FaceGlobal {
   const T* TR;
   const T* FW;
+  static constexpr bool OWN_IN_THREAD = false;  // own traces come from TR
   struct Pre {};  // nothing prefetched: the FP64 kernels hide load latency behind the FP64 pipe
   template <int N>
   __device__ __forceinline__ void prefetch(Pre&, long long, int, const bool (&)[6],
                                            const long long (&)[6]) const {}
   template <int N, bool UPPER>
   __device__ __forceinline__ void get(const Pre&, long long c, int lc, int f, bool in,
-                                      long long cn, int fn, int pt, T& cv, T& cdm) const {
+                                      long long cn, int fn, int pt, T, T, T& cv,
+                                      T& cdm) const {
     (void)lc;
     face_point<N, UPPER>(TR, FW, c, f, in, cn, fn, pt, cv, cdm);
   }
@@ -266,13 +257,15 @@ template <typename T>
 struct FaceNbr {
   const T* TR;
   const T* FW;
+  static constexpr bool OWN_IN_THREAD = false;  // own terms are in the line operators
   struct Pre {};
   template <int N>
   __device__ __forceinline__ void prefetch(Pre&, long long, int, const bool (&)[6],
                                            const long long (&)[6]) const {}
   template <int N, bool UPPER>
   __device__ __forceinline__ void get(const Pre&, long long c, int lc, int f, bool in,
-                                      long long cn, int fn, int pt, T& cv, T& cdm) const {
+                                      long long cn, int fn, int pt, T, T, T& cv,
+                                      T& cdm) const {
     constexpr int N2 = N * N;
     constexpr T S2 = T(4 * N * N);
     (void)lc;
@@ -292,18 +285,19 @@ struct FaceNbr {
   }
 };
 
-// FaceLocal: own traces from shared memory (computed in the same kernel),
-// neighbour traces from the pass-1 buffer, weights from h*gamma per face
-// (W/2 = h gamma w_s w_t / 2; the derivative weight doubles on the boundary).
+// FaceLocal: own traces formed by the calling line-thread from its own line's
+// values (passed in as uo, go), neighbour traces from the pass-1 buffer,
+// weights from h*gamma per face (W/2 = h gamma w_s w_t / 2; the derivative
+// weight doubles on the boundary).
 // The global loads (neighbour traces, h*gamma) of all six faces are issued
 // together by prefetch() when the cell phase starts, so their latency overlaps
 // the volume work instead of stalling each direction's face step.
 template <typename T>
 struct FaceLocal {
   const T* TR;
-  const T* str;
   const T* gh;
   const DGTab<T>* tab;
+  static constexpr bool OWN_IN_THREAD = true;
   struct Pre {
     T un[6], gn[6], wh[6];  // neighbour trace; W/2 = h gamma w_s w_t / 2 per face
   };
@@ -324,13 +318,13 @@ struct FaceLocal {
   }
   template <int N, bool UPPER>
   __device__ __forceinline__ void get(const Pre& pre, long long c, int lc, int f, bool in,
-                                      long long cn, int fn, int pt, T& cv, T& cdm) const {
-    constexpr int N2 = N * N;
+                                      long long cn, int fn, int pt, T uo, T go, T& cv,
+                                      T& cdm) const {
     (void)c;
+    (void)lc;
     (void)cn;
     (void)fn;
-    const T* own = str + lc * str_stride<N>() + (2 * f) * N2 + pt;
-    const T uo = own[0], go = own[N2];
+    (void)pt;
     const T un = pre.un[f], gn = in ? pre.gn[f] : go;
     const T wh = pre.wh[f];
     flux<N, UPPER>(uo, go, un, gn, wh, in ? wh : wh + wh, cv, cdm);
@@ -348,12 +342,13 @@ struct FaceLocal {
 // in the loads and barriers.
 // trace_core: s already holds the cells' modal coefficients.
 //   MODE 0 (pass 1): writes U, X and the face traces to global memory;
-//   MODE 1: leaves U in s, copies X to sx and the traces to str (shared);
-//   MODE 2: writes only the face traces to global memory.
+//   MODE 2: writes only the face traces to global memory;
+//   MODE 3: leaves U in s and copies X to sx, no traces (the cell phase forms
+//           each line's own traces itself, FaceLocal).
 template <int N, typename T, int MODE>
 __device__ __forceinline__ void trace_core(T* __restrict__ U, T* __restrict__ Xm,
                                            T* __restrict__ TR, long long c0, int nblk,
-                                           const DGTab<T>& tab, T* s, T* sx, T* str) {
+                                           const DGTab<T>& tab, T* s, T* sx) {
   constexpr int N2 = N * N, N3 = N * N * N, H = N / 2;
 
   const int lc = threadIdx.x / N2;
@@ -384,7 +379,7 @@ __device__ __forceinline__ void trace_core(T* __restrict__ U, T* __restrict__ Xm
   }
   __syncthreads();
   // along x: thread owns (b = p, e = q); X is modal in x, nodal in y and z
-  T* tr = (MODE == 1) ? str + lc * str_stride<N>() : TR + c * (12 * N2);
+  T* tr = (MODE == 3) ? nullptr : TR + c * (12 * N2);
   if (active) {
     T X[N], u[N];
 #pragma unroll
@@ -396,25 +391,27 @@ __device__ __forceinline__ void trace_core(T* __restrict__ U, T* __restrict__ Xm
     }
     // x-face traces from the modes: L_i(1) = a_i, L_i(0) = (-1)^i a_i,
     // L_i'(1) = d_i, L_i'(0) = (-1)^(i+1) d_i, a_0 = 1, d_0 = 0
-    T Se = X[0], So = tab.a1[1] * X[1];
+    if (MODE != 3) {
+      T Se = X[0], So = tab.a1[1] * X[1];
 #pragma unroll
-    for (int i = 2; i < N; i += 2) Se = fma(tab.a1[i], X[i], Se);
+      for (int i = 2; i < N; i += 2) Se = fma(tab.a1[i], X[i], Se);
 #pragma unroll
-    for (int i = 3; i < N; i += 2) So = fma(tab.a1[i], X[i], So);
-    T Do = tab.d1[1] * X[1];
+      for (int i = 3; i < N; i += 2) So = fma(tab.a1[i], X[i], So);
+      T Do = tab.d1[1] * X[1];
 #pragma unroll
-    for (int i = 3; i < N; i += 2) Do = fma(tab.d1[i], X[i], Do);
-    T De = T(0);
-    if (N > 2) {
-      De = tab.d1[2] * X[2];
+      for (int i = 3; i < N; i += 2) Do = fma(tab.d1[i], X[i], Do);
+      T De = T(0);
+      if (N > 2) {
+        De = tab.d1[2] * X[2];
 #pragma unroll
-      for (int i = 4; i < N; i += 2) De = fma(tab.d1[i], X[i], De);
+        for (int i = 4; i < N; i += 2) De = fma(tab.d1[i], X[i], De);
+      }
+      const int pt = p + N * q;
+      tr[0 * N2 + pt] = Se - So;                 // x- value
+      tr[1 * N2 + pt] = (N > 2) ? Do - De : Do;  // x- derivative
+      tr[2 * N2 + pt] = Se + So;                 // x+ value
+      tr[3 * N2 + pt] = (N > 2) ? Do + De : Do;  // x+ derivative
     }
-    const int pt = p + N * q;
-    tr[0 * N2 + pt] = Se - So;                 // x- value
-    tr[1 * N2 + pt] = (N > 2) ? Do - De : Do;  // x- derivative
-    tr[2 * N2 + pt] = Se + So;                 // x+ value
-    tr[3 * N2 + pt] = (N > 2) ? Do + De : Do;  // x+ derivative
     b_fwd<N>(tab, X, u);
 #pragma unroll
     for (int a = 0; a < N; ++a) {
@@ -422,6 +419,7 @@ __device__ __forceinline__ void trace_core(T* __restrict__ U, T* __restrict__ Xm
       if (MODE == 0) U[c * N3 + q * N2 + p * N + a] = u[a];
     }
   }
+  if (MODE == 3) return;  // the caller synchronises before reading s
   __syncthreads();
   if (active) {
     // y-faces: thread owns points (a = p, e = q); z-faces: (a = p, b = q)
@@ -467,7 +465,7 @@ __device__ __forceinline__ void trace_cells(const T* __restrict__ x, T* __restri
   const T* xb = x + c0 * N3;
   for (int t = threadIdx.x; t < nblk * N3; t += blockDim.x) s[t] = xb[t];
   __syncthreads();
-  trace_core<N, T, 0>(U, Xm, TR, c0, nblk, tab, s, nullptr, nullptr);
+  trace_core<N, T, 0>(U, Xm, TR, c0, nblk, tab, s, nullptr);
 }
 
 template <int N, typename T>
@@ -590,8 +588,24 @@ __device__ __forceinline__ void cell_core(const FS& fs, T* __restrict__ y, long 
       const bool inl = (dir == 0) ? (cz > 0) : (cy > 0);
       const long long st = (dir == 0) ? sz : sy;
       T cv1, cd1, cv0, cd0;
-      fs.template get<N, true>(pre, c, lc, fu, inu, c + st, fl, pt, cv1, cd1);
-      fs.template get<N, false>(pre, c, lc, fl, inl, c - st, fu, pt, cv0, cd0);
+      // own traces of the line's end points (FaceLocal only): Lagrange end
+      // values and derivatives of the line's nodal values
+      T vm = T(0), vp = T(0), gm = T(0), gp = T(0);
+      if constexpr (FS::OWN_IN_THREAD) {
+        vm = tab.l0[0] * u[0];
+        vp = tab.l1[0] * u[0];
+        gm = tab.dl0[0] * u[0];
+        gp = tab.dl1[0] * u[0];
+#pragma unroll
+        for (int e = 1; e < N; ++e) {
+          vm = fma(tab.l0[e], u[e], vm);
+          vp = fma(tab.l1[e], u[e], vp);
+          gm = fma(tab.dl0[e], u[e], gm);
+          gp = fma(tab.dl1[e], u[e], gp);
+        }
+      }
+      fs.template get<N, true>(pre, c, lc, fu, inu, c + st, fl, pt, vp, gp, cv1, cd1);
+      fs.template get<N, false>(pre, c, lc, fl, inl, c - st, fu, pt, vm, gm, cv0, cd0);
 #pragma unroll
       for (int e = 0; e < N; ++e) {
         T acc = fma(tab.l1[e], cv1, r[e]);
@@ -632,8 +646,29 @@ __device__ __forceinline__ void cell_core(const FS& fs, T* __restrict__ y, long 
       bt_bdt<N>(tab, rr, kg, R);
     }
     T cv1, cd1, cv0, cd0;
-    fs.template get<N, true>(pre, c, lc, 1, cx < Nc - 1, c + 1, 0, pt, cv1, cd1);
-    fs.template get<N, false>(pre, c, lc, 0, cx > 0, c - 1, 1, pt, cv0, cd0);
+    // own x-face traces from the modes (FaceLocal only): L_i(1) = a_i,
+    // L_i(0) = (-1)^i a_i, L_i'(1) = d_i, L_i'(0) = (-1)^(i+1) d_i
+    T xm = T(0), xp = T(0), dxm = T(0), dxp = T(0);
+    if constexpr (FS::OWN_IN_THREAD) {
+      T Se = X[0], So = tab.a1[1] * X[1], Do = tab.d1[1] * X[1], De = T(0);
+#pragma unroll
+      for (int i = 2; i < N; i += 2) Se = fma(tab.a1[i], X[i], Se);
+#pragma unroll
+      for (int i = 3; i < N; i += 2) So = fma(tab.a1[i], X[i], So);
+#pragma unroll
+      for (int i = 3; i < N; i += 2) Do = fma(tab.d1[i], X[i], Do);
+      if (N > 2) {
+        De = tab.d1[2] * X[2];
+#pragma unroll
+        for (int i = 4; i < N; i += 2) De = fma(tab.d1[i], X[i], De);
+      }
+      xm = Se - So;
+      xp = Se + So;
+      dxm = Do - De;
+      dxp = Do + De;
+    }
+    fs.template get<N, true>(pre, c, lc, 1, cx < Nc - 1, c + 1, 0, pt, xp, dxp, cv1, cd1);
+    fs.template get<N, false>(pre, c, lc, 0, cx > 0, c - 1, 1, pt, xm, dxm, cv0, cd0);
     // modal test functions: value a_i at 1, (-1)^i a_i at 0; derivative -d_i cd
     // at 1, -(-1)^(i+1) d_i cd at 0 (a_0 = 1, d_0 = 0)
     const T sp = cv1 + cv0, sm = cv1 - cv0;

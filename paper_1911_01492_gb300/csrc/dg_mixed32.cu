@@ -9,8 +9,9 @@
 //             pass 1 of p writing only the face traces (no U, X).  Its inputs
 //             are staged in shared memory by bulk copies (TMA engine),
 //             double-buffered over groups of cells in a persistent grid.
-//   k_cell32: reloads p, recomputes its nodal values, x-modal values and own
-//             face traces in shared memory, reads the neighbours' traces,
+//   k_cell32: reloads p, recomputes its nodal and x-modal values in shared
+//             memory (each line-thread forms its own face traces from its
+//             line's values), reads the neighbours' traces,
 //             forms the face weights from h*gamma, computes q = A p, and folds
 //             <p, q> (FP64-accurate: exact products summed in compensated
 //             float-float) into its epilogue; the last block to finish commits
@@ -201,7 +202,7 @@ k_dir32_bulk(const float* __restrict__ r, float* __restrict__ p, float* __restri
         }
       }
       __syncthreads();
-      trace_core<N, float, 2>(nullptr, nullptr, TR, cg0, nblk, tab, sp, nullptr, nullptr);
+      trace_core<N, float, 2>(nullptr, nullptr, TR, cg0, nblk, tab, sp, nullptr);
       __syncthreads();
     }
   }
@@ -232,7 +233,6 @@ k_cell32(const float* __restrict__ p, const float* __restrict__ TR, const float*
   float* sx = su + C * N3;
   float* sr = sx + C * N3;
   float* sk = sr + C * N3;
-  float* str = sk + C * N3;  // C cells x str_stride<N>() own face traces (padded)
   __shared__ float rh[NT], rl[NT];
   __shared__ bool is_last;
   const long long c0 = (long long)blockIdx.x * C;
@@ -251,9 +251,9 @@ k_cell32(const float* __restrict__ p, const float* __restrict__ TR, const float*
     }
   }
   __syncthreads();
-  trace_core<N, float, 1>(nullptr, nullptr, nullptr, c0, nblk, tab, su, sx, str);
+  trace_core<N, float, 3>(nullptr, nullptr, nullptr, c0, nblk, tab, su, sx);
   __syncthreads();
-  const FaceLocal<float> fs{TR, str, gh, &tab};
+  const FaceLocal<float> fs{TR, gh, &tab};
   cell_core<N, float>(fs, q, c0, nblk, Nc, tab, su, sx, sr, sk);
   // <p, q> over the block's cells; q is still in sx after cell_core
   float hi = 0.0f, lo = 0.0f;
@@ -335,7 +335,7 @@ struct Mixed32F {
       k_dir32_bulk<N, false><<<gb, Dir32Bulk<N, false>::THREADS, Dir32Bulk<N, false>::SMEM, s>>>(
           m->r32, m->p32, m->TR32, dinv, m->ncells, m->state, limit, stall_now ? 1 : 0,
           m->tab32);
-    const size_t sm2 = sizeof(float) * (4 * C * N3 + C * str_stride<N>());
+    const size_t sm2 = sizeof(float) * 4 * C * N3;
     k_cell32<N><<<blocks, Cfg<N>::THREADS, sm2, s>>>(m->p32, m->TR32, m->kt32, m->gh32, m->q32,
                                                      m->ncells, m->N, m->partials_cells,
                                                      m->state, m->tab32);
