@@ -19,7 +19,7 @@
 //             sets alpha = rho / <p, q>.
 // Per DOF this moves ~38 B for the operator (instead of ~66 B in the generic
 // two-pass FP32 path) and removes the separate direction and dot kernels.
-// Measured at 48^3 Q4 (13.8 M DOFs): k_dir32_bulk 58 us + k_cell32 168 us per
+// Measured at 48^3 Q4 (13.8 M DOFs): k_dir32_bulk 58 us + k_cell32 124 us per
 // iteration.  The same fusion built on stored U and X (generic pass 2) was
 // slower, so recomputing in shared memory is kept.  k_cell32 is bound by
 // instruction issue and block barriers (~9 warp instructions per DOF).
@@ -272,17 +272,32 @@ k_cell32(const float* __restrict__ p, const float* __restrict__ TR, const float*
   rh[threadIdx.x] = hi;
   rl[threadIdx.x] = lo;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float h = 0.0f, l = 0.0f;
-    for (int i = 0; i < NT; ++i) {
+  // Fixed-order compensated block sum: lane l of warp 0 folds entries
+  // l, l + 32, ... (NT >= 32 for every degree, so warp 0 is full), then a
+  // butterfly over the warp.  A serial sum by one thread kept the whole block
+  // resident for ~NT dependent TwoSums.
+  if (threadIdx.x < 32) {
+    float h = rh[threadIdx.x], l = rl[threadIdx.x];
+    for (int i = threadIdx.x + 32; i < NT; i += 32) {
       float s1, t1;
       two_sum_f(h, rh[i], s1, t1);
       h = s1;
       l += t1 + rl[i];
     }
-    partials[blockIdx.x] = (double)h + (double)l;
-    __threadfence();
-    is_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h, off);
+      const float ol = __shfl_xor_sync(0xffffffffu, l, off);
+      float s1, t1;
+      two_sum_f(h, oh, s1, t1);
+      h = s1;
+      l += ol + t1;
+    }
+    if (threadIdx.x == 0) {
+      partials[blockIdx.x] = (double)h + (double)l;
+      __threadfence();
+      is_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+    }
   }
   __syncthreads();
   if (!is_last) return;
