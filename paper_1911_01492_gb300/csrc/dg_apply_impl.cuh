@@ -345,10 +345,26 @@ struct FaceLocal {
 //   MODE 2: writes only the face traces to global memory;
 //   MODE 3: leaves U in s and copies X to sx, no traces (the cell phase forms
 //           each line's own traces itself, FaceLocal).
-template <int N, typename T, int MODE>
+// Default z-line input of trace_core: the line's modal values already in s.
+struct ZFromShared {
+  template <int N, typename T>
+  __device__ __forceinline__ void operator()(const T* sc, int lc, int p, int q,
+                                             T (&v)[N]) const {
+    (void)lc;
+#pragma unroll
+    for (int l = 0; l < N; ++l) v[l] = sc[l * N * N + q * N + p];
+  }
+};
+
+// ZL: fills v[l] (l = 0..n-1) with the modal values of the thread's z-line
+// (x-mode p, y-mode q of cell lc); a kernel that produces those values itself
+// (a direction update, a load from global memory) passes its own loader and
+// needs no barrier between producing them and the first contraction.
+template <int N, typename T, int MODE, typename ZL = ZFromShared>
 __device__ __forceinline__ void trace_core(T* __restrict__ U, T* __restrict__ Xm,
                                            T* __restrict__ TR, long long c0, int nblk,
-                                           const DGTab<T>& tab, T* s, T* sx) {
+                                           const DGTab<T>& tab, T* s, T* sx,
+                                           const ZL& zload = ZL()) {
   constexpr int N2 = N * N, N3 = N * N * N, H = N / 2;
 
   const int lc = threadIdx.x / N2;
@@ -361,8 +377,7 @@ __device__ __forceinline__ void trace_core(T* __restrict__ U, T* __restrict__ Xm
   // along z: thread owns (i = p, j = q)
   if (active) {
     T v[N], u[N];
-#pragma unroll
-    for (int l = 0; l < N; ++l) v[l] = sc[l * N2 + q * N + p];
+    zload.template operator()<N, T>(sc, lc, p, q, v);
     b_fwd<N>(tab, v, u);
 #pragma unroll
     for (int e = 0; e < N; ++e) sc[e * N2 + q * N + p] = u[e];

@@ -19,7 +19,7 @@
 //             sets alpha = rho / <p, q>.
 // Per DOF this moves ~38 B for the operator (instead of ~66 B in the generic
 // two-pass FP32 path) and removes the separate direction and dot kernels.
-// Measured at 48^3 Q4 (13.8 M DOFs): k_dir32_bulk 58 us + k_cell32 124 us per
+// Measured at 48^3 Q4 (13.8 M DOFs): k_dir32_bulk 53 us + k_cell32 123 us per
 // iteration.  The same fusion built on stored U and X (generic pass 2) was
 // slower, so recomputing in shared memory is kept.  k_cell32 is bound by
 // instruction issue and block barriers (~9 warp instructions per DOF).
@@ -97,6 +97,51 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
   return false;
 }
 
+// z-line loaders for trace_core (see ZFromShared): the thread that owns a
+// z-line produces its values itself, with no barrier before the contraction.
+// ZDirUpdate: p = z + beta p (z = M^-1 r) from the staged group buffers,
+// written to global p (the operator pass reads it) and returned for the
+// contraction.
+template <bool PC>
+struct ZDirUpdate {
+  const float* sr;  // staged r of the group
+  const float* sd;  // staged 1/diag(A) (PC)
+  float* pg;        // global p of the group
+  float beta;
+  template <int N, typename T>
+  __device__ __forceinline__ void operator()(const T* sc, int lc, int pp, int qq,
+                                             T (&v)[N]) const {
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      const int idx = l * N * N + qq * N + pp;
+      const int off = lc * N * N * N + idx;
+      float z = sr[off];
+      if constexpr (PC) z = sd[off] * z;
+      const float val = fmaf(beta, sc[idx], z);
+      pg[off] = val;
+      v[l] = val;
+    }
+  }
+};
+
+// ZLoadKeep: the z-line of p from global memory, also kept in `keep` for the
+// <p, q> epilogue (each element of the block is on exactly one z-line).
+template <int NK>
+struct ZLoadKeep {
+  const float* pg;  // global p of the block's first cell
+  float (&keep)[NK];
+  template <int N, typename T>
+  __device__ __forceinline__ void operator()(const T* sc, int lc, int pp, int qq,
+                                             T (&v)[N]) const {
+    (void)sc;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      v[l] = pg[lc * N * N * N + l * N * N + qq * N + pp];
+      keep[l] = v[l];
+    }
+  }
+};
+
 // Direction kernel with the block's inputs staged by bulk copies,
 // double-buffered.  The cells are cut into groups of G = 4 CPB cells: G n^3
 // floats are a multiple of 16 bytes for every n, so each group of r, p (and
@@ -135,16 +180,18 @@ k_dir32_bulk(const float* __restrict__ r, float* __restrict__ p, float* __restri
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);
   float* buf = reinterpret_cast<float*>(smem_raw + 16);
-  float* const br[2] = {buf, buf + G * N3};
-  float* const bp[2] = {buf + 2 * G * N3, buf + 3 * G * N3};
-  float* const bd[2] = {buf + 4 * G * N3, buf + 5 * G * N3};  // PC only
+  // buffer b (0, 1) of r, p and 1/diag: pointer arithmetic, not arrays
+  // indexed at run time (which would live in local memory)
+  auto br = [&](int b) { return buf + b * G * N3; };
+  auto bp = [&](int b) { return buf + (2 + b) * G * N3; };
+  auto bd = [&](int b) { return buf + (4 + b) * G * N3; };  // PC only
   const long long ngroups = (ncells + G - 1) / G;
   const long long nfull = ncells / G;  // groups moved by bulk copies
   auto issue = [&](long long g, int b) {  // thread 0 only
     mbar_arrive_expect_tx(&bar[b], B::NARR * B::GROUP_BYTES);
-    bulk_g2s(br[b], r + g * G * N3, B::GROUP_BYTES, &bar[b]);
-    bulk_g2s(bp[b], p + g * G * N3, B::GROUP_BYTES, &bar[b]);
-    if constexpr (PC) bulk_g2s(bd[b], dinv + g * G * N3, B::GROUP_BYTES, &bar[b]);
+    bulk_g2s(br(b), r + g * G * N3, B::GROUP_BYTES, &bar[b]);
+    bulk_g2s(bp(b), p + g * G * N3, B::GROUP_BYTES, &bar[b]);
+    if constexpr (PC) bulk_g2s(bd(b), dinv + g * G * N3, B::GROUP_BYTES, &bar[b]);
   };
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
@@ -153,10 +200,15 @@ k_dir32_bulk(const float* __restrict__ r, float* __restrict__ p, float* __restri
   }
   __syncthreads();
   long long g = blockIdx.x;
-  bool issued[2] = {false, false};  // a copy into buffer b is in flight (thread 0's view)
+  // a copy into buffer 0 / 1 is in flight (thread 0's view)
+  bool issued0 = false, issued1 = false;
+  auto set_issued = [&](int b, bool v) {
+    if (b) issued1 = v;
+    else issued0 = v;
+  };
   if (threadIdx.x == 0 && g < nfull && !stall_test) {
     issue(g, 0);
-    issued[0] = true;
+    issued0 = true;
   }
   bool failed = false;
   int it = 0;
@@ -166,7 +218,7 @@ k_dir32_bulk(const float* __restrict__ r, float* __restrict__ p, float* __restri
     if (threadIdx.x == 0 && gn < nfull) {
       fence_proxy_async();  // the previous group's generic accesses to buffer b^1
       issue(gn, b ^ 1);
-      issued[b ^ 1] = true;
+      set_issued(b ^ 1, true);
     }
     const long long cg0 = g * G;
     if (g < nfull) {
@@ -175,34 +227,21 @@ k_dir32_bulk(const float* __restrict__ r, float* __restrict__ p, float* __restri
         failed = true;
         break;
       }
-      if (threadIdx.x == 0) issued[b] = false;
+      if (threadIdx.x == 0) set_issued(b, false);
     } else {  // ragged last group
       const int n = (int)(ncells - cg0) * N3;
       for (int t = threadIdx.x; t < n; t += NT) {
-        br[b][t] = r[cg0 * N3 + t];
-        bp[b][t] = p[cg0 * N3 + t];
-        if constexpr (PC) bd[b][t] = dinv[cg0 * N3 + t];
+        br(b)[t] = r[cg0 * N3 + t];
+        bp(b)[t] = p[cg0 * N3 + t];
+        if constexpr (PC) bd(b)[t] = dinv[cg0 * N3 + t];
       }
       __syncthreads();
     }
     {
       const int nblk = (int)((ncells - cg0) < G ? (ncells - cg0) : G);
-      float* sp = bp[b];
-      const float* sr = br[b];
-      const float* sd = bd[b];
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        const int t = threadIdx.x + k * NT;
-        if (t < nblk * N3) {
-          float z = sr[t];
-          if constexpr (PC) z = sd[t] * z;  // z = M^-1 r
-          const float v = fmaf(beta, sp[t], z);  // p = z + beta p
-          sp[t] = v;
-          p[cg0 * N3 + t] = v;
-        }
-      }
-      __syncthreads();
-      trace_core<N, float, 2>(nullptr, nullptr, TR, cg0, nblk, tab, sp, nullptr);
+      // p = z + beta p by the z-line threads, then pass 1 of p (traces only)
+      const ZDirUpdate<PC> zl{br(b), bd(b), p + cg0 * N3, beta};
+      trace_core<N, float, 2>(nullptr, nullptr, TR, cg0, nblk, tab, bp(b), nullptr, zl);
       __syncthreads();
     }
   }
@@ -212,7 +251,8 @@ k_dir32_bulk(const float* __restrict__ r, float* __restrict__ p, float* __restri
     st->ru_skip = 1;
     // copies of this block still in flight: wait for them, bounded again
     for (int bb = 0; bb < 2; ++bb)
-      if (issued[bb]) mbar_wait_bounded(&bar[bb], (unsigned)(((it + (bb != (it & 1))) >> 1) & 1), limit);
+      if (bb ? issued1 : issued0)
+        mbar_wait_bounded(&bar[bb], (unsigned)(((it + (bb != (it & 1))) >> 1) & 1), limit);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -237,31 +277,38 @@ k_cell32(const float* __restrict__ p, const float* __restrict__ TR, const float*
   __shared__ bool is_last;
   const long long c0 = (long long)blockIdx.x * C;
   const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
-  // NT = C n^2 threads cover the block's C n^3 values in N strides; each
-  // thread keeps its p values in registers for the <p, q> epilogue
-  float preg[N];
+  // h w K of the block's cells: loaded into registers now, stored to shared
+  // memory after pass 1 (the cell phase reads it), so that these loads and
+  // the z-line loads of p below are in flight together
+  float kreg[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     const int t = threadIdx.x + k * NT;
-    preg[k] = 0.0f;
-    if (t < nblk * N3) {
-      preg[k] = p[c0 * N3 + t];
-      su[t] = preg[k];
-      sk[t] = kt[c0 * N3 + t];
-    }
+    kreg[k] = t < nblk * N3 ? kt[c0 * N3 + t] : 0.0f;
   }
-  __syncthreads();
-  trace_core<N, float, 3>(nullptr, nullptr, nullptr, c0, nblk, tab, su, sx);
+  // pass 1 in shared memory; each z-line thread loads its line of p from
+  // global memory and keeps it for the <p, q> epilogue
+  float preg[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) preg[l] = 0.0f;
+  const ZLoadKeep<N> zl{p + c0 * N3, preg};
+  trace_core<N, float, 3>(nullptr, nullptr, nullptr, c0, nblk, tab, su, sx, zl);
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int t = threadIdx.x + k * NT;
+    if (t < nblk * N3) sk[t] = kreg[k];
+  }
   __syncthreads();
   const FaceLocal<float> fs{TR, gh, &tab};
   cell_core<N, float>(fs, q, c0, nblk, Nc, tab, su, sx, sr, sk);
-  // <p, q> over the block's cells; q is still in sx after cell_core
+  // <p, q> over the block's cells on the z-lines of p kept above; q is
+  // still in sx after cell_core (same layout as p)
   float hi = 0.0f, lo = 0.0f;
+  const int zlc = threadIdx.x / N2, zt2 = threadIdx.x - zlc * N2;
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    const int t = threadIdx.x + k * NT;
-    if (t >= nblk * N3) break;
-    const float a = preg[k], b = sx[t];
+  for (int l = 0; l < N; ++l) {
+    if (zlc >= nblk) break;
+    const float a = preg[l], b = sx[zlc * N3 + l * N2 + zt2];
     const float pr = a * b;
     const float e = fmaf(a, b, -pr);
     float s1, t1;
