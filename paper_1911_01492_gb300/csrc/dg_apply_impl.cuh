@@ -356,6 +356,19 @@ struct ZFromShared {
   }
 };
 
+// z-line input straight from global memory (xg: the block's first cell).
+template <typename TG>
+struct ZFromGlobal {
+  const TG* xg;
+  template <int N, typename T>
+  __device__ __forceinline__ void operator()(const T* sc, int lc, int p, int q,
+                                             T (&v)[N]) const {
+    (void)sc;
+#pragma unroll
+    for (int l = 0; l < N; ++l) v[l] = xg[lc * N * N * N + l * N * N + q * N + p];
+  }
+};
+
 // ZL: fills v[l] (l = 0..n-1) with the modal values of the thread's z-line
 // (x-mode p, y-mode q of cell lc); a kernel that produces those values itself
 // (a direction update, a load from global memory) passes its own loader and
@@ -477,10 +490,9 @@ __device__ __forceinline__ void trace_cells(const T* __restrict__ x, T* __restri
                                             T* __restrict__ Xm, T* __restrict__ TR, long long c0,
                                             int nblk, const DGTab<T>& tab, T* s) {
   constexpr int N3 = N * N * N;
-  const T* xb = x + c0 * N3;
-  for (int t = threadIdx.x; t < nblk * N3; t += blockDim.x) s[t] = xb[t];
-  __syncthreads();
-  trace_core<N, T, 0>(U, Xm, TR, c0, nblk, tab, s, nullptr);
+  // each z-line thread loads its own line of x: no staging barrier
+  const ZFromGlobal<T> zl{x + c0 * N3};
+  trace_core<N, T, 0>(U, Xm, TR, c0, nblk, tab, s, nullptr, zl);
 }
 
 template <int N, typename T>
