@@ -118,7 +118,7 @@ int dg_coeff_grad(const dg_mesh* mesh, const double* u, const double* v, double*
  * mode DG_CG_FP64: FP64 operator and vectors.
  * mode DG_CG_MIXED_IR: mixed-precision CG with iterative refinement of the
  *   residual: the CG recurrence runs on the FP32 operator with FP32 vectors and
- *   FP64-accurate inner products; each time its residual has dropped by 10x
+ *   FP64-accurate inner products; each time its residual has dropped by 5x
  *   the FP32 correction is added to x in FP64 and r = b - A x is recomputed
  *   with the FP64 operator and replaces the FP32 residual (the search
  *   direction is kept).
