@@ -113,7 +113,8 @@ int dg_apply_host(const dg_mesh* mesh, const void* x_host, void* y_host, int pre
  * form with gamma = 1.  g must not alias u or v. */
 int dg_coeff_grad(const dg_mesh* mesh, const double* u, const double* v, double* g, void* stream);
 
-/* Solve A(K) x = b by CG (Section 2.4, PCG with M = I).  b, x: FP64 device
+/* Solve A(K) x = b by CG (Section 2.4's PCG; M = I unless the mode adds
+ * DG_CG_PRECOND_JACOBI).  b, x: FP64 device
  * pointers; x holds the initial guess on entry and the solution on exit.
  * mode DG_CG_FP64: FP64 operator and vectors.
  * mode DG_CG_MIXED_IR: mixed-precision CG with iterative refinement of the
@@ -130,7 +131,9 @@ int dg_coeff_grad(const dg_mesh* mesh, const double* u, const double* v, double*
  *   solve after dg_set_coefficient (one kernel, see dg_diagonal).
  * Stops when ||b - A x|| <= rtol ||b|| recomputed in FP64.  Blocking.
  * Returns NOT_CONVERGED at maxit (x holds the last iterate), BREAKDOWN on
- * <p, Ap> <= 0 or non-finite scalars.  st may be NULL. */
+ * <p, Ap> <= 0 or non-finite scalars, TIMEOUT if a bounded wait of the mixed
+ * mode's FP32 direction kernel on its bulk copies ran out (the kernel stops
+ * cleanly; the context stays usable).  st may be NULL. */
 int dg_cg_solve(const dg_mesh* mesh, const double* b, double* x, double rtol, int maxit,
                 int mode, dg_cg_stats* st, void* stream);
 
@@ -149,7 +152,8 @@ int dg_diagonal(const dg_mesh* mesh, double* d, void* stream);
  * samples is one persistent launch, and the iteration loop is captured in a
  * CUDA graph.  b[s], x[s]: device pointers (arrays of count pointers on the
  * host).  st: count entries (may be NULL).  Returns the first non-OK sample
- * status, or OK.  Blocking. */
+ * status, or OK; TIMEOUT if a bounded grid-barrier wait of the persistent
+ * kernel ran out (the kernel stops cleanly).  Blocking. */
 int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, const double* const* b,
                         double* const* x, double rtol, int maxit, dg_cg_stats* st, void* stream);
 
