@@ -62,25 +62,36 @@ typedef struct {
 } dg_cg_stats;
 
 /* Last error message of the calling thread ("" if none).  The pointer stays
- * valid until the next failing call on this thread. */
+ * valid until the next failing call on this thread.  (Library bookkeeping; the
+ * paper has no counterpart.) */
 const char* dg_last_error(void);
 
 /* Create a mesh of n_cells^3 cubes of the unit cube with Q_degree elements,
  * 1 <= n_cells <= 1024, 1 <= degree <= 8, on the current CUDA device.
+ * Section 4.1 (continuous problem and discretization): the fine partition of
+ * the domain and the broken polynomial space V on it on which the SWIPDG form
+ * is posed; here the partition is n_cells^3 axis-aligned cubes and V is the
+ * tensor-product Q_degree space of each cube (Section 3.3 uses the same
+ * tensor-product structure for sum factorisation).
  * Allocates the device workspaces (coefficient data, traces).  K is unset
  * until dg_set_coefficient.  Errors: INVALID_ARG, OOM, CUDA. */
 int dg_create_mesh(int n_cells, int degree, dg_mesh** out);
 
-/* Free the mesh and its workspaces (NULL is accepted). Synchronises the device. */
+/* Free the mesh and its workspaces (NULL is accepted). Synchronises the device.
+ * (Library bookkeeping; the paper has no counterpart.) */
 int dg_destroy_mesh(dg_mesh* mesh);
 
-/* Sizes: DOFs (= n_cells^3 (degree+1)^3), cells, n = degree+1, sigma. Any
- * output pointer may be NULL. */
+/* Sizes: DOFs (= n_cells^3 (degree+1)^3), cells, n = degree+1, sigma (the
+ * penalty factor sigma_e of the Section 4.1 face form).  Any output pointer
+ * may be NULL. */
 int dg_mesh_info(const dg_mesh* mesh, long long* n_dofs, long long* n_cells_total,
                  int* n_points_1d, double* sigma);
 
 /* Set the diffusion coefficient K (device pointer, FP64, layout K[c*n^3 + q],
- * values at the volume Gauss points).  Derives the weighted volume factors
+ * values at the volume Gauss points).  K is the coefficient A = lambda kappa of
+ * the Section 4.1 problem -div(A grad p) = f (here a scalar field); Section 5
+ * draws it as a lognormal random field, the workload this library targets.
+ * Derives the weighted volume factors
  * h w_q K (FP64 and FP32 copies), Kbar per cell and gamma per face side.
  * Blocks until done: K <= 0 or non-finite anywhere returns INVALID_ARG and
  * leaves the mesh without a coefficient. */
@@ -93,12 +104,16 @@ int dg_set_coefficient(dg_mesh* mesh, const double* K, void* stream);
  * accumulates in FP32 from FP32-rounded tables and coefficients. */
 int dg_apply(const dg_mesh* mesh, const void* x, void* y, int prec, void* stream);
 
-/* xbar = A(K)^T ybar.  The SIPG form is symmetric (a(u,v) = a(v,u)), so the
- * transposed data flow (test functions <-> trial functions) is the same
- * sequence of contractions; arguments as dg_apply. */
+/* xbar = A(K)^T ybar.  The paper has no counterpart: this is the adjoint that
+ * differentiation through dg_apply needs.  The Section 4.1 SWIPDG form is
+ * symmetric (b(v,w) = b(w,v)), so the transposed data flow (test functions <->
+ * trial functions) is the same sequence of contractions; arguments as
+ * dg_apply. */
 int dg_apply_adjoint(const dg_mesh* mesh, const void* ybar, void* xbar, int prec, void* stream);
 
-/* Same as dg_apply but x and y are HOST buffers (pinned or pageable).  The
+/* Same as dg_apply but x and y are HOST buffers (pinned or pageable): the
+ * Section 3.3 operator application with the host<->device copies inside the
+ * call (the paper has no counterpart; it runs on host memory throughout).  The
  * mesh is cut into at most 16 slabs of z-layers: x is copied in slab by slab
  * on a copy stream, pass 1 of each slab runs on an internal stream as soon as
  * its x has arrived, pass 2 of slab s runs on `stream` once pass 1 has covered
@@ -108,7 +123,10 @@ int dg_apply_adjoint(const dg_mesh* mesh, const void* ybar, void* xbar, int prec
 int dg_apply_host(const dg_mesh* mesh, const void* x_host, void* y_host, int prec, void* stream);
 
 /* g[c*n^3 + q] = d(v^T A(K) u) / d log K_{c,q}  (FP64 device pointers, g
- * overwritten).  Volume part h w_q K_q grad u . grad v at the point; face part
+ * overwritten).  The paper has no counterpart: this differentiates the
+ * Section 4.1 form b(u, v) with respect to the log of its coefficient A at the
+ * volume Gauss points (the gradient that a loss on the Section 5 lognormal
+ * field needs).  Volume part h w_q K_q grad u . grad v at the point; face part
  * w_q * sum over the cell's faces of d gamma_F / d log Kbar_c times the face
  * form with gamma = 1.  g must not alias u or v. */
 int dg_coeff_grad(const dg_mesh* mesh, const double* u, const double* v, double* g, void* stream);
@@ -148,7 +166,10 @@ int dg_cg_solve(const dg_mesh* mesh, const double* b, double* x, double rtol, in
 int dg_diagonal(const dg_mesh* mesh, double* d, void* stream);
 
 /* Solve count independent systems A_s x_s = b_s (meshes may differ in size and
- * degree; FP64) with CG run in lock-step: every iteration of all unfinished
+ * degree; FP64) with CG run in lock-step.  Section 3.5 runs k independent
+ * Krylov solvers in lock-step (horizontal vectorisation); Section 5 needs many
+ * independent solves on levels of different size (multilevel Monte Carlo).
+ * Every iteration of all unfinished
  * samples is one persistent launch, and the iteration loop is captured in a
  * CUDA graph.  b[s], x[s]: device pointers (arrays of count pointers on the
  * host).  st: count entries (may be NULL).  Returns the first non-OK sample
@@ -176,20 +197,25 @@ int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count, const doub
 int dg_timing_enable(dg_mesh* mesh, int max_applies);
 int dg_timing_read(dg_mesh* mesh, int* n_applies, double* ms_pass1, double* ms_pass2);
 
-/* y = A(K) x in FP64, for callers that cannot allocate device memory (the
- * paper has no counterpart; this is a deployment variant of dg_apply).
- * Callers that cannot call cudaMalloc -- code inside a captured CUDA graph,
- * allocator-free runtimes, or frameworks that own every device allocation --
- * pass K (FP64 at the volume Gauss points, layout as dg_set_coefficient), x and
- * y (FP64, n_cells^3 (degree+1)^3 values, device pointers) and get y without
- * any allocation.  Temporaries live in a 64 MiB file-scope device array that
- * every GPU loading the library holds until exit; sizes whose temporaries do
- * not fit (about 75 bytes per DOF, e.g. more than 24^3 cells at degree 3)
- * return INVALID_ARG with the needed size.  The first call on a device looks up
- * the array's device address, so it should come before any stream capture.
- * The array is shared by all calls: calls that overlap on the GPU race.
- * Blocks until y is written (it reads back the K validity flag); K <= 0 or
- * non-finite returns INVALID_ARG.  Calls no cudaMalloc/cudaFree. */
+/* y = A(K) x in FP64, for callers that cannot allocate device memory.  The
+ * paper has no counterpart; this is a deployment variant of dg_apply (Section
+ * 3.3 application of the Section 4.1 form).  Some callers may not call
+ * cudaMalloc: allocator-free embedded or real-time runtimes that reserve all
+ * device memory when they start, and host frameworks that own every device
+ * allocation and forbid libraries to make their own.  dg_create_mesh allocates
+ * its workspaces, so these callers pass K (FP64 at the volume Gauss points,
+ * layout as dg_set_coefficient), x and y (FP64, n_cells^3 (degree+1)^3 values,
+ * device pointers owned by the caller) and get y without any allocation: the
+ * call makes no cudaMalloc, cudaFree or allocating library call.  Temporaries
+ * live in a 64 MiB file-scope device array that every GPU loading the library
+ * holds until exit; sizes whose temporaries do not fit (about 75 bytes per DOF,
+ * e.g. more than 24^3 cells at degree 3) return INVALID_ARG with the needed
+ * size.  The first call on a device looks up the array's device address, so it
+ * should come before any stream capture.  The array is shared by all calls and
+ * keeps the last call's contents: calls that overlap on the GPU race and must
+ * be serialised by the caller.  Blocks until y is written (it copies the K
+ * validity flag back to the host and synchronises `stream`); K <= 0 or
+ * non-finite returns INVALID_ARG. */
 int dg_apply_static(int n_cells, int degree, const double* K, const double* x, double* y,
                     void* stream);
 

@@ -32,7 +32,8 @@ Parity status: every public function is pinned by tests/test_oracle_pins.py
 (closed-form one-cell matrices, the Kronecker-sum identity, symmetry,
 positive definiteness and the continuum eigenvalue, consistency on harmonic
 polynomials, L2 convergence rates, Euler homogeneity and finite differences of
-the gradient, CG against a direct solve).
+the gradient, CG against a direct solve, and the per-cell face coefficient and
+face weights in closed form for a log K quadratic inside the cells).
 """
 from __future__ import annotations
 

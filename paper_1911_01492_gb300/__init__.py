@@ -156,7 +156,7 @@ class Mesh:
         self.n_cells_total = nc.value
         self.n = n1.value
         self.sigma = sg.value
-        self._coef_key = None
+        self._autograd_logK = None   # log K of the last coefficient set by autograd
 
     @property
     def handle(self):
@@ -176,9 +176,9 @@ class Mesh:
     # -- coefficient --------------------------------------------------------
     def set_coefficient(self, K, stream=None):
         """K: CUDA float64 tensor of n_dofs values at the volume Gauss points."""
+        self._autograd_logK = None
         _check(library().dg_set_coefficient(self._h, _ptr(K, _f64(), self.n_dofs, "K"),
                                             _stream(stream)), "dg_set_coefficient")
-        self._coef_key = (K.data_ptr(), K._version)
 
     # -- operator --------------------------------------------------------------
     def apply(self, x, y=None, stream=None, adjoint: bool = False):
@@ -285,9 +285,11 @@ def cg_solve_batched(meshes, bs, xs, rtol: float = 1e-8, maxit: int = 100000, st
 
 
 def apply_static(n_cells: int, degree: int, K, x, y=None, stream=None):
-    """y = A(K) x in FP64 without any device allocation by the library (its
-    temporaries live in a fixed 64 MiB device array; see dg_apply_static).
-    For callers that cannot allocate; everyone else should use Mesh."""
+    """y = A(K) x in FP64 with no device allocation by the library: its
+    temporaries live in a fixed 64 MiB device array (see dg_apply_static).
+    For callers that may not allocate device memory; everyone else should use
+    Mesh.  An allocation-free caller must pass y: with y=None this wrapper
+    allocates the output itself with torch.empty_like."""
     import torch
     nd = n_cells ** 3 * (degree + 1) ** 3
     if y is None:

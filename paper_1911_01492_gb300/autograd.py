@@ -1,8 +1,11 @@
 """Differentiable operator application and solve (torch.autograd.Function).
 
 Both functions take log K (the coefficient at the volume Gauss points, CUDA
-float64) as an input so that gradients flow to it; the mesh's coefficient is
-re-derived from it on every forward and backward call.
+float64) as an input so that gradients flow to it.  The mesh's coefficient is
+derived from it (dg_set_coefficient) only when it differs from the log K the
+mesh was last set from by these functions: each call compares log K exactly
+with a private copy of that last value (one device comparison), so repeated
+applies and solves with an unchanged coefficient skip the setup.
 
 apply(x, logK, mesh) = A(K) x
     d/dx:     A^T ybar                      (dg_apply_adjoint)
@@ -20,9 +23,17 @@ from . import DG_CG_FP64, DG_CG_PRECOND_JACOBI, Mesh
 
 
 def _ensure_coefficient(mesh: Mesh, logK: torch.Tensor):
-    # Always re-derive: a tensor's storage can change without its version
-    # counter (writes through .data), and the derivation costs one pass over K.
-    mesh.set_coefficient(torch.exp(logK.detach()).contiguous())
+    # An exact comparison with a private copy, not the version counter: a
+    # tensor's values can change without its version (writes through .data).
+    # Mesh.set_coefficient drops the copy, so a coefficient set directly by the
+    # caller is never mistaken for this one.
+    lk = logK.detach()
+    last = mesh._autograd_logK
+    if (last is not None and last.shape == lk.shape and last.device == lk.device
+            and torch.equal(last, lk)):
+        return
+    mesh.set_coefficient(torch.exp(lk).contiguous())
+    mesh._autograd_logK = lk.clone()
 
 
 class ApplyFn(torch.autograd.Function):

@@ -127,6 +127,17 @@ void dg_timing_mark(const dg_mesh* m, int slot, cudaStream_t s);
 #define DG_RED_THREADS 256
 #define DG_RED_SUMS 4     // most sums one reduction kernel may form (partials size)
 
+// coefficient setup kernels (dg_mesh.cu), shared with the allocation-free
+// apply: h w_q K and Kbar per cell (FP32 copy skipped when kt32 is NULL); h gamma
+// and d gamma / d log Kbar per face side (gh32 / dgam skipped when NULL)
+__global__ void k_coef_cells(const double* __restrict__ K, double* __restrict__ kt64,
+                             float* __restrict__ kt32, double* __restrict__ kbar,
+                             long long ncells, int n, double h, int* flag,
+                             const __grid_constant__ DGTab<double> tab);
+__global__ void k_coef_faces(const double* __restrict__ kbar, double* __restrict__ gh64,
+                             float* __restrict__ gh32, double* __restrict__ dgam, int Nc,
+                             double h);
+
 // error reporting (dg_mesh.cu)
 int dg_fail(int code, const char* fmt, ...);
 int dg_cuda_fail(cudaError_t e, const char* what);

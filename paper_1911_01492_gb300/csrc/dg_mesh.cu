@@ -31,8 +31,8 @@ extern "C" const char* dg_last_error(void) { return g_err; }
 // coefficient setup kernels
 // ---------------------------------------------------------------------------
 
-// One warp per cell: Kt = h w_q K (FP64 and FP32), Kbar = exp(sum_q w_q log K).
-// Invalid K (<= 0, NaN, inf) raises bit 0 of *flag.
+// One warp per cell: Kt = h w_q K (FP64, and FP32 unless kt32 is NULL),
+// Kbar = exp(sum_q w_q log K).  Invalid K (<= 0, NaN, inf) raises bit 0 of *flag.
 __global__ void k_coef_cells(const double* __restrict__ K, double* __restrict__ kt64,
                              float* __restrict__ kt32, double* __restrict__ kbar,
                              long long ncells, int n, double h, int* flag,
@@ -50,7 +50,7 @@ __global__ void k_coef_cells(const double* __restrict__ K, double* __restrict__ 
     if (!(Kq > 0.0) || !(Kq < INFINITY)) bad = true;
     const double v = h * wq * Kq;
     kt64[c * n3 + q] = v;
-    kt32[c * n3 + q] = (float)v;
+    if (kt32 != nullptr) kt32[c * n3 + q] = (float)v;
     acc += wq * log(Kq);
   }
   if (bad) atomicOr(flag, 1);
@@ -58,7 +58,8 @@ __global__ void k_coef_cells(const double* __restrict__ K, double* __restrict__ 
   if (lane == 0) kbar[c] = exp(acc);
 }
 
-// One thread per cell: h*gamma and d gamma / d log Kbar_c on its six faces.
+// One thread per cell: h*gamma (FP64, and FP32 unless gh32 is NULL) and, unless
+// dgam is NULL, d gamma / d log Kbar_c on its six faces.
 __global__ void k_coef_faces(const double* __restrict__ kbar, double* __restrict__ gh64,
                              float* __restrict__ gh32, double* __restrict__ dgam, int Nc,
                              double h) {
@@ -82,8 +83,8 @@ __global__ void k_coef_faces(const double* __restrict__ kbar, double* __restrict
       dg = k;
     }
     gh64[c * 6 + f] = h * g;
-    gh32[c * 6 + f] = (float)(h * g);
-    dgam[c * 6 + f] = dg;
+    if (gh32 != nullptr) gh32[c * 6 + f] = (float)(h * g);
+    if (dgam != nullptr) dgam[c * 6 + f] = dg;
   }
 }
 

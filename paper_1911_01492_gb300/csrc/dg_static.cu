@@ -1,27 +1,32 @@
 // dg_apply_static: the FP64 operator application for callers that cannot
-// allocate device memory.
+// allocate device memory.  The paper has no counterpart; this is a deployment
+// variant of dg_apply.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA graph that
-// is being captured or replayed, allocator-free embedded runtimes, or a host
-// framework that owns every device allocation and forbids libraries from making
-// their own.  dg_create_mesh allocates (coefficient data and workspaces), so
-// those callers get this entry point instead.  It takes the raw coefficient K,
-// the input x and the output y from the caller.  Its temporaries live in one
-// file-scope __device__ array of DG_STATIC_SCRATCH_BYTES:
+// Some callers may not call cudaMalloc: allocator-free embedded or real-time
+// runtimes that reserve all device memory when they start, and host frameworks
+// that own every device allocation and forbid libraries to make their own.
+// dg_create_mesh allocates (coefficient data and workspaces), so those callers
+// get this entry point instead.  It takes the raw coefficient K, the input x
+// and the output y from the caller, and calls no cudaMalloc, cudaFree or
+// allocating library routine.  Its temporaries live in one file-scope
+// __device__ array of DG_STATIC_SCRATCH_BYTES:
 //   the derived coefficients h w_q K, h gamma_F and the face-point weights,
 //   the per-cell Kbar,
 //   the validity flag,
 //   the nodal values, the x-modal values and the face traces of x.
 // Every GPU that loads the library holds this array until the process exits.
+// The coefficient kernels are the ones dg_set_coefficient runs (FP64 outputs
+// only); the two passes are the generic FP64 trace and cell kernels.
 //
 // Host code cannot use the array's name as a device address (it is a host-side
 // stand-in).  The first call on each device therefore looks up the array's
 // device address with cudaGetSymbolAddress, with that device current, and
-// caches it.  That first call should come before any stream capture.  Every
+// caches it; that first call should come before any stream capture.  Every
 // call shares the array and leaves its contents behind; the only value that
 // must start at zero, the flag, is cleared on every call.  Calls that overlap
 // on the GPU (on different streams or devices sharing a context) race on the
-// array and must be serialised by the caller.
+// array and must be serialised by the caller.  The call blocks: it copies the
+// K validity flag back to the host and synchronises the stream.
 #include <mutex>
 
 #include "dg_apply_impl.cuh"
@@ -54,50 +59,6 @@ int scratch_address(void** out) {
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
-
-// h w_q K and Kbar = exp(sum_q w_q log K), one warp per cell; bad K sets *flag.
-__global__ void k_static_cells(const double* __restrict__ K, double* __restrict__ kt,
-                               double* __restrict__ kbar, long long ncells, int n, double h,
-                               int* flag, const __grid_constant__ DGTab<double> tab) {
-  const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-  const int lane = threadIdx.x & 31;
-  if (c >= ncells) return;
-  const int n3 = n * n * n;
-  double acc = 0.0;
-  bool bad = false;
-  for (int q = lane; q < n3; q += 32) {
-    const int a = q % n, b = (q / n) % n, e = q / (n * n);
-    const double wq = tab.w[a] * tab.w[b] * tab.w[e];
-    const double Kq = K[c * n3 + q];
-    if (!(Kq > 0.0) || !(Kq < INFINITY)) bad = true;
-    kt[c * n3 + q] = h * wq * Kq;
-    acc += wq * log(Kq);
-  }
-  if (bad) atomicOr(flag, 1);
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if (lane == 0) kbar[c] = exp(acc);
-}
-
-// h gamma_F on the six faces of each cell (harmonic mean inside, Kbar on the boundary).
-__global__ void k_static_faces(const double* __restrict__ kbar, double* __restrict__ gh, int Nc,
-                               double h) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= (long long)Nc * Nc * Nc) return;
-  const int crd[3] = {(int)(c % Nc), (int)((c / Nc) % Nc), (int)(c / ((long long)Nc * Nc))};
-  const long long stride[3] = {1, Nc, (long long)Nc * Nc};
-  const double k = kbar[c];
-  for (int f = 0; f < 6; ++f) {
-    const int d = f >> 1;
-    const bool upper = f & 1;
-    const bool interior = upper ? (crd[d] < Nc - 1) : (crd[d] > 0);
-    double g = k;
-    if (interior) {
-      const double kn = kbar[upper ? c + stride[d] : c - stride[d]];
-      g = 2.0 * k * kn / (k + kn);
-    }
-    gh[c * 6 + f] = h * g;
-  }
-}
 
 template <int N>
 struct StaticApplyF {
@@ -150,6 +111,8 @@ extern "C" int dg_apply_static(int n_cells, int degree, const double* K, const d
   unsigned char* base = nullptr;
   int rc = scratch_address((void**)&base);
   if (rc) return rc;
+  rc = dg_prepare_apply_f64(n);  // kernel attributes only (no allocation)
+  if (rc) return rc;
   int* flag = (int*)(base + o_flag);
   double* kbar = (double*)(base + o_kbar);
   double* gh = (double*)(base + o_gh);
@@ -165,9 +128,11 @@ extern "C" int dg_apply_static(int n_cells, int degree, const double* K, const d
   dg_build_tables(n, 2.0 * n * n, &tab, &tab32);
   cudaStream_t s = (cudaStream_t)stream;
   DG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
-  k_static_cells<<<(unsigned)((ncells * 32 + 255) / 256), 256, 0, s>>>(K, kt, kbar, ncells, n, h,
-                                                                       flag, tab);
-  k_static_faces<<<(unsigned)((ncells + 255) / 256), 256, 0, s>>>(kbar, gh, n_cells, h);
+  // the coefficient kernels of dg_set_coefficient, FP64 outputs only
+  k_coef_cells<<<(unsigned)((ncells * 32 + 255) / 256), 256, 0, s>>>(K, kt, nullptr, kbar, ncells,
+                                                                     n, h, flag, tab);
+  k_coef_faces<<<(unsigned)((ncells + 255) / 256), 256, 0, s>>>(kbar, gh, nullptr, nullptr,
+                                                                n_cells, h);
   dgk::k_face_weights<double><<<(unsigned)((ncells + 255) / 256), 256, 0, s>>>(gh, FW, n_cells, n,
                                                                               tab);
   DG_CUDA(cudaGetLastError());

@@ -51,6 +51,35 @@ def test_apply_gradcheck_tiny(dg):
                                     atol=1e-7, rtol=1e-6)
 
 
+def test_coefficient_setup_runs_only_when_log_k_changes(dg, monkeypatch):
+    import torch
+    from paper_1911_01492_gb300 import autograd as dga
+    N, k = 3, 2
+    D = SIPG(N, k)
+    m = dg.Mesh(N, k)
+    calls = []
+    orig = m.set_coefficient
+    monkeypatch.setattr(m, "set_coefficient", lambda K, stream=None: (calls.append(1), orig(K, stream)))
+    K0 = inputs.lognormal_coefficient(N, k, seed=3)
+    x = torch.from_numpy(inputs.uniform_vector(N, k, 4)).cuda()
+    logK = torch.from_numpy(np.log(K0)).cuda().requires_grad_()
+    for _ in range(3):                       # unchanged log K: one setup in all
+        y = dga.apply(x, logK, m)
+    y.sum().backward()
+    assert len(calls) == 1
+    # a write that the version counter does not see still re-derives K
+    logK.data.add_(0.25)
+    y = dga.apply(x, logK, m)
+    assert len(calls) == 2
+    yref = D.apply(K0 * math.exp(0.25), x.cpu().numpy())
+    assert np.abs(y.detach().cpu().numpy() - yref).max() <= 1e-12 * np.abs(yref).max()
+    # a coefficient set directly by the caller is not mistaken for log K's
+    orig(torch.from_numpy(K0).cuda())
+    y = dga.apply(x, logK, m)
+    assert len(calls) == 3
+    assert np.abs(y.detach().cpu().numpy() - yref).max() <= 1e-12 * np.abs(yref).max()
+
+
 def observed_solution(D, K_ref_np, b, seed):
     A = D.assemble(K_ref_np).tocsc()
     u = spla.spsolve(A, b)

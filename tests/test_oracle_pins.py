@@ -476,3 +476,90 @@ def test_constant_modes_couple_with_two_point_flux_transmissibility():
                 assert abs(A[c * D.n3, c2 * D.n3] + D.sigma * T) <= 1e-12 * D.sigma * T
     # and the per-cell face coefficient of a cell-constant K is that constant
     assert np.abs(D.kbar(K) - Kc).max() <= 1e-14 * Kc.max()
+
+
+# --------------------------------------------------------------------------
+# Per-cell face coefficient Kbar_c = exp(sum_q w_q log K_{c,q}) with log K
+# varying inside the cells.  For log K = alpha + beta x^2 + delta y^2 + eps z^2
+# + mu y the Gauss-weighted mean over cell c (side h, corner h (cx, cy, cz)) is
+# exact (the n >= 2 point rule integrates quadratics); the cell averages of
+# (x/h)^2 and y/h are cx^2 + cx + 1/3 and cy + 1/2.  With n = 3 the Gauss
+# weights differ (4/9 vs 5/18), so an unweighted mean of log K along any axis
+# (which gives cx^2 + cx + 0.35), an arithmetic mean of K, or a mean over the
+# wrong array axis all miss these values.  The face weights are then fixed in
+# closed form: the constant modes of two neighbours couple only through the
+# penalty term, A[(c,0),(c',0)] = -sigma h gamma_F with
+# gamma_F = 2 Kbar Kbar' / (Kbar + Kbar'), and the constant mode's diagonal
+# entry is sigma h times the sum of gamma_F over its six faces (gamma_F = Kbar_c
+# on a boundary face).
+# --------------------------------------------------------------------------
+
+def _quadratic_log_coefficient(N, k, alpha, quad, mu):
+    """log K = alpha + quad[0] x^2 + quad[1] y^2 + quad[2] z^2 + mu y at the
+    Gauss points, in the [cell][e][b][a] layout."""
+    n = k + 1
+    t, _ = np.polynomial.legendre.leggauss(n)
+    xi = 0.5 * (t + 1.0)
+    h = 1.0 / N
+    logK = np.empty((N, N, N, n, n, n))        # [cz, cy, cx, e, b, a]
+    for cz in range(N):
+        for cy in range(N):
+            for cx in range(N):
+                X = h * (cx + xi)[None, None, :]
+                Y = h * (cy + xi)[None, :, None]
+                Z = h * (cz + xi)[:, None, None]
+                logK[cz, cy, cx] = (alpha + quad[0] * X ** 2 + quad[1] * Y ** 2
+                                    + quad[2] * Z ** 2 + mu * Y)
+    return logK.reshape(-1)
+
+
+def _closed_form_kbar(D, alpha, quad, mu):
+    h = D.h
+    out = {}
+    for c in range(D.n_cells_total):
+        crd = [int(v) for v in D.cell_coords(c)]
+        mean_sq = [h * h * (v * v + v + 1.0 / 3.0) for v in crd]
+        out[c] = math.exp(alpha + sum(a * m for a, m in zip(quad, mean_sq))
+                          + mu * h * (crd[1] + 0.5))
+    return out
+
+
+def test_kbar_is_the_gauss_weighted_geometric_mean_in_closed_form():
+    N, k = 2, 2
+    alpha, quad, mu = 0.3, (2.0, -1.1, 0.7), -1.5
+    D = SIPG(N, k)
+    K = np.exp(_quadratic_log_coefficient(N, k, alpha, quad, mu))
+    kb = D.kbar(K)
+    ref = _closed_form_kbar(D, alpha, quad, mu)
+    for c in range(D.n_cells_total):
+        assert abs(kb[c] - ref[c]) <= 1e-14 * ref[c], (c, kb[c], ref[c])
+
+
+def test_face_weights_of_a_varying_coefficient_in_closed_form():
+    N, k = 2, 2
+    alpha, quad, mu = -0.2, (1.7, 0.8, -1.3), 0.9
+    D = SIPG(N, k)
+    h, s = D.h, D.sigma
+    K = np.exp(_quadratic_log_coefficient(N, k, alpha, quad, mu))
+    kb = _closed_form_kbar(D, alpha, quad, mu)
+    A = D.assemble(K).tocsr()
+    n3 = D.n3
+    for c in range(D.n_cells_total):
+        coords = [int(v) for v in D.cell_coords(c)]
+        gsum = 0.0
+        for d in range(3):
+            for upper in (False, True):
+                inside = coords[d] < N - 1 if upper else coords[d] > 0
+                if inside:
+                    c2 = c + D.stride(d) if upper else c - D.stride(d)
+                    g = 2.0 * kb[c] * kb[c2] / (kb[c] + kb[c2])
+                    ref = -s * h * g
+                    assert abs(A[c * n3, c2 * n3] - ref) <= 1e-12 * abs(ref), (c, c2)
+                else:
+                    g = kb[c]
+                gsum += g
+        ref = s * h * gsum
+        assert abs(A[c * n3, c * n3] - ref) <= 1e-12 * ref, c
+    # the matrix-free apply uses the same face weights as the assembly
+    x = inputs.uniform_vector(N, k, 3)
+    assert np.abs(D.apply(K, x) - A @ x).max() <= 1e-12 * np.abs(A @ x).max()
