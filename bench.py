@@ -1,16 +1,29 @@
-"""Benchmark: FP64 SIPG-DG operator application throughput (GDOF/s) on the
-64^3 Q3 lognormal-K workload, plus CG time to a 1e-10 residual, mixed precision
-vs FP64, on 48^3 Q4.
+"""Benchmark of the matrix-free SIPG-DG hot path on one GB300.
 
-One step = one FP64 dg_apply (both passes) of the 64^3 Q3 operator over one
-synthetic input vector held in HBM.  Prints one JSON line on rank 0.
+Headline (`value`): FP64 dg_apply throughput in GDOF/s on the 64^3 Q3
+lognormal-K workload (16.8 M DOFs).  One step = one sweep of
+APPLIES_PER_STEP FP64 applies of that operator over one synthetic input vector
+held in HBM (inputs, workspaces and output each larger than L2).  The second
+half of the metric, CG time to a 1e-10 residual with mixed precision against
+FP64, is the `cg` object (48^3 Q4).  The other workloads of the method are
+separate keys of the same line: `config1` (8^3 Q2, K = 1: one apply in us and
+a manufactured-solution CG), `config2_cg` (the unpreconditioned FP64 CG on the
+64^3 Q3 operator), `config4` (32^3 Q3: apply, adjoint, coefficient gradient,
+differentiable apply and adjoint-CG gradient), `batched_cg` (the small level
+of the 256-sample batch, one batched solve against one solve per call), `mlmc`
+(one multilevel Monte-Carlo Estimate step for the mean inlet flux of the
+Section 5 flow problem over the three batched levels), and
+`oracle_legs` (the FP64 CPU oracle: one thread and all threads, CSR SpMV and
+CG where the matrix fits, projected CG elsewhere).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-cg]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--no-cg] [--no-extra] [--no-e2e] [--no-cpu-baseline]
 
-Under torchrun (N > 1) every rank applies its own replica of the operator
-(no data-path collective); `value` is the total DOFs of all ranks per second.
-`--impl reference` times the FP64 CPU oracle (element-wise, full 3D quadrature)
-on a bounded sample of the same workload on this host's cores.
+Prints one JSON line on rank 0.  Under torchrun (N > 1) every rank applies its
+own replica of the operator (no data-path collective); `value` is the total
+DOFs of all ranks per second.  `--impl reference` times the FP64 CPU oracle
+(element-wise, full 3D quadrature) on a bounded sample of the same workload on
+this host's cores.
 """
 from __future__ import annotations
 
@@ -18,26 +31,51 @@ import argparse
 import csv
 import io
 import json
+import math
 import os
 import statistics
 import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = {"n_cells": 64, "degree": 3, "K": "lognormal", "K_seed": 2, "x_seed": 3}
+APPLIES_PER_STEP = 32
 CG_WORKLOAD = {"n_cells": 48, "degree": 4, "K": "lognormal", "K_seed": 4, "rtol": 1e-10}
+CONFIG1 = {"n_cells": 8, "degree": 2, "x_seed": 1, "rtol": 1e-10}
+CONFIG4 = {"n_cells": 32, "degree": 3, "K_seed": 5, "x_seed": 6, "K_ref_seed": 40,
+           "noise_seed": 41, "rtol": 1e-10}
 # 256 lognormal samples on three uneven levels (multilevel Monte-Carlo shape)
 BATCH_LEVELS = [(128, 16, 2), (96, 24, 3), (32, 32, 4)]   # (samples, n_cells, degree)
 METRIC = "SIPG-DG apply GDOF/s (FP64)"
 NOMINAL_FP64_TFLOPS = 1.25   # GB300 FP64 rate: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
+# Executed FP64 operations of the apply kernels at Q3 (DFMA counted 2, DADD and
+# DMUL 1), from ncu's sm__sass_thread_inst_executed_op_{dfma,dadd,dmul} counters
+# on 32^3 and 40^3 launches, which fit (per cell, per interior face side)
+# exactly (profiles/apply_fp64_q3_executed_flops.md).  Set an entry to None
+# when its kernel changes until it is counted again.
+EXEC_FP64_Q3 = {"k_trace": (1792.0, 0.0), "k_cell_lo": (3440.0, 64.0)}
+
+
+def executed_fp64_per_dof(kernel: str, N: int, n: int):
+    """Executed FP64 operations per DOF of one launch on an N^3 mesh (Q3 only)."""
+    e = EXEC_FP64_Q3.get(kernel) if n == 4 else None
+    if e is None:
+        return None
+    per_cell, per_face_side = e
+    face_sides = 6 * N * N * (N - 1)       # interior faces, seen from both cells
+    return (per_cell * N ** 3 + per_face_side * face_sides) / (N ** 3 * n ** 3)
+
+
 # DRAM bytes (read + write) per DOF of one pass-2 launch (k_cell_lo<4,double>),
-# from an ncu capture of the 40^3 Q3 case (462.9 MB read + 27.4 MB written for
+# from an ncu capture of the 40^3 Q3 case (462.4 MB read + 27.6 MB written for
 # 4,096,000 DOFs), scaled by DOFs to the benchmark's launch; set to None when
 # the kernel changes until it is captured again.
-K_CELL_TRAFFIC_PER_DOF = (462.859264e6 + 27.433984e6) / 4096000
+K_CELL_TRAFFIC_PER_DOF = (462.4e6 + 27.6e6) / 4096000
 
 
 def flops_per_dof(n: int):
@@ -214,19 +252,29 @@ def run_reference(args, world, rank):
 
 
 # ---------------------------------------------------------------------------
-def time_applies(m, x, y, steps, warmup, world):
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def time_applies(m, x, y, steps, warmup, world, per_step=APPLIES_PER_STEP):
+    """`steps` timed sweeps of `per_step` FP64 applies after `warmup` untimed
+    sweeps; CUDA events on the launching stream, per-pass events inside the
+    library (dg_timing_enable) for the roofline."""
     import torch
     for _ in range(warmup):
-        m.apply(x, y)
+        for _ in range(per_step):
+            m.apply(x, y)
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
-    m.timing_enable(steps)
+    m.timing_enable(steps * per_step)
     s = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events()
     e0.record(s)
     for _ in range(steps):
-        m.apply(x, y)
+        for _ in range(per_step):
+            m.apply(x, y)
     e1.record(s)
     torch.cuda.synchronize()
     barrier(world)
@@ -235,7 +283,9 @@ def time_applies(m, x, y, steps, warmup, world):
     return ms, napp, ms1, ms2
 
 
-def time_e2e(m, xh, yh, steps, warmup, world):
+def time_e2e(m, xh, yh, steps, warmup, world, per_step=APPLIES_PER_STEP):
+    """The same sweeps through the host-buffer entry point: every apply copies
+    x in from pinned host memory and y back out, inside the timed region."""
     import torch
     for _ in range(warmup):
         m.apply_host(xh, yh)
@@ -243,14 +293,53 @@ def time_e2e(m, xh, yh, steps, warmup, world):
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(steps):
-        m.apply_host(xh, yh)      # H2D x, apply, D2H y, synchronise
+        for _ in range(per_step):
+            m.apply_host(xh, yh)      # H2D x, apply, D2H y, synchronise
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     barrier(world)
     return dt
 
 
-def run_cg(world):
+def time_setup(m, Kd, reps=3):
+    """Wall time of dg_set_coefficient (coefficient kernels, line operators,
+    face weights and its blocking validity check), best of reps."""
+    import torch
+    best = 1e300
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.set_coefficient(Kd)
+        torch.cuda.synchronize()
+        best = min(best, time.perf_counter() - t0)
+    return best * 1e3
+
+
+def time_gpu_calls(fn, reps, warmup=3):
+    """Mean ms of fn() over reps calls (CUDA events on the current stream)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = _events()
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _solve_entry(st, world):
+    return {"seconds": max_over_ranks(st["seconds"], world), "iterations": st["iterations"],
+            "outer": st["outer_iterations"], "rel_residual": st["rel_residual"],
+            "status": st["status"]}
+
+
+def run_cg(world, modes=None):
+    """Config 3: 48^3 Q4 lognormal K, f = 1; FP64 CG against the mixed CG to
+    a 1e-10 FP64-recomputed residual, without and with M = diag(A)."""
     import torch
     import paper_1911_01492_gb300 as dg
     from paper_1911_01492_gb300 import inputs
@@ -263,9 +352,12 @@ def run_cg(world):
     out = {"workload": f"{N}^3 Q{k} SIPG-DG, lognormal K (seed 4), f = 1, "
                        f"{m.n_dofs} DOFs, to rel. residual {CG_WORKLOAD['rtol']:g} "
                        "recomputed in FP64; Jacobi times include forming diag(A)"}
-    for name, mode in (("mixed_ir", dg.DG_CG_MIXED_IR), ("fp64", dg.DG_CG_FP64),
-                       ("mixed_ir_jacobi", dg.DG_CG_MIXED_IR | dg.DG_CG_PRECOND_JACOBI),
-                       ("fp64_jacobi", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_JACOBI)):
+    modes = modes or (("mixed_ir", dg.DG_CG_MIXED_IR), ("fp64", dg.DG_CG_FP64),
+                      ("mixed_ir_jacobi", dg.DG_CG_MIXED_IR | dg.DG_CG_PRECOND_JACOBI),
+                      ("fp64_jacobi", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_JACOBI),
+                      ("mixed_ir_restart_jacobi",
+                       dg.DG_CG_MIXED_IR_RESTART | dg.DG_CG_PRECOND_JACOBI))
+    for name, mode in modes:
         if mode & dg.DG_CG_PRECOND_JACOBI:
             m.set_coefficient(Kd)  # drops the cached diagonal: the solve forms it
         x = torch.zeros_like(b)
@@ -273,14 +365,137 @@ def run_cg(world):
         barrier(world)
         _, st = m.cg_solve(b, x, rtol=CG_WORKLOAD["rtol"], maxit=200000, mode=mode,
                            raise_on_error=False)
-        out[name] = {"seconds": max_over_ranks(st["seconds"], world),
-                     "iterations": st["iterations"], "outer": st["outer_iterations"],
-                     "rel_residual": st["rel_residual"], "status": st["status"]}
+        out[name] = _solve_entry(st, world)
     if out["fp64"]["status"] == 0 and out["mixed_ir"]["status"] == 0:
         out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed_ir"]["seconds"]
     if out["fp64_jacobi"]["status"] == 0 and out["mixed_ir_jacobi"]["status"] == 0:
         out["speedup_mixed_vs_fp64_jacobi"] = (out["fp64_jacobi"]["seconds"]
                                                / out["mixed_ir_jacobi"]["seconds"])
+    m.close()
+    return out, K
+
+
+def run_config2_cg(m, world):
+    """Config 2's solve: the unpreconditioned FP64 CG (and the mixed CG) on the
+    64^3 Q3 lognormal operator, f = 1, to 1e-10."""
+    import torch
+    import paper_1911_01492_gb300 as dg
+    from paper_1911_01492_gb300 import inputs
+    N, k = m.n_cells, m.degree
+    b = torch.from_numpy(inputs.constant_load_vector(N, k)).cuda()
+    out = {"workload": f"{N}^3 Q{k} SIPG-DG, lognormal K (seed 2), f = 1, {m.n_dofs} DOFs, "
+                       "to rel. residual 1e-10 recomputed in FP64, M = I"}
+    for name, mode in (("fp64", dg.DG_CG_FP64), ("mixed_ir", dg.DG_CG_MIXED_IR)):
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        barrier(world)
+        _, st = m.cg_solve(b, x, rtol=1e-10, maxit=200000, mode=mode, raise_on_error=False)
+        out[name] = _solve_entry(st, world)
+    if out["fp64"]["status"] == 0 and out["mixed_ir"]["status"] == 0:
+        out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed_ir"]["seconds"]
+    return out
+
+
+def manufactured_source(x, y, z):
+    """f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) for u = sin(pi x) sin(pi y) sin(pi z), K = 1."""
+    return 3.0 * math.pi ** 2 * (np.sin(math.pi * x) * np.sin(math.pi * y)
+                                 * np.sin(math.pi * z))
+
+
+def run_config1(world):
+    """Config 1: 8^3 Q2, K = 1.  One FP64 apply in microseconds (mean over
+    many launches), and the FP64 and mixed CG to 1e-10 for the manufactured
+    right-hand side (formed by dg_load_vector from f at the Gauss points)."""
+    import torch
+    import paper_1911_01492_gb300 as dg
+    from paper_1911_01492_gb300 import inputs
+    N, k = CONFIG1["n_cells"], CONFIG1["degree"]
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(inputs.unit_coefficient(N, k)).cuda())
+    x = torch.from_numpy(inputs.uniform_vector(N, k, CONFIG1["x_seed"])).cuda()
+    y = torch.empty_like(x)
+    us = 1e3 * time_gpu_calls(lambda: m.apply(x, y), 2000, warmup=20)
+    f = torch.from_numpy(inputs.values_at_gauss_points(N, k, manufactured_source)).cuda()
+    b = m.load_vector(f)
+    out = {"workload": f"{N}^3 Q{k}, K = 1, {m.n_dofs} DOFs; x ~ U[-1,1] (seed 1); "
+                       "f = 3 pi^2 sin sin sin",
+           "apply_us": us, "apply_gdof_s": m.n_dofs / (us * 1e-6) / 1e9}
+    for name, mode in (("fp64", dg.DG_CG_FP64), ("mixed_ir", dg.DG_CG_MIXED_IR)):
+        xs = torch.zeros_like(b)
+        m.cg_solve(b, xs, rtol=CONFIG1["rtol"], maxit=10000, mode=mode, raise_on_error=False)
+        xs.zero_()
+        torch.cuda.synchronize()
+        _, st = m.cg_solve(b, xs, rtol=CONFIG1["rtol"], maxit=10000, mode=mode,
+                           raise_on_error=False)
+        out["cg_" + name] = _solve_entry(st, world)
+    m.close()
+    return out
+
+
+def run_config4(world):
+    """Config 4: 32^3 Q3 lognormal K.  Mean ms of dg_apply, dg_apply_adjoint,
+    dg_coeff_grad, the differentiable apply (forward + backward) with the
+    coefficient cached and with it re-derived on every call, and one gradient of
+    L = 0.5 ||u(K) - u_obs||^2 by the adjoint CG (forward and adjoint solves,
+    FP64 with M = diag(A), to 1e-10)."""
+    import torch
+    import paper_1911_01492_gb300 as dg
+    from paper_1911_01492_gb300 import autograd as dga
+    from paper_1911_01492_gb300 import inputs
+    c = CONFIG4
+    N, k = c["n_cells"], c["degree"]
+    K = inputs.lognormal_coefficient(N, k, seed=c["K_seed"])
+    Kd = torch.from_numpy(K).cuda()
+    m = dg.Mesh(N, k)
+    out = {"workload": f"{N}^3 Q{k}, lognormal K (seed 5), {N ** 3 * (k + 1) ** 3} DOFs"}
+    out["setup_ms"] = time_setup(m, Kd)
+    x = torch.from_numpy(inputs.uniform_vector(N, k, c["x_seed"])).cuda()
+    v = torch.from_numpy(inputs.uniform_vector(N, k, c["x_seed"] + 1)).cuda()
+    y = torch.empty_like(x)
+    g = torch.empty_like(x)
+    reps = 50
+    out["apply_ms"] = time_gpu_calls(lambda: m.apply(x, y), reps)
+    out["apply_adjoint_ms"] = time_gpu_calls(lambda: m.apply_adjoint(x, y), reps)
+    out["coeff_grad_ms"] = time_gpu_calls(lambda: m.coeff_grad(x, v, g), reps)
+    logK = torch.log(Kd).requires_grad_()
+    xg = x.clone().requires_grad_()
+
+    def fwd_bwd(lk):
+        yy = dga.apply(xg, lk, m)
+        (yy * v).sum().backward()
+    out["autograd_apply_fwd_bwd_ms_cached"] = time_gpu_calls(lambda: fwd_bwd(logK), 20)
+    logK2 = (logK.detach() + 1e-3).requires_grad_()
+    flip = [logK, logK2]
+    state = {"i": 0}
+
+    def alternating():
+        state["i"] ^= 1
+        fwd_bwd(flip[state["i"]])
+    out["autograd_apply_fwd_bwd_ms_rederived"] = time_gpu_calls(alternating, 10)
+    # the loss gradient by the adjoint CG
+    b = torch.from_numpy(inputs.constant_load_vector(N, k)).cuda()
+    mref = dg.Mesh(N, k)
+    mref.set_coefficient(torch.from_numpy(
+        inputs.lognormal_coefficient(N, k, seed=c["K_ref_seed"])).cuda())
+    # the reference state to 1e-11: FP64 CG stagnates near 5e-12 on this field
+    uref, _ = mref.cg_solve(b, rtol=1e-11, maxit=100000,
+                            mode=dg.DG_CG_FP64 | dg.DG_CG_PRECOND_JACOBI, raise_on_error=False)
+    mref.close()
+    rng = np.random.default_rng(c["noise_seed"])
+    ur = uref.cpu().numpy()
+    uobs = torch.from_numpy(ur + 0.01 * np.sqrt(np.mean(ur ** 2))
+                            * rng.standard_normal(ur.shape)).cuda()
+    lk = torch.log(Kd).requires_grad_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    u = dga.solve(b, lk, m, rtol=c["rtol"], precond="jacobi")
+    loss = 0.5 * ((u - uobs) ** 2).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    out["loss_gradient_adjoint_cg_s"] = time.perf_counter() - t0
+    out["loss_gradient_note"] = ("forward CG + adjoint CG + dg_coeff_grad, FP64 with "
+                                 "M = diag(A), rtol 1e-10, coefficient derived once")
+    out["dlogK_norm"] = float(lk.grad.norm())
     m.close()
     return out
 
@@ -338,18 +553,23 @@ def _timed_sequential(meshes, bs, sizes, picked):
     return {"samples": len(picked), "seconds": t, "gdof_per_s": work / t / 1e9}
 
 
-def run_batched(world, rank, sequential_samples: int = 1, full: bool = False):
+def run_batched(world, rank, sequential_samples: int = 1, full: bool = False,
+                larger_levels: bool = True):
     """Batched lock-step CG (FP64, rtol 1e-8) on the 256-sample workload.
 
     Always: the 128 small samples (16^3 Q2) in one batched solve against 16 of
-    them solved one per dg_cg_solve call, and one-per-call rates of the larger
-    levels, and the small batch again with M = diag(A_s).  With full = True
-    also the whole 256-sample batch, without and with M (minutes).
+    them solved one per dg_cg_solve call, and the small batch again with
+    M = diag(A_s).  With larger_levels: one-per-call rates of the larger
+    levels.  With full = True also the whole 256-sample batch, without and
+    with M (minutes).
     """
+    import torch
     out = {"workload": "256 lognormal-K samples: 128 x 16^3 Q2, 96 x 24^3 Q3, 32 x 32^3 Q4 "
                        "(230,162,432 DOFs), FP64 CG to 1e-8; seeds 1000 + sample"}
     small = [BATCH_LEVELS[0]]
     meshes, bs, xs, sizes = _batch_meshes(small)
+    # the first call tunes the launch shape; time the second
+    _timed_batched(meshes[:8], bs[:8], xs[:8], sizes[:8], world)
     out["small_level_batched"] = _timed_batched(meshes, bs, xs, sizes, world)
     out["small_level_one_per_call"] = _timed_sequential(
         meshes, bs, sizes, list(range(min(len(meshes), 16))))
@@ -360,16 +580,17 @@ def run_batched(world, rank, sequential_samples: int = 1, full: bool = False):
                                                        precond="jacobi")
     for m in meshes:
         m.close()
-    rates = {}
-    start = 0
-    for count, N, k in BATCH_LEVELS[1:]:
-        ms_, bs_, xs_, sz_ = _batch_meshes([(min(count, sequential_samples), N, k)],
-                                           seed0=1000 + BATCH_LEVELS[0][0] + start)
-        rates[f"{N}^3 Q{k}"] = _timed_sequential(ms_, bs_, sz_, list(range(len(ms_))))
-        start += count
-        for m in ms_:
-            m.close()
-    out["one_per_call_larger_levels"] = rates
+    if larger_levels:
+        rates = {}
+        start = 0
+        for count, N, k in BATCH_LEVELS[1:]:
+            ms_, bs_, xs_, sz_ = _batch_meshes([(min(count, sequential_samples), N, k)],
+                                               seed0=1000 + BATCH_LEVELS[0][0] + start)
+            rates[f"{N}^3 Q{k}"] = _timed_sequential(ms_, bs_, sz_, list(range(len(ms_))))
+            start += count
+            for m in ms_:
+                m.close()
+        out["one_per_call_larger_levels"] = rates
     if full:
         meshes, bs, xs, sizes = _batch_meshes(BATCH_LEVELS)
         out["full_batch"] = _timed_batched(meshes, bs, xs, sizes, world)
@@ -377,16 +598,125 @@ def run_batched(world, rank, sequential_samples: int = 1, full: bool = False):
                                                   precond="jacobi")
         for m in meshes:
             m.close()
+    torch.cuda.empty_cache()
     return out
 
 
-def run_cg_probe(iters: int):
+def run_mlmc(world):
+    """Section 5: one Estimate step of MLMC for the mean inlet flux of the flow
+    problem (p = 1 at x = 0, p = 0 at x = 1, zero flux elsewhere; lognormal k,
+    correlation length 0.1, variance 1) on the batched levels 16^3 Q2, 24^3 Q3,
+    32^3 Q4 with 32 / 8 / 4 coupled samples; every solve in the batched FP64 CG
+    with M = diag(A) to 1e-10.  Reports the estimate, the level variances and
+    costs, and the samples the allocation rule asks for at eps = 0.01."""
+    from paper_1911_01492_gb300 import mlmc
+    levels = [(N, k) for _, N, k in BATCH_LEVELS]
+    t0 = time.perf_counter()
+    r = mlmc.estimate(levels, eps=0.01, n_init=[32, 8, 4], max_cycles=1, seed0=9000,
+                      pool=32)
+    r["wall_s"] = time.perf_counter() - t0
+    r.pop("Y", None)
+    return r
+
+
+# ---------------------------------------------------------------------------
+# Oracle legs (FP64 CPU oracle on this host; rank 0 only)
+# ---------------------------------------------------------------------------
+def _oracle_apply_rate(N, k, K, x, ncell, target_s):
+    """GDOF/s of the oracle's element-wise apply on `ncell` random cells of the
+    mesh, repeated for about target_s seconds."""
+    from oracle import SIPG
+    D = SIPG(N, k)
+    n3 = (k + 1) ** 3
+    rng = np.random.default_rng(1)
+    cells = rng.choice(N ** 3, min(ncell, N ** 3), replace=False)
+    D.apply(K, x, cells=cells[:64])
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        D.apply(K, x, cells=cells)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= target_s:
+            break
+    return reps * len(cells) * n3 / dt / 1e9
+
+
+def oracle_leg_main(args):
+    """Child process of the one-thread oracle leg (BLAS limited to one thread
+    through the environment): apply rate on a sample of the apply workload."""
+    N, k = WORKLOAD["n_cells"], WORKLOAD["degree"]
+    K, x = make_inputs(N, k, WORKLOAD["K_seed"], WORKLOAD["x_seed"])
+    rate = _oracle_apply_rate(N, k, K, x, 2048, 4.0)
+    print(json.dumps({"gdof_per_s": rate, "cells": 2048}), flush=True)
+
+
+def run_oracle_legs(cpu_all_threads, cg3, cg2, cfg1, K48=None):
+    """The FP64 CPU oracle on this host, beside the GPU numbers:
+    one thread vs all threads (element-wise apply of the 64^3 Q3 workload),
+    config 1 with the assembled CSR matrix (SpMV rate, CG to 1e-10 in full),
+    and projected CG times (apply time per iteration x the GPU's iteration
+    count) where the CSR matrix would not fit."""
+    from oracle import SIPG, cg
+    out = {"cores_all": cpu_threads()}
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-leg"],
+                           capture_output=True, text=True, env=env, timeout=300)
+        one = json.loads(r.stdout.strip().splitlines()[-1])
+        out["apply_64q3_one_thread_gdof_s"] = one["gdof_per_s"]
+        out["apply_64q3_one_thread_sample"] = f"{one['cells']} random cells, ~4 s"
+    except Exception as e:  # reported, not fatal: the GPU numbers stand alone
+        out["apply_64q3_one_thread_error"] = repr(e)[:200]
+    if cpu_all_threads is not None:
+        out["apply_64q3_all_threads_gdof_s"] = cpu_all_threads["value"]
+    # config 1: CSR assembled in full
+    from paper_1911_01492_gb300 import inputs
+    N, k = CONFIG1["n_cells"], CONFIG1["degree"]
+    D = SIPG(N, k)
+    K1 = inputs.unit_coefficient(N, k)
+    t0 = time.perf_counter()
+    A = D.assemble(K1)
+    out["config1_csr_assembly_s"] = time.perf_counter() - t0
+    out["config1_csr_nnz"] = int(A.nnz)
+    x1 = inputs.uniform_vector(N, k, CONFIG1["x_seed"])
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < 1.0:
+        A @ x1
+        reps += 1
+    dt = time.perf_counter() - t0
+    out["config1_csr_spmv_us"] = 1e6 * dt / reps
+    out["config1_csr_spmv_gdof_s"] = reps * D.n_dofs / dt / 1e9
+    b1 = D.load_vector(manufactured_source)
+    t0 = time.perf_counter()
+    _, it, rel, _ = cg(lambda v: A @ v, b1, rtol=CONFIG1["rtol"], maxit=10000)
+    out["config1_csr_cg"] = {"seconds": time.perf_counter() - t0, "iterations": it,
+                             "rel_residual": rel}
+    # projected CG: element-wise apply per iteration x GPU iterations
+    if cpu_all_threads is not None and cg2 is not None and "fp64" in cg2:
+        sec_per_apply = 16777216 / (cpu_all_threads["value"] * 1e9)
+        out["config2_cg_fp64_projected_s"] = sec_per_apply * cg2["fp64"]["iterations"]
+    if cg3 is not None and K48 is not None:
+        N3, k3 = CG_WORKLOAD["n_cells"], CG_WORKLOAD["degree"]
+        x3 = inputs.uniform_vector(N3, k3, 9)
+        rate = _oracle_apply_rate(N3, k3, K48, x3, 8192, 3.0)
+        out["apply_48q4_all_threads_gdof_s"] = rate
+        nd = N3 ** 3 * (k3 + 1) ** 3
+        out["config3_cg_fp64_projected_s"] = nd / (rate * 1e9) * cg3["fp64"]["iterations"]
+        out["config3_cg_fp64_jacobi_projected_s"] = (nd / (rate * 1e9)
+                                                     * cg3["fp64_jacobi"]["iterations"])
+    out["projection"] = ("oracle element-wise apply time of the whole mesh x the GPU "
+                         "solver's iteration count (vector operations not counted)")
+    return out
+
+
+def run_cg_probe(iters: int, n_cells: int = 0):
     """A fixed number of iterations of the mixed and FP64 CG on the CG
-    workload (48^3 Q4), with wall times; for kernel launch lists."""
+    workload (48^3 Q4, or n_cells^3 Q4), with wall times; for kernel profiles."""
     import torch
     import paper_1911_01492_gb300 as dg
     from paper_1911_01492_gb300 import inputs
-    N, k = CG_WORKLOAD["n_cells"], CG_WORKLOAD["degree"]
+    N, k = n_cells or CG_WORKLOAD["n_cells"], CG_WORKLOAD["degree"]
     m = dg.Mesh(N, k)
     m.set_coefficient(torch.from_numpy(inputs.lognormal_coefficient(N, k, seed=CG_WORKLOAD["K_seed"])).cuda())
     b = torch.from_numpy(inputs.constant_load_vector(N, k)).cuda()
@@ -400,34 +730,99 @@ def run_cg_probe(iters: int):
               flush=True)
 
 
+def roofline_entry(N, n, nd, napp, ms1, ms2, ms_step, peak_fp64):
+    """Roofline of the dominant apply kernel against the FP64 pipe: executed
+    FP64 operations (ncu counts per DOF) per launch over its CUDA-event
+    duration, divided by the FP64 rate measured in this run."""
+    f1, f2 = flops_per_dof(n)
+    t1, t2 = ms1 / max(napp, 1), ms2 / max(napp, 1)
+    if t2 >= t1:
+        dom_ms, dom_alg, dom_name, slot = t2, f2 * nd, "k_cell_lo", "k_cell_lo"
+    else:
+        dom_ms, dom_alg, dom_name, slot = t1, f1 * nd, "k_trace", "k_trace"
+    exec_per_dof = executed_fp64_per_dof(slot, N, n)
+    other = "k_trace" if slot == "k_cell_lo" else "k_cell_lo"
+    exec_other = executed_fp64_per_dof(other, N, n)
+    alg_tflops = dom_alg / (dom_ms * 1e-3) / 1e12
+    r = {"bound": "alu", "kernel": dom_name, "unit": "TFLOP/s",
+         "pass_ms": {"k_trace": t1, "k_cell_lo": t2},
+         "algorithmic_tflops": alg_tflops,
+         "apply_tflops_algorithmic": (f1 + f2) * nd / (ms_step * 1e-3 / APPLIES_PER_STEP) / 1e12,
+         "peak_nominal": NOMINAL_FP64_TFLOPS,
+         "peak_source": "FP64 DFMA throughput measured in this run by dg_peak_probe "
+                        "(best of 6 launches filling every SM); nominal 1.25"}
+    if exec_per_dof is not None:
+        achieved = exec_per_dof * nd / (dom_ms * 1e-3) / 1e12
+        r.update({"achieved": achieved, "peak": peak_fp64, "frac": achieved / peak_fp64,
+                  "executed_flops_per_dof": exec_per_dof,
+                  "frac_of_nominal": achieved / NOMINAL_FP64_TFLOPS,
+                  "achieved_source": "executed FP64 operations per DOF from ncu instruction "
+                                     "counters (DFMA x2 + DADD + DMUL) x DOFs / live "
+                                     "CUDA-event duration of the kernel"})
+    else:
+        r.update({"achieved": alg_tflops, "peak": peak_fp64, "frac": alg_tflops / peak_fp64,
+                  "achieved_source": "algorithmic flops (no executed-operation count for "
+                                     "this kernel build)"})
+    if exec_other is not None:
+        t_other = t1 if other == "k_trace" else t2
+        r["other_kernel"] = {"kernel": other, "executed_flops_per_dof": exec_other,
+                             "achieved": exec_other * nd / (t_other * 1e-3) / 1e12,
+                             "frac": exec_other * nd / (t_other * 1e-3) / 1e12 / peak_fp64}
+    traffic = (K_CELL_TRAFFIC_PER_DOF * nd
+               if (dom_name == "k_cell_lo" and n == 4 and K_CELL_TRAFFIC_PER_DOF) else None)
+    r["traffic"] = traffic
+    r["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the pass-2 "
+                           "kernel on 40^3 Q3, scaled by DOFs")
+    return r
+
+
+def _leg(fn, *a, **kw):
+    """Run one auxiliary measurement; a failure is reported in its key instead
+    of ending the benchmark (the headline numbers stand on their own)."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:  # noqa: BLE001 - reported in the JSON line
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": repr(e)[:300]}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution part")
+    ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution parts")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip configs 1 and 4, the batched small level and the oracle legs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--batched", action="store_true",
-                    help="also run the 256-sample batched CG workload")
+                    help="also run the larger batched levels one per call")
     ap.add_argument("--batched-sequential", type=int, default=1,
                     help="samples of each larger level solved one per call for reference")
     ap.add_argument("--cg-probe", type=int, default=0, metavar="ITERS",
                     help="only run ITERS iterations of each CG mode on the CG workload "
                          "(for kernel profiles) and exit")
+    ap.add_argument("--cg-probe-cells", type=int, default=0, metavar="N",
+                    help="with --cg-probe: run it on an N^3 Q4 mesh instead of 48^3")
     ap.add_argument("--batched-full", action="store_true",
                     help="with --batched: also solve the whole 256-sample batch (minutes)")
     ap.add_argument("--n-cells", type=int, default=WORKLOAD["n_cells"],
                     help="cells per direction (default: the 64^3 workload)")
     ap.add_argument("--degree", type=int, default=WORKLOAD["degree"])
+    ap.add_argument("--oracle-leg", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
 
     WORKLOAD["n_cells"], WORKLOAD["degree"] = args.n_cells, args.degree
+    if args.oracle_leg:
+        oracle_leg_main(args)
+        return
     world, rank, local = dist_setup()
     if args.cg_probe:
-        run_cg_probe(args.cg_probe)
+        run_cg_probe(args.cg_probe, args.cg_probe_cells)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -437,9 +832,12 @@ def main(argv=None):
     import paper_1911_01492_gb300 as dg
     N, k = WORKLOAD["n_cells"], WORKLOAD["degree"]
     n = k + 1
+    t_start = time.perf_counter()
     K, x = make_inputs(N, k, WORKLOAD["K_seed"], WORKLOAD["x_seed"])
+    peak_fp64 = dg.peak_probe("fp64")
     m = dg.Mesh(N, k)
-    m.set_coefficient(torch.from_numpy(K).cuda())
+    Kd = torch.from_numpy(K).cuda()
+    setup_ms = time_setup(m, Kd)
     xd = torch.from_numpy(x).cuda()
     yd = torch.empty_like(xd)
     nd = m.n_dofs
@@ -448,52 +846,48 @@ def main(argv=None):
         ms, napp, ms1, ms2 = time_applies(m, xd, yd, args.steps, args.warmup, world)
     ms = max_over_ranks(ms, world)
     ms_step = ms / args.steps
-    value = world * nd / (ms_step * 1e-3) / 1e9
-
-    # roofline of the dominant kernel (pass 2, the cell kernel): FP64 pipe
-    f1, f2 = flops_per_dof(n)
-    t1, t2 = ms1 / max(napp, 1), ms2 / max(napp, 1)
-    dom_ms, dom_flops, dom_name = ((t2, f2 * nd, "k_cell_lo") if t2 >= t1
-                                   else (t1, f1 * nd, "k_trace"))
-    achieved = dom_flops / (dom_ms * 1e-3) / 1e12
-    traffic = (K_CELL_TRAFFIC_PER_DOF * nd
-               if (dom_name == "k_cell_lo" and n == 4 and K_CELL_TRAFFIC_PER_DOF) else None)
-    roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved,
-                "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
-                                  "pass-2 kernel on 40^3 Q3, scaled by DOFs",
-                "peak_source": "nominal GB300 FP64 rate (derived: 152 SMs x 2 DFMA/clk x 2 x "
-                               "2.06 GHz); a DFMA throughput probe measured 1.0 TFLOP/s",
-                "pass_ms": {"k_trace": t1, "k_cell_lo": t2},
-                "apply_tflops_algorithmic": (f1 + f2) * nd / (ms_step * 1e-3) / 1e12}
+    value = world * nd * APPLIES_PER_STEP / (ms_step * 1e-3) / 1e9
+    roofline = roofline_entry(N, n, nd, napp, ms1, ms2, ms_step, peak_fp64)
 
     # end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
         xh = torch.from_numpy(x).pin_memory()
         yh = torch.empty_like(xh).pin_memory()
-        e2e_steps = max(3, min(args.steps, 20))
+        e2e_steps = max(1, min(args.steps, 20)) if args.steps >= 1 else 1
         dt = time_e2e(m, xh, yh, e2e_steps, 2, world)
         dt = max_over_ranks(dt, world)
-        e2e = {"value": world * nd * e2e_steps / dt / 1e9, "unit": "GDOF/s",
-               "h2d_bytes_per_step": xh.numel() * 8, "d2h_bytes_per_step": yh.numel() * 8}
+        e2e = {"value": world * nd * e2e_steps * APPLIES_PER_STEP / dt / 1e9, "unit": "GDOF/s",
+               "h2d_bytes_per_step": xh.numel() * 8 * APPLIES_PER_STEP,
+               "d2h_bytes_per_step": yh.numel() * 8 * APPLIES_PER_STEP,
+               "steps": e2e_steps}
+        del xh, yh
 
-    cg = None
+    cg2 = cg = K48 = None
     if not args.no_cg:
-        m.close()
-        del xd, yd
-        torch.cuda.empty_cache()
-        cg = run_cg(world)
+        cg2 = _leg(run_config2_cg, m, world)
+    m.close()
+    del xd, yd, Kd
+    torch.cuda.empty_cache()
+    if not args.no_cg:
+        r = _leg(run_cg, world)
+        cg, K48 = r if isinstance(r, tuple) else (r, None)
 
-    batched = None
-    if args.batched:
-        torch.cuda.empty_cache()
-        batched = run_batched(world, rank, args.batched_sequential, args.batched_full)
+    cfg1 = cfg4 = batched = mlmc_r = None
+    if not args.no_extra:
+        cfg1 = _leg(run_config1, world)
+        cfg4 = _leg(run_config4, world)
+        batched = _leg(run_batched, world, rank, args.batched_sequential, args.batched_full,
+                       larger_levels=args.batched)
+        mlmc_r = _leg(run_mlmc, world)
+    elif args.batched or args.batched_full:
+        batched = _leg(run_batched, world, rank, args.batched_sequential, args.batched_full)
 
-    cpu = None
+    cpu = legs = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(K, x, N, k)
+    if rank == 0 and not args.no_extra and not args.no_cpu_baseline:
+        legs = _leg(run_oracle_legs, cpu, cg, cg2, cfg1, K48)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
@@ -502,12 +896,17 @@ def main(argv=None):
                 "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"{N}^3 Q{k} SIPG-DG apply, lognormal K (GRF corr. 0.1, "
                                        "var 1, seed 2), x~U[-1,1] (seed 3)",
+                           "step": f"one sweep of {APPLIES_PER_STEP} FP64 applies",
                            "dofs_per_gpu": nd, "parallelism": f"replicas x{world}",
-                           "l2": "inputs larger than L2 (x, h w K and y are 134 MB each)"},
-                "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * args.steps,
-                "clocks": clk.summary(), "cpu_baseline": cpu, "cg": cg}
-        if batched is not None:
-            line["batched_cg"] = batched
+                           "l2": "inputs larger than L2 (x, h w K and y are 134 MB each; "
+                                 "line operators 1 GB)"},
+                "roofline": roofline, "e2e": e2e,
+                "gpu_launches": 2 * args.steps * APPLIES_PER_STEP,
+                "setup_ms": setup_ms,
+                "clocks": clk.summary(), "cpu_baseline": cpu, "cg": cg,
+                "config2_cg": cg2, "config1": cfg1, "config4": cfg4,
+                "batched_cg": batched, "mlmc": mlmc_r, "oracle_legs": legs,
+                "bench_wall_s": time.perf_counter() - t_start}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -48,6 +48,9 @@ enum {
 enum { DG_FP64 = 0, DG_FP32 = 1 };            /* operator precision            */
 enum { DG_CG_FP64 = 0, DG_CG_MIXED_IR = 1, DG_CG_MIXED_IR_RESTART = 2 };  /* dg_cg_solve modes */
 enum { DG_CG_PRECOND_JACOBI = 256 };  /* OR into a mode: PCG with M = diag(A) */
+/* Boundary conditions (dg_set_boundary): bit f set = boundary side f is Dirichlet,
+ * sides in the order x-, x+, y-, y+, z-, z+; the other sides carry zero flux. */
+enum { DG_BC_DIRICHLET = 0x3F, DG_BC_FLOW_X = 0x03 };
 
 typedef struct dg_mesh dg_mesh;
 
@@ -86,6 +89,17 @@ int dg_destroy_mesh(dg_mesh* mesh);
  * may be NULL. */
 int dg_mesh_info(const dg_mesh* mesh, long long* n_dofs, long long* n_cells_total,
                  int* n_points_1d, double* sigma);
+
+/* Boundary conditions of the mesh: bit f of dirichlet_mask set = boundary side f
+ * (x-, x+, y-, y+, z-, z+) carries a weak Dirichlet condition (the SIPG boundary
+ * face terms; the data enter only the right-hand side, dg_dirichlet_rhs); a
+ * clear bit = zero flux (homogeneous Neumann: no boundary face term).
+ * DG_BC_DIRICHLET (default, every side) is the Section 4.1 problem in H^1_0;
+ * DG_BC_FLOW_X is the Section 5 flow problem (p given on x = 0 and x = 1, zero
+ * flux on the other four sides).  Drops the coefficient (and the Jacobi
+ * diagonal): call dg_set_coefficient again afterwards.  Errors: INVALID_ARG
+ * (NULL mesh, mask outside 1..0x3f: at least one side must be Dirichlet). */
+int dg_set_boundary(dg_mesh* mesh, int dirichlet_mask);
 
 /* Set the diffusion coefficient K (device pointer, FP64, layout K[c*n^3 + q],
  * values at the volume Gauss points).  K is the coefficient A = lambda kappa of
@@ -187,6 +201,14 @@ int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count, const doub
                              double* const* x, double rtol, int maxit, int mode,
                              dg_cg_stats* st, void* stream);
 
+/* b = the load vector of f (Section 4.1 right-hand side l(v) = sum over cells of
+ * the integral of f v): b[c*n^3 + m] = h^3 sum_q w_q f[c*n^3 + q] phi_m(xi_q),
+ * with f given at the volume Gauss points (FP64 device pointer, layout as K)
+ * and the mesh's n-point Gauss rule per direction; b (FP64 device pointer,
+ * n_dofs values) is overwritten.  Needs no coefficient.  Asynchronous on
+ * `stream`.  Errors: INVALID_ARG (NULL mesh or vector, f == b), CUDA. */
+int dg_load_vector(const dg_mesh* mesh, const double* f, double* b, void* stream);
+
 /* Kernel timing for measurement tools (no paper counterpart).  While enabled,
  * each dg_apply / dg_apply_adjoint on this mesh records CUDA
  * events on its stream before pass 1 (traces), between the passes and after
@@ -196,6 +218,37 @@ int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count, const doub
  * Errors: INVALID_ARG (NULL mesh, max_applies < 1 or > 65536), OOM, CUDA. */
 int dg_timing_enable(dg_mesh* mesh, int max_applies);
 int dg_timing_read(dg_mesh* mesh, int* n_applies, double* ms_pass1, double* ms_pass2);
+
+/* b = the right-hand side of constant Dirichlet data g[f] on each Dirichlet
+ * boundary side f (host array of six doubles, sides x-, x+, y-, y+, z-, z+;
+ * entries of zero-flux sides are ignored): b_{c,m} = sum over the cell's
+ * Dirichlet faces of int_F gamma_F g [ -(d_n phi_m) + (sigma/h) phi_m ] dA, the
+ * weak Dirichlet terms of the SIPG form (Section 4.1 face form on the boundary;
+ * the Section 5 flow problem has p = 1 on x = 0, p = 0 on x = 1).  b (FP64
+ * device pointer, n_dofs values) is overwritten; add a load vector for a source
+ * term.  Needs the coefficient.  Asynchronous.  Errors: INVALID_ARG (NULL
+ * pointer, no coefficient, non-finite g), CUDA. */
+int dg_dirichlet_rhs(const dg_mesh* mesh, const double* g, double* b, void* stream);
+
+/* *q = the total flux through Dirichlet boundary side `side` (0..5) of the
+ * discrete solution u with data g on that side (Section 5's quantity of
+ * interest, the flux through the inlet x = 0 for side 0):
+ *   Q = sum over the side's faces of int_F gamma_F [ d_n u - (sigma/h)(u - g) ] dA,
+ * n outward: the boundary flux that the SIPG form conserves (for the solution
+ * of the flow problem the inlet and outlet fluxes cancel).  u, q: FP64 device
+ * pointers (q: one double, overwritten).  Asynchronous; fixed summation order.
+ * Errors: INVALID_ARG (NULL pointer, no coefficient, side outside 0..5 or a
+ * zero-flux side, non-finite g), CUDA. */
+int dg_boundary_flux(const dg_mesh* mesh, const double* u, int side, double g, double* q,
+                     void* stream);
+
+/* Arithmetic-throughput probe for measurement tools (no paper counterpart):
+ * the best of several timed launches of a kernel that keeps the FP64 (kind 0),
+ * FP32 (kind 1) or packed FP32x2 (kind 2) fused multiply-add pipe busy on every
+ * SM of the current device, in TFLOP/s (an FMA counts 2 flops per lane).
+ * Benchmarks divide the executed operation rate of the operator kernels by it.
+ * Blocks; allocates and frees 64 bytes.  Errors: INVALID_ARG, CUDA. */
+int dg_peak_probe(int kind, double* tflops, void* stream);
 
 /* y = A(K) x in FP64, for callers that cannot allocate device memory.  The
  * paper has no counterpart; this is a deployment variant of dg_apply (Section

@@ -81,9 +81,23 @@ class SIPG:
     or their flattening.
     """
 
-    def __init__(self, n_cells: int, degree: int, sigma: float | None = None):
+    # Boundary conditions.  "dirichlet": u = g on every boundary face (g = 0 in
+    # the operator; the weak Dirichlet terms of the SIPG form).  "flow_x": the
+    # Section 5 flow problem -- Dirichlet data on the faces x = 0 and x = 1,
+    # zero flux (homogeneous Neumann: no boundary face term at all) on the
+    # faces y = 0, y = 1, z = 0, z = 1.  Boundary sides in the order
+    # (x-, x+, y-, y+, z-, z+).
+    BOUNDARY = {"dirichlet": (True,) * 6,
+                "flow_x": (True, True, False, False, False, False)}
+
+    def __init__(self, n_cells: int, degree: int, sigma: float | None = None,
+                 bc: str = "dirichlet"):
         if n_cells < 1 or degree < 1:
             raise ValueError("need n_cells >= 1 and degree >= 1")
+        if bc not in self.BOUNDARY:
+            raise ValueError(f"unknown boundary condition {bc!r}")
+        self.bc = bc
+        self.dirichlet = self.BOUNDARY[bc]
         self.N = n_cells
         self.k = degree
         self.n = n = degree + 1
@@ -234,6 +248,8 @@ class SIPG:
                 # -{d_n u}[phi] - {d_n phi}[u] + sigma [u][phi], weighted by W
                 y_int = (W * (-avg + sigma * jump)) @ Jphi - (W * jump) @ Aphi
                 y_bnd = (W * (-dn_b + sigma * jump_b)) @ Jphi_b - (W * jump_b) @ Aphi_b
+                if not self.dirichlet[2 * d + int(upper)]:
+                    y_bnd = np.zeros_like(y_bnd)      # zero-flux boundary: no face term
                 y += np.where(interior[:, None], y_int, y_bnd)
         return y
 
@@ -276,11 +292,11 @@ class SIPG:
                             Js, As = side[sname]
                             B = Jt.T @ (W[:, None] * (-As + sigma * Js)) - At.T @ (W[:, None] * Js)
                             add_block(tc, sc, B)
-                if coord == self.N - 1:       # upper boundary face, outward +e_d
+                if coord == self.N - 1 and self.dirichlet[2 * d + 1]:  # upper boundary, outward +e_d
                     W = Kbar[c] * wf
                     Jt, At = V1, D1
                     add_block(c, c, Jt.T @ (W[:, None] * (-At + sigma * Jt)) - At.T @ (W[:, None] * Jt))
-                if coord == 0:                # lower boundary face, outward -e_d
+                if coord == 0 and self.dirichlet[2 * d]:               # lower boundary, outward -e_d
                     W = Kbar[c] * wf
                     Jt, At = V0, -D0
                     add_block(c, c, Jt.T @ (W[:, None] * (-At + sigma * Jt)) - At.T @ (W[:, None] * Jt))
@@ -316,6 +332,8 @@ class SIPG:
                     J, A_int, A_bnd = -V0, 0.5 * D0, D0
                 f_int = wf @ (sigma * J * J - 2.0 * J * A_int)
                 f_bnd = wf @ (sigma * J * J - 2.0 * J * A_bnd)
+                if not self.dirichlet[2 * d + int(upper)]:
+                    f_bnd = np.zeros_like(f_bnd)
                 dg += gamma[:, None] * np.where(interior[:, None], f_int[None, :], f_bnd[None, :])
         return dg.reshape(-1) if full else dg
 
@@ -356,7 +374,10 @@ class SIPG:
 
                 ju, au = traces(u)
                 jv, av = traces(v)
-                out[:, 2 * d + int(upper)] = ((-au * jv - av * ju + sigma * ju * jv) * wf[None, :]).sum(1)
+                form = ((-au * jv - av * ju + sigma * ju * jv) * wf[None, :]).sum(1)
+                if not self.dirichlet[2 * d + int(upper)]:
+                    form = np.where(interior, form, 0.0)   # zero-flux boundary face
+                out[:, 2 * d + int(upper)] = form
         return out
 
     def coeff_grad(self, K, u, v):
@@ -388,6 +409,52 @@ class SIPG:
         return g + dface[:, None] * self.wq[None, :]
 
     # -- right-hand side and errors --------------------------------------------
+    # -- Dirichlet data and the boundary flux (Section 5 flow problem) --------
+    def _boundary_cells(self, side: int):
+        d, upper = side // 2, bool(side % 2)
+        c = np.arange(self.n_cells_total)
+        coord = self.cell_coords(c)[d]
+        return c[coord == (self.N - 1 if upper else 0)], d, upper
+
+    def dirichlet_rhs(self, K, g):
+        """Right-hand side of the weak Dirichlet condition u = g_s on each
+        Dirichlet boundary side s (g: six constants, sides x-, x+, y-, y+, z-, z+):
+        b_{c,m} = sum over the Dirichlet faces of cell c of
+        int_F gamma_F g [ -(d_n phi_m) + (sigma/h) phi_m ] dA,
+        by the face Gauss rule (dA = h^2 w_p, d_n = outward derivative / h)."""
+        Nc, n3, h, sigma = self.n_cells_total, self.n3, self.h, self.sigma
+        Kbar = self.kbar(K)
+        b = np.zeros((Nc, n3))
+        for side in range(6):
+            if not self.dirichlet[side] or g[side] == 0.0:
+                continue
+            cells, d, upper = self._boundary_cells(side)
+            V = self.face_val[(d, int(upper))]             # (p, m)
+            Dn = self.face_der[(d, int(upper))] * (1.0 if upper else -1.0)   # outward
+            wa = h * h * self.face_w[d]                      # h^2 w_p
+            per_m = wa @ (-Dn / h + (sigma / h) * V)         # (m,)
+            b[cells] += (Kbar[cells] * g[side])[:, None] * per_m[None, :]
+        return b.reshape(-1)
+
+    def boundary_flux(self, K, u, side: int, g: float):
+        """Total flux through one Dirichlet boundary side, the quantity of interest
+        of Section 5: Q = int_side [ gamma_F d_n u - gamma_F (sigma/h)(u - g) ] dA
+        (the boundary flux the SIPG form conserves; n outward).  Summed by the
+        face Gauss rule over the side's cells."""
+        if not self.dirichlet[side]:
+            raise ValueError("the flux is defined on a Dirichlet side")
+        h, sigma = self.h, self.sigma
+        u = np.asarray(u, float).reshape(self.n_cells_total, self.n3)
+        Kbar = self.kbar(K)
+        cells, d, upper = self._boundary_cells(side)
+        V = self.face_val[(d, int(upper))]
+        Dn = self.face_der[(d, int(upper))] * (1.0 if upper else -1.0)
+        wa = h * h * self.face_w[d]
+        uf = u[cells] @ V.T                                  # (cells, p)
+        dnu = (u[cells] @ Dn.T) / h
+        q = (Kbar[cells][:, None] * (dnu - (sigma / h) * (uf - g)) * wa[None, :]).sum()
+        return float(q)
+
     def load_vector(self, f, nq: int | None = None):
         """b_{c,m} = int_T f phi_m by an nq-point Gauss rule per direction
         (default nq = n)."""

@@ -27,6 +27,8 @@ DG_CG_FP64 = 0
 DG_CG_MIXED_IR = 1
 DG_CG_MIXED_IR_RESTART = 2
 DG_CG_PRECOND_JACOBI = 256
+DG_BC_DIRICHLET = 0x3F
+DG_BC_FLOW_X = 0x03
 
 ERROR_NAMES = {
     DG_ERR_INVALID_ARG: "DG_ERR_INVALID_ARG",
@@ -63,6 +65,11 @@ _SIGS = {
                                                 _VP, _VP]),
     "dg_apply_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "dg_diagonal": (ctypes.c_int, [_VP, _VP, _VP]),
+    "dg_load_vector": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "dg_set_boundary": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "dg_dirichlet_rhs": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), _VP, _VP]),
+    "dg_boundary_flux": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_double, _VP, _VP]),
+    "dg_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _VP]),
     "dg_timing_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "dg_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_double),
@@ -173,7 +180,15 @@ class Mesh:
         except Exception:
             pass
 
-    # -- coefficient --------------------------------------------------------
+    # -- boundary conditions and coefficient -----------------------------------
+    def set_boundary(self, bc):
+        """bc: "dirichlet" (every side, the default), "flow_x" (Dirichlet on
+        x = 0 and x = 1, zero flux elsewhere) or a Dirichlet-side bit mask.
+        Drops the coefficient: call set_coefficient afterwards."""
+        mask = {"dirichlet": DG_BC_DIRICHLET, "flow_x": DG_BC_FLOW_X}.get(bc, bc)
+        _check(library().dg_set_boundary(self._h, int(mask)), "dg_set_boundary")
+        self._autograd_logK = None
+
     def set_coefficient(self, K, stream=None):
         """K: CUDA float64 tensor of n_dofs values at the volume Gauss points."""
         self._autograd_logK = None
@@ -227,6 +242,39 @@ class Mesh:
         _check(library().dg_diagonal(self._h, _ptr(d, _f64(), self.n_dofs, "d"),
                                      _stream(stream)), "dg_diagonal")
         return d
+
+    def load_vector(self, f, b=None, stream=None):
+        """b = integral of f phi_m per DOF, f (CUDA float64) at the volume Gauss
+        points in the layout of K."""
+        import torch
+        if b is None:
+            b = torch.empty(self.n_dofs, dtype=torch.float64, device="cuda")
+        _check(library().dg_load_vector(self._h, _ptr(f, _f64(), self.n_dofs, "f"),
+                                        _ptr(b, _f64(), self.n_dofs, "b"), _stream(stream)),
+               "dg_load_vector")
+        return b
+
+    def dirichlet_rhs(self, g, b=None, stream=None):
+        """b = weak Dirichlet right-hand side of constant data g (six values,
+        sides x-, x+, y-, y+, z-, z+; zero-flux sides ignored)."""
+        import torch
+        if b is None:
+            b = torch.empty(self.n_dofs, dtype=torch.float64, device="cuda")
+        gv = (ctypes.c_double * 6)(*[float(v) for v in g])
+        _check(library().dg_dirichlet_rhs(self._h, gv, _ptr(b, _f64(), self.n_dofs, "b"),
+                                          _stream(stream)), "dg_dirichlet_rhs")
+        return b
+
+    def boundary_flux(self, u, side: int, g: float, q=None, stream=None):
+        """Total flux of u through Dirichlet side `side` with data g (a one-element
+        CUDA float64 tensor, written asynchronously)."""
+        import torch
+        if q is None:
+            q = torch.empty(1, dtype=torch.float64, device="cuda")
+        _check(library().dg_boundary_flux(self._h, _ptr(u, _f64(), self.n_dofs, "u"), int(side),
+                                          float(g), _ptr(q, _f64(), 1, "q"), _stream(stream)),
+               "dg_boundary_flux")
+        return q
 
     # -- measurement -------------------------------------------------------------
     def timing_enable(self, max_applies: int):
@@ -298,6 +346,15 @@ def apply_static(n_cells: int, degree: int, K, x, y=None, stream=None):
                                       _ptr(x, _f64(), nd, "x"), _ptr(y, _f64(), nd, "y"),
                                       _stream(stream)), "dg_apply_static")
     return y
+
+
+def peak_probe(kind: str = "fp64", stream=None) -> float:
+    """Measured fused multiply-add throughput of the current GPU in TFLOP/s:
+    kind "fp64", "fp32" or "fp32x2" (packed FP32 pairs)."""
+    k = {"fp64": 0, "fp32": 1, "fp32x2": 2}[kind]
+    out = ctypes.c_double()
+    _check(library().dg_peak_probe(k, ctypes.byref(out), _stream(stream)), "dg_peak_probe")
+    return out.value
 
 
 def _f64():

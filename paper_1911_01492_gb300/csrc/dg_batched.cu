@@ -1,64 +1,82 @@
 // Batched CG: many independent systems A_s x_s = b_s (different coefficient
 // samples, mesh sizes and degrees, as in the multilevel Monte-Carlo setting of
-// Section 5) solved by lock-step CG in one persistent kernel.
+// Section 5) solved in lock-step by one persistent kernel.
 //
-// Each sample runs the PCG of Section 2.4 (M = I, or M = diag(A) with
-// DG_CG_PRECOND_JACOBI) with its own scalars, like
-// the k independent solvers running in lock-step of the horizontal
-// vectorisation in Section 3.5.  The cells of all samples are cut into work
-// units (one block's worth of cells of one sample); every iteration of every
-// unfinished sample is executed by one persistent cooperative launch:
-//   A  p = z + beta p (z = M^-1 r) on the unit's cells, then pass 1 (nodal
-//      values, face traces) of p;
-//   B  pass 2 (volume + face terms) -> q, and the unit's partial <p, q>;
-//   C  per sample: alpha = rho / <p, q>  (partials summed in a fixed order);
-//   D  x += alpha p, r -= alpha q, the unit's partials <r, r> and <z, r>;
-//   E  per sample: rho' = <z, r>, convergence test on <r, r>, beta = rho'/rho;
-// separated by grid-wide barriers.  Each barrier spins a bounded number of
-// times; on expiry the kernel raises an error flag and returns, and the host
-// reports DG_ERR_TIMEOUT.  Work units of finished samples are skipped, so
-// uneven samples cost what they need (work proportional to size x iterations,
-// as in the proportional allocation rule of Section 5).
+// Each sample runs preconditioned CG (M = I, or M = diag(A) with
+// DG_CG_PRECOND_JACOBI) with its own scalars, like the k independent solvers
+// running in lock-step of the horizontal vectorisation in Section 3.5.  The
+// recurrence is the single-reduction variant of Section 2.4 (Chronopoulos and
+// Gear): s = A p is carried by its own recurrence, so every iteration applies
+// the operator once, to u = M^-1 r, and needs the three inner products
+// (r, u), (w, u) and (r, r) (w = A u) at one point:
+//   phase 1, per work unit:  p = u + beta p,  s = w + beta s,  x += alpha p,
+//                            r -= alpha s,  u = M^-1 r,  pass 1 of u
+//                            (nodal values and face traces);
+//   phase 2, per work unit:  pass 2 -> w = A u; the unit's partial sums of
+//                            (r, u), (w, u), (r, r); the last unit of a sample
+//                            to finish (a per-sample ticket) adds the sample's
+//                            partials in a fixed order and forms
+//                            gamma' = (r, u), beta = gamma' / gamma and
+//                            alpha = gamma' / ((w, u) - beta gamma' / alpha),
+//                            and tests (r, r) against the tolerance.
+// Two grid-wide barriers per iteration: between the passes (pass 2 reads the
+// neighbours' traces) and after the scalars.  Each barrier spins a bounded
+// number of times; on expiry the kernel raises an error flag and returns, and
+// the host reports DG_ERR_TIMEOUT.  Work units of finished samples are
+// skipped, so uneven samples cost what they need (work proportional to size x
+// iterations, the proportional allocation of Section 5).  A launch runs until
+// every sample is done or for a number of iterations sized to about two
+// seconds of work, and is captured in a CUDA graph that is replayed until the
+// device-side count of active samples reaches zero.
 //
-// The launch is captured in a CUDA graph and replayed until every sample is
-// done.  An autotuner picks the number of resident blocks per SM by timing the
-// first graph replays (real CG iterations) for each candidate.
+// An autotuner picks the launch shape: resident blocks per SM and the tile of
+// cells a block takes per work unit (1, 2 or 4 groups of the operator kernels'
+// cells per block), by timing the first graph replays (real CG iterations)
+// of each candidate.  Choices are cached per batch signature in the process
+// and, if DG_TUNE_CACHE names a file, in that file.  DG_BATCHED_SHAPE="B,T"
+// forces B blocks per SM (at most the resident maximum) and tile index T.
+//
+// Degrees 1..4 run in 128-thread blocks; a batch with any degree 5..8 runs in
+// a 256-thread instantiation (the operator kernels' cell groups need up to
+// 256 threads there).
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "dg_apply_impl.cuh"
 
 namespace {
 
-constexpr int BT = 128;        // threads per block (>= n^2 * cells per unit for n <= 5)
-constexpr int MAXN_B = 5;      // batched solver supports n = 2..5 (degree 1..4)
-constexpr int ITERS_PER_LAUNCH = 64;  // lock-step iterations per persistent launch
 constexpr int ITERS_TUNE = 4;         // iterations per launch while autotuning
+constexpr int TILES[3] = {1, 2, 4};   // cell groups per work unit (tuned)
+constexpr double LAUNCH_SECONDS = 2.0;   // work per production launch (estimate)
+constexpr double EST_DOF_RATE = 7.0e9;   // DOF-iterations per second for that estimate
 
-__constant__ DGTab<double> c_btab[MAXN_B - 1];  // tables for n = 2..5
+__constant__ DGTab<double> c_btab[DG_MAXN - 1];  // tables for n = 2..9
 
 struct SampleDev {
   const double* b;
   double* x;
-  double *r, *p, *q;
+  double *r, *u, *w, *p, *s;  // u == r when M = I
   double *U, *X, *TR;
-  const double* kt;
+  const double* kt;      // h w K (not read: the line operators hold the volume term)
   const double* fw;
   const double* lineop;
   const double* dinv;  // 1 / diag(A) for M = diag(A); nullptr for M = I
   long long ncells;
-  int Nc;       // cells per direction
-  int n;        // points per direction
-  int ubeg, uend;  // work units of this sample
+  int Nc;          // cells per direction
+  int n;           // points per direction
+  int ubeg, uend;  // work units of this sample in the launch's unit list
 };
 
 struct BState {
-  double rho, rho_new, alpha, beta, tol2, bnorm2, pq;
-  double rr;  // <r, r>, the convergence norm (rho = <z, r>)
+  double gamma, delta, alpha, beta, rr, tol2, bnorm2;
   int done, breakdown, iters, maxit;
 };
 
@@ -66,7 +84,7 @@ struct BCtl {
   unsigned count;     // barrier arrivals
   unsigned gen;       // barrier generation
   int err;            // 1: a barrier wait expired
-  int active;         // samples not done (written by block 0 after phase E)
+  int active;         // samples not done (decremented by the sample's last unit)
   unsigned long long iterations_run;  // lock-step iterations executed
 };
 
@@ -75,7 +93,8 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block sum (blockDim.x == BT); result valid in every thread.
+// Block sum in a fixed order; result valid in every thread.
+template <int BT>
 __device__ double block_sum(double v, double* sred) {
   v = warp_sum(v);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -116,228 +135,297 @@ __device__ bool grid_sync(BCtl* ctl, unsigned nblocks, long long limit) {
   return ((volatile int*)&ctl->err)[0] == 0;
 }
 
+__host__ __device__ constexpr int group_cells(int n) {
+  return n == 2 ? dgk::Cfg<2>::CPB : n == 3 ? dgk::Cfg<3>::CPB : n == 4 ? dgk::Cfg<4>::CPB
+       : n == 5 ? dgk::Cfg<5>::CPB : n == 6 ? dgk::Cfg<6>::CPB : n == 7 ? dgk::Cfg<7>::CPB
+       : n == 8 ? dgk::Cfg<8>::CPB : dgk::Cfg<9>::CPB;
+}
+
 template <int N>
-__device__ __forceinline__ void unit_pass1(const SampleDev& S, long long c0, int nblk,
-                                           double* smem) {
-  dgk::trace_cells<N, double>(S.p, S.U, S.X, S.TR, c0, nblk, c_btab[N - 2], smem);
+__device__ __forceinline__ void group_pass1(const SampleDev& S, long long c0, int nblk,
+                                            double* smem) {
+  dgk::trace_cells<N, double>(S.u, S.U, S.X, S.TR, c0, nblk, c_btab[N - 2], smem);
 }
 template <int N>
-__device__ __forceinline__ void unit_pass2(const SampleDev& S, long long c0, int nblk,
-                                           double* smem) {
-  dgk::cell_cells<N, double, true>(S.U, S.X, S.TR, S.kt, S.fw, S.q, c0, nblk, S.Nc,
+__device__ __forceinline__ void group_pass2(const SampleDev& S, long long c0, int nblk,
+                                            double* smem) {
+  dgk::cell_cells<N, double, true>(S.U, S.X, S.TR, S.kt, S.fw, S.w, c0, nblk, S.Nc,
                                    c_btab[N - 2], smem, S.lineop);
 }
 
-__device__ __forceinline__ int unit_cells(int n) {
-  return n == 2 ? dgk::Cfg<2>::CPB : n == 3 ? dgk::Cfg<3>::CPB : n == 4 ? dgk::Cfg<4>::CPB
-                                                                        : dgk::Cfg<5>::CPB;
+template <int MAXN>
+__device__ __forceinline__ void pass1_dispatch(const SampleDev& sd, long long c, int nblk,
+                                               double* smem) {
+  switch (sd.n) {
+    case 2: group_pass1<2>(sd, c, nblk, smem); break;
+    case 3: group_pass1<3>(sd, c, nblk, smem); break;
+    case 4: group_pass1<4>(sd, c, nblk, smem); break;
+    case 5: group_pass1<5>(sd, c, nblk, smem); break;
+    default:
+      if constexpr (MAXN > 5) {
+        switch (sd.n) {
+          case 6: group_pass1<6>(sd, c, nblk, smem); break;
+          case 7: group_pass1<7>(sd, c, nblk, smem); break;
+          case 8: group_pass1<8>(sd, c, nblk, smem); break;
+          default: group_pass1<9>(sd, c, nblk, smem); break;
+        }
+      }
+      break;
+  }
 }
 
-__global__ void __launch_bounds__(BT)
-kb_persistent(const SampleDev* __restrict__ S, int ns, const int2* __restrict__ units, int nu,
-              BState* st, double* part, BCtl* ctl, int iters, long long limit, int stall_test) {
+template <int MAXN>
+__device__ __forceinline__ void pass2_dispatch(const SampleDev& sd, long long c, int nblk,
+                                               double* smem) {
+  switch (sd.n) {
+    case 2: group_pass2<2>(sd, c, nblk, smem); break;
+    case 3: group_pass2<3>(sd, c, nblk, smem); break;
+    case 4: group_pass2<4>(sd, c, nblk, smem); break;
+    case 5: group_pass2<5>(sd, c, nblk, smem); break;
+    default:
+      if constexpr (MAXN > 5) {
+        switch (sd.n) {
+          case 6: group_pass2<6>(sd, c, nblk, smem); break;
+          case 7: group_pass2<7>(sd, c, nblk, smem); break;
+          case 8: group_pass2<8>(sd, c, nblk, smem); break;
+          default: group_pass2<9>(sd, c, nblk, smem); break;
+        }
+      }
+      break;
+  }
+}
+
+// One persistent launch of up to `iters` lock-step iterations over every
+// unfinished sample.  `tile`: cell groups per work unit.
+template <int BT, int MAXN>
+__global__ void __launch_bounds__(BT, BT == 128 ? 6 : 3)
+kb_persistent(const SampleDev* __restrict__ S, const int2* __restrict__ units, int nu, int tile,
+              BState* st, double* part, unsigned* tickets, BCtl* ctl, int iters, long long limit,
+              int stall_test) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* smem = reinterpret_cast<double*>(smem_raw);
   __shared__ double sred[BT / 32];
+  __shared__ bool is_last;
   const unsigned nb = gridDim.x;
   if (stall_test && blockIdx.x == 0) return;  // test hook: one block never arrives
   for (int it = 0; it < iters; ++it) {
     if (((volatile int*)&ctl->active)[0] == 0) break;
-    // A: p = r + beta p on the unit, then pass 1 of p
-    for (int u = blockIdx.x; u < nu; u += nb) {
-      const int s = units[u].x;
+    // phase 1: vector recurrences on the unit's cells, then pass 1 of u
+    for (int uu = blockIdx.x; uu < nu; uu += nb) {
+      const int s = units[uu].x;
       if (st[s].done) continue;
       const SampleDev& sd = S[s];
-      const long long c0 = units[u].y;
-      const int cpu = unit_cells(sd.n);
-      const int nblk = (int)((sd.ncells - c0) < cpu ? (sd.ncells - c0) : cpu);
+      const int cpb = group_cells(sd.n);
+      const long long c0 = units[uu].y;
+      const long long c1 = (c0 + (long long)tile * cpb) < sd.ncells ? c0 + (long long)tile * cpb
+                                                                    : sd.ncells;
       const long long n3 = (long long)sd.n * sd.n * sd.n;
-      const double be = st[s].beta;
-      if (sd.dinv)
-        for (long long i = c0 * n3 + threadIdx.x; i < (c0 + nblk) * n3; i += BT)
-          sd.p[i] = fma(be, sd.p[i], sd.dinv[i] * sd.r[i]);
-      else
-        for (long long i = c0 * n3 + threadIdx.x; i < (c0 + nblk) * n3; i += BT)
-          sd.p[i] = fma(be, sd.p[i], sd.r[i]);
-      __syncthreads();
-      switch (sd.n) {
-        case 2: unit_pass1<2>(sd, c0, nblk, smem); break;
-        case 3: unit_pass1<3>(sd, c0, nblk, smem); break;
-        case 4: unit_pass1<4>(sd, c0, nblk, smem); break;
-        default: unit_pass1<5>(sd, c0, nblk, smem); break;
-      }
-      __syncthreads();
-    }
-    if (!grid_sync(ctl, nb, limit)) return;
-    // B: pass 2 -> q, partial <p, q>
-    for (int u = blockIdx.x; u < nu; u += nb) {
-      const int s = units[u].x;
-      if (st[s].done) continue;
-      const SampleDev& sd = S[s];
-      const long long c0 = units[u].y;
-      const int cpu = unit_cells(sd.n);
-      const int nblk = (int)((sd.ncells - c0) < cpu ? (sd.ncells - c0) : cpu);
-      switch (sd.n) {
-        case 2: unit_pass2<2>(sd, c0, nblk, smem); break;
-        case 3: unit_pass2<3>(sd, c0, nblk, smem); break;
-        case 4: unit_pass2<4>(sd, c0, nblk, smem); break;
-        default: unit_pass2<5>(sd, c0, nblk, smem); break;
-      }
-      __syncthreads();
-      const long long n3 = (long long)sd.n * sd.n * sd.n;
-      double a = 0.0;
-      for (long long i = c0 * n3 + threadIdx.x; i < (c0 + nblk) * n3; i += BT)
-        a = fma(sd.p[i], sd.q[i], a);
-      a = block_sum(a, sred);
-      if (threadIdx.x == 0) part[3 * u] = a;
-    }
-    if (!grid_sync(ctl, nb, limit)) return;
-    // C: alpha per sample
-    for (int s = blockIdx.x; s < ns; s += nb) {
-      if (st[s].done) continue;
-      double a = 0.0;
-      for (int u = S[s].ubeg + threadIdx.x; u < S[s].uend; u += BT) a += part[3 * u];
-      a = block_sum(a, sred);
-      if (threadIdx.x == 0) {
-        st[s].pq = a;
-        if (!(a > 0.0) || !isfinite(a)) {
-          st[s].breakdown = 1;
-          st[s].done = 1;
-        } else {
-          st[s].alpha = st[s].rho / a;
-        }
-      }
-    }
-    if (!grid_sync(ctl, nb, limit)) return;
-    // D: x += alpha p, r -= alpha q, partials <r, r> and <z, r>
-    for (int u = blockIdx.x; u < nu; u += nb) {
-      const int s = units[u].x;
-      if (st[s].done) continue;
-      const SampleDev& sd = S[s];
-      const long long c0 = units[u].y;
-      const int cpu = unit_cells(sd.n);
-      const int nblk = (int)((sd.ncells - c0) < cpu ? (sd.ncells - c0) : cpu);
-      const long long n3 = (long long)sd.n * sd.n * sd.n;
-      const double al = st[s].alpha;
-      double a = 0.0, z = 0.0;
+      const double al = st[s].alpha, be = st[s].beta;
       if (sd.dinv) {  // two loops: no per-element branch between the loads
-        for (long long i = c0 * n3 + threadIdx.x; i < (c0 + nblk) * n3; i += BT) {
-          sd.x[i] = fma(al, sd.p[i], sd.x[i]);
-          const double ri = fma(-al, sd.q[i], sd.r[i]);
+        for (long long i = c0 * n3 + threadIdx.x; i < c1 * n3; i += BT) {
+          const double pi = fma(be, sd.p[i], sd.u[i]);
+          const double si = fma(be, sd.s[i], sd.w[i]);
+          sd.p[i] = pi;
+          sd.s[i] = si;
+          sd.x[i] = fma(al, pi, sd.x[i]);
+          const double ri = fma(-al, si, sd.r[i]);
           sd.r[i] = ri;
-          a = fma(ri, ri, a);
-          z = fma(sd.dinv[i] * ri, ri, z);
+          sd.u[i] = sd.dinv[i] * ri;
         }
       } else {
-        for (long long i = c0 * n3 + threadIdx.x; i < (c0 + nblk) * n3; i += BT) {
-          sd.x[i] = fma(al, sd.p[i], sd.x[i]);
-          const double ri = fma(-al, sd.q[i], sd.r[i]);
-          sd.r[i] = ri;
-          a = fma(ri, ri, a);
+        for (long long i = c0 * n3 + threadIdx.x; i < c1 * n3; i += BT) {
+          const double pi = fma(be, sd.p[i], sd.r[i]);
+          const double si = fma(be, sd.s[i], sd.w[i]);
+          sd.p[i] = pi;
+          sd.s[i] = si;
+          sd.x[i] = fma(al, pi, sd.x[i]);
+          sd.r[i] = fma(-al, si, sd.r[i]);
         }
       }
-      a = block_sum(a, sred);
-      if (sd.dinv) z = block_sum(z, sred);  // uniform: the block works on one unit
-      if (threadIdx.x == 0) {
-        part[3 * u + 1] = a;
-        part[3 * u + 2] = z;
+      __syncthreads();
+      for (long long c = c0; c < c1; c += cpb) {
+        const int nblk = (int)((c1 - c) < cpb ? (c1 - c) : cpb);
+        pass1_dispatch<MAXN>(sd, c, nblk, smem);
+        __syncthreads();
       }
     }
     if (!grid_sync(ctl, nb, limit)) return;
-    // E: rho' = <z, r>, convergence on <r, r>, beta
-    for (int s = blockIdx.x; s < ns; s += nb) {
+    // phase 2: w = A u, the unit's partial sums, the sample's scalars
+    for (int uu = blockIdx.x; uu < nu; uu += nb) {
+      const int s = units[uu].x;
       if (st[s].done) continue;
-      const bool pc = S[s].dinv != nullptr;
-      double a = 0.0, z = 0.0;
-      for (int u = S[s].ubeg + threadIdx.x; u < S[s].uend; u += BT) {
-        a += part[3 * u + 1];
-        if (pc) z += part[3 * u + 2];
+      const SampleDev& sd = S[s];
+      const int cpb = group_cells(sd.n);
+      const long long c0 = units[uu].y;
+      const long long c1 = (c0 + (long long)tile * cpb) < sd.ncells ? c0 + (long long)tile * cpb
+                                                                    : sd.ncells;
+      for (long long c = c0; c < c1; c += cpb) {
+        const int nblk = (int)((c1 - c) < cpb ? (c1 - c) : cpb);
+        pass2_dispatch<MAXN>(sd, c, nblk, smem);
+        __syncthreads();
       }
-      a = block_sum(a, sred);
-      if (pc) z = block_sum(z, sred);
+      const long long n3 = (long long)sd.n * sd.n * sd.n;
+      double ru = 0.0, wu = 0.0, rr = 0.0;
+      for (long long i = c0 * n3 + threadIdx.x; i < c1 * n3; i += BT) {
+        const double ri = sd.r[i], ui = sd.u[i];
+        ru = fma(ri, ui, ru);
+        wu = fma(sd.w[i], ui, wu);
+        rr = fma(ri, ri, rr);
+      }
+      ru = block_sum<BT>(ru, sred);
+      wu = block_sum<BT>(wu, sred);
+      rr = block_sum<BT>(rr, sred);
       if (threadIdx.x == 0) {
-        BState& b = st[s];
-        const double zr = pc ? z : a;
-        b.iters += 1;
-        if (!isfinite(a) || !isfinite(zr)) {
-          b.breakdown = 1;
-          b.done = 1;
+        part[3 * uu] = ru;
+        part[3 * uu + 1] = wu;
+        part[3 * uu + 2] = rr;
+        __threadfence();
+        is_last = atomicAdd(&tickets[s], 1u) == (unsigned)(sd.uend - sd.ubeg) - 1;
+      }
+      __syncthreads();
+      if (!is_last) continue;
+      __threadfence();
+      // the sample's last unit: fixed-order sums of all its units' partials
+      double a = 0.0, b = 0.0, c = 0.0;
+      const volatile double* vp = part;
+      for (int v = sd.ubeg + threadIdx.x; v < sd.uend; v += BT) {
+        a += vp[3 * v];
+        b += vp[3 * v + 1];
+        c += vp[3 * v + 2];
+      }
+      a = block_sum<BT>(a, sred);
+      b = block_sum<BT>(b, sred);
+      c = block_sum<BT>(c, sred);
+      if (threadIdx.x == 0) {
+        BState& q = st[s];
+        q.iters += 1;
+        if (!isfinite(a) || !isfinite(b) || !isfinite(c)) {
+          q.breakdown = 1;
+          q.done = 1;
         } else {
-          b.beta = zr / b.rho;
-          b.rho = zr;
-          b.rr = a;
-          if (a <= b.tol2 || b.iters >= b.maxit) b.done = 1;
+          q.rr = c;
+          if (c <= q.tol2 || q.iters >= q.maxit) {
+            q.done = 1;
+          } else {
+            const double beta = a / q.gamma;
+            const double den = b - beta * a / q.alpha;  // (p, A p) of the next direction
+            if (!(den > 0.0) || !(a > 0.0)) {
+              q.breakdown = 1;
+              q.done = 1;
+            } else {
+              q.beta = beta;
+              q.alpha = a / den;
+              q.gamma = a;
+              q.delta = b;
+            }
+          }
         }
+        if (q.done) atomicSub(&ctl->active, 1);
+        tickets[s] = 0u;
       }
+      __syncthreads();
     }
     if (!grid_sync(ctl, nb, limit)) return;
-    if (blockIdx.x == 0) {
-      int act = 0;
-      for (int s = threadIdx.x; s < ns; s += BT) act += st[s].done ? 0 : 1;
-      act = (int)block_sum((double)act, sred);
-      if (threadIdx.x == 0) {
-        ctl->active = act;
-        ctl->iterations_run += 1;
-      }
-    }
-    if (!grid_sync(ctl, nb, limit)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->iterations_run += 1;
   }
 }
 
-// Per-sample start: r = b - q (q = A x), p = z = M^-1 r (dinv, or M = I when
-// dinv is null), rho = <z, r>, rr = <r, r>, bnorm2 = <b, b>, beta = 0.  One
-// launch per sample; the last block publishes the sums.
+// Deterministic sums of up to three products over a vector: a fixed grid of
+// 256 blocks writes partials, the last block adds them in a fixed order.
+// Start of a sample (after w = A x):
+//   r = b - w, u = M^-1 r (dinv; u is r itself for M = I), p = s = 0,
+//   bnorm2 = (b, b), rr = (r, r), tol2 = rtol^2 bnorm2.
 __global__ void __launch_bounds__(256)
-kb_init(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
-        double* __restrict__ p, const double* __restrict__ dinv, long long n, double rtol,
-        double* partials, unsigned* ticket, BState* st, int maxit, int keep_iters) {
-  __shared__ double sw[8];
+kb_init_r(const double* __restrict__ b, const double* __restrict__ w, double* __restrict__ r,
+          double* __restrict__ u, double* __restrict__ p, double* __restrict__ sv,
+          const double* __restrict__ dinv, long long n, double rtol, double* partials,
+          unsigned* ticket, BState* st, int maxit, int keep_iters) {
+  __shared__ double sred[8];
   __shared__ bool last;
-  double rr = 0.0, bb = 0.0, zr = 0.0;
+  double rr = 0.0, bb = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const double ri = b[i] - q[i];
-    const double zi = dinv ? dinv[i] * ri : ri;
+    const double ri = b[i] - w[i];
     r[i] = ri;
-    p[i] = zi;
+    if (dinv) u[i] = dinv[i] * ri;
+    p[i] = 0.0;
+    sv[i] = 0.0;
     rr = fma(ri, ri, rr);
     bb = fma(b[i], b[i], bb);
-    zr = fma(zi, ri, zr);
   }
-  double tot[3] = {rr, bb, zr};
-  for (int k = 0; k < 3; ++k) {
-    double v = warp_sum(tot[k]);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int i = 0; i < 8; ++i) t += sw[i];
-    if (threadIdx.x == 0) partials[3 * blockIdx.x + k] = t;
+  rr = block_sum<256>(rr, sred);
+  bb = block_sum<256>(bb, sred);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = rr;
+    partials[2 * blockIdx.x + 1] = bb;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
   if (threadIdx.x == 0) {
-    double a = 0.0, c = 0.0, z = 0.0;
+    double a = 0.0, c = 0.0;
     for (unsigned i = 0; i < gridDim.x; ++i) {
-      a += ((volatile double*)partials)[3 * i];
-      c += ((volatile double*)partials)[3 * i + 1];
-      z += ((volatile double*)partials)[3 * i + 2];
+      a += ((volatile double*)partials)[2 * i];
+      c += ((volatile double*)partials)[2 * i + 1];
     }
     BState s = {};
-    s.rho = z;
     s.rr = a;
     s.bnorm2 = c;
     s.tol2 = rtol * rtol * c;
-    s.beta = 0.0;
     s.maxit = maxit;
     s.iters = keep_iters;
-    s.breakdown = !(isfinite(a) && isfinite(c) && isfinite(z));
+    s.breakdown = !(isfinite(a) && isfinite(c));
     // b = 0: the solution is x = 0 (set by the host), nothing to iterate
     s.done = s.breakdown || c == 0.0 || a <= s.tol2 || keep_iters >= maxit;
+    *st = s;
+    *ticket = 0u;
+  }
+}
+
+// After w = A u: gamma = (r, u), delta = (w, u), alpha = gamma / delta, beta = 0.
+__global__ void __launch_bounds__(256)
+kb_init_scalars(const double* __restrict__ r, const double* __restrict__ u,
+                const double* __restrict__ w, long long n, double* partials, unsigned* ticket,
+                BState* st) {
+  __shared__ double sred[8];
+  __shared__ bool last;
+  double g = 0.0, d = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    g = fma(r[i], u[i], g);
+    d = fma(w[i], u[i], d);
+  }
+  g = block_sum<256>(g, sred);
+  d = block_sum<256>(d, sred);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = g;
+    partials[2 * blockIdx.x + 1] = d;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0;
+    for (unsigned i = 0; i < gridDim.x; ++i) {
+      a += ((volatile double*)partials)[2 * i];
+      c += ((volatile double*)partials)[2 * i + 1];
+    }
+    BState s = *st;
+    if (!s.done) {
+      if (!isfinite(a) || !isfinite(c) || !(c > 0.0) || !(a > 0.0)) {
+        s.breakdown = 1;
+        s.done = 1;
+      } else {
+        s.gamma = a;
+        s.delta = c;
+        s.alpha = a / c;
+        s.beta = 0.0;
+      }
+    }
     *st = s;
     *ticket = 0u;
   }
@@ -347,33 +435,34 @@ kb_init(const double* __restrict__ b, const double* __restrict__ q, double* __re
 __global__ void __launch_bounds__(256)
 kb_residual(const double* __restrict__ b, const double* __restrict__ q, long long n,
             double* out) {
-  __shared__ double sw[8];
+  __shared__ double sred[8];
   double rr = 0.0, bb = 0.0;
   for (long long i = threadIdx.x; i < n; i += blockDim.x) {
     const double ri = b[i] - q[i];
     rr = fma(ri, ri, rr);
     bb = fma(b[i], b[i], bb);
   }
-  double tot[2] = {rr, bb};
-  for (int k = 0; k < 2; ++k) {
-    double v = warp_sum(tot[k]);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int i = 0; i < 8; ++i) t += sw[i];
-      out[k] = t;
-    }
+  rr = block_sum<256>(rr, sred);
+  bb = block_sum<256>(bb, sred);
+  if (threadIdx.x == 0) {
+    out[0] = rr;
+    out[1] = bb;
   }
 }
 
+template <int MAXN>
 size_t persistent_smem() {
   size_t m = 0;
   m = std::max(m, dgk::cell_smem<2, double>());
   m = std::max(m, dgk::cell_smem<3, double>());
   m = std::max(m, dgk::cell_smem<4, double>());
   m = std::max(m, dgk::cell_smem<5, double>());
+  if (MAXN > 5) {
+    m = std::max(m, dgk::cell_smem<6, double>());
+    m = std::max(m, dgk::cell_smem<7, double>());
+    m = std::max(m, dgk::cell_smem<8, double>());
+    m = std::max(m, dgk::cell_smem<9, double>());
+  }
   return m;
 }
 
@@ -382,26 +471,60 @@ double now_s() {
       .count();
 }
 
-// Autotuner cache: batch signature -> blocks per SM.
+// Autotuner cache: batch signature -> (blocks per SM, tile index), in the
+// process and optionally in the file DG_TUNE_CACHE (one "signature bpsm tile"
+// line per entry; the signature includes the GPU name).
 std::mutex g_tune_mu;
-std::map<std::vector<long long>, int> g_tune;
+std::map<std::string, std::pair<int, int>> g_tune;
+bool g_tune_file_read = false;
+
+void tune_cache_load() {
+  if (g_tune_file_read) return;
+  g_tune_file_read = true;
+  const char* path = std::getenv("DG_TUNE_CACHE");
+  if (path == nullptr || path[0] == 0) return;
+  FILE* f = std::fopen(path, "r");
+  if (f == nullptr) return;
+  char line[4096];
+  while (std::fgets(line, sizeof(line), f)) {
+    char sig[3800];
+    int bpsm = 0, tile = 0;
+    if (std::sscanf(line, "%3799s %d %d", sig, &bpsm, &tile) == 3 && bpsm > 0 && tile >= 0 &&
+        tile < 3)
+      g_tune[sig] = {bpsm, tile};
+  }
+  std::fclose(f);
+}
+
+void tune_cache_store(const std::string& sig, int bpsm, int tile) {
+  g_tune[sig] = {bpsm, tile};
+  const char* path = std::getenv("DG_TUNE_CACHE");
+  if (path == nullptr || path[0] == 0 || sig.size() >= 3800) return;
+  FILE* f = std::fopen(path, "a");
+  if (f == nullptr) return;
+  std::fprintf(f, "%s %d %d\n", sig.c_str(), bpsm, tile);
+  std::fclose(f);
+}
 
 struct Batch {
   std::vector<dg_mesh*> meshes;
-  SampleDev* d_samples = nullptr;
-  int2* d_units = nullptr;
+  SampleDev* d_samples = nullptr;  // 3 x count: one copy per tile choice
+  int2* d_units = nullptr;         // unit lists of the three tile choices, concatenated
+  int unit_off[3] = {0, 0, 0};
+  int nunits[3] = {0, 0, 0};
   BState* d_state = nullptr;
   double* d_part = nullptr;
+  unsigned* d_tickets = nullptr;
   BCtl* d_ctl = nullptr;
   BCtl* h_ctl = nullptr;
   double* d_aux = nullptr;      // init partials, residual outputs
   unsigned* d_ticket = nullptr;
-  int nunits = 0;
   ~Batch() {
     cudaFree(d_samples);
     cudaFree(d_units);
     cudaFree(d_state);
     cudaFree(d_part);
+    cudaFree(d_tickets);
     cudaFree(d_ctl);
     cudaFree(d_aux);
     cudaFree(d_ticket);
@@ -409,62 +532,57 @@ struct Batch {
   }
 };
 
-int launch_persistent(Batch& B, int ns, int blocks, int iters, long long limit, int stall,
-                      cudaStream_t s) {
+template <int BT, int MAXN>
+int launch_persistent(Batch& B, int count, int tsel, int blocks, int iters, long long limit,
+                      int stall, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(BT);
-  cfg.dynamicSmemBytes = persistent_smem();
+  cfg.dynamicSmemBytes = persistent_smem<MAXN>();
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  DG_CUDA(cudaLaunchKernelEx(&cfg, kb_persistent, (const SampleDev*)B.d_samples, ns,
-                             (const int2*)B.d_units, B.nunits, B.d_state, B.d_part, B.d_ctl,
-                             iters, limit, stall));
+  DG_CUDA(cudaLaunchKernelEx(&cfg, kb_persistent<BT, MAXN>,
+                             (const SampleDev*)(B.d_samples + (size_t)tsel * count),
+                             (const int2*)(B.d_units + B.unit_off[tsel]), B.nunits[tsel],
+                             TILES[tsel], B.d_state, B.d_part, B.d_tickets, B.d_ctl, iters,
+                             limit, stall));
   return DG_OK;
 }
 
-}  // namespace
+// Start (or restart) sample i: w = A x, r = b - w, u = M^-1 r, w = A u, scalars.
+int start_sample(Batch& B, const SampleDev& d, dg_mesh* m, const double* b, const double* x,
+                 double rtol, int maxit, int keep_iters, int i, cudaStream_t s) {
+  int rc = dg_launch_apply_f64(m, x, d.w, nullptr, s);
+  if (rc) return rc;
+  kb_init_r<<<256, 256, 0, s>>>(b, d.w, d.r, d.u, d.p, d.s, d.dinv, m->ndofs, rtol, B.d_aux,
+                                B.d_ticket, B.d_state + i, maxit, keep_iters);
+  DG_CUDA(cudaGetLastError());
+  rc = dg_launch_apply_f64(m, d.u, d.w, nullptr, s);
+  if (rc) return rc;
+  kb_init_scalars<<<256, 256, 0, s>>>(d.r, d.u, d.w, m->ndofs, B.d_aux, B.d_ticket,
+                                      B.d_state + i);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
 
-extern "C" int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count,
-                                        const double* const* b, double* const* x, double rtol,
-                                        int maxit, int mode, dg_cg_stats* st, void* stream) {
-  if (mode != DG_CG_FP64 && mode != (DG_CG_FP64 | DG_CG_PRECOND_JACOBI))
-    return dg_fail(DG_ERR_INVALID_ARG,
-                   "dg_cg_solve_batched: mode %d; the batched solver runs DG_CG_FP64, with or "
-                   "without DG_CG_PRECOND_JACOBI", mode);
-  const bool jacobi = (mode & DG_CG_PRECOND_JACOBI) != 0;
-  if (meshes == nullptr || b == nullptr || x == nullptr || count < 1)
-    return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: NULL array or count < 1");
-  if (!(rtol > 0.0) || !(rtol < 1.0))
-    return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: rtol=%g outside (0, 1)", rtol);
-  if (maxit < 1) return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: maxit=%d < 1", maxit);
+template <int BT, int MAXN>
+int solve_batched(const dg_mesh* const* meshes, int count, const double* const* b,
+                  double* const* x, double rtol, int maxit, bool jacobi, int mode,
+                  dg_cg_stats* st, void* stream) {
   const double t0 = now_s();
   Batch B;
   B.meshes.resize(count);
   std::vector<SampleDev> hs(count);
-  std::vector<int2> hu;
-  std::vector<long long> sig;
+  std::vector<int2> hu[3];
+  std::vector<SampleDev> hst3;
+  std::string sig = "bt" + std::to_string(BT) + "_mode" + std::to_string(mode);
+  long long total_dofs = 0;
   for (int s = 0; s < count; ++s) {
     dg_mesh* m = const_cast<dg_mesh*>(meshes[s]);
-    if (m == nullptr || b[s] == nullptr || x[s] == nullptr)
-      return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: NULL mesh or vector (sample %d)", s);
-    if (!m->has_coef)
-      return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: sample %d has no coefficient", s);
-    if (m->n > MAXN_B)
-      return dg_fail(DG_ERR_INVALID_ARG,
-                     "dg_cg_solve_batched: sample %d has degree %d; the batched solver supports "
-                     "degree 1..%d", s, m->k, MAXN_B - 1);
-    if ((const void*)b[s] == (const void*)x[s])
-      return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: b and x alias (sample %d)", s);
-    for (int t = 0; t < s; ++t)
-      if (meshes[t] == meshes[s])
-        return dg_fail(DG_ERR_INVALID_ARG,
-                       "dg_cg_solve_batched: samples %d and %d share a mesh (its workspaces)", t,
-                       s);
     int rc = dg_ensure_solver_ws(m);
     if (rc) return rc;
     B.meshes[s] = m;
@@ -473,7 +591,9 @@ extern "C" int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count,
     d.x = x[s];
     d.r = m->r64;
     d.p = m->p64;
-    d.q = m->q64;
+    d.w = m->q64;
+    d.s = m->s64;
+    d.u = m->r64;  // M = I: u is r itself
     d.U = m->U64;
     d.X = m->X64;
     d.TR = m->TR64;
@@ -485,54 +605,72 @@ extern "C" int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count,
       rc = dg_ensure_diagonal(m, m->solve_stream);
       if (rc) return rc;
       d.dinv = m->dinv64;
+      d.u = m->t64;
     }
     d.ncells = m->ncells;
     d.Nc = m->N;
     d.n = m->n;
-    d.ubeg = (int)hu.size();
-    const int cpu = m->n == 2 ? dgk::Cfg<2>::CPB : m->n == 3 ? dgk::Cfg<3>::CPB
-                  : m->n == 4 ? dgk::Cfg<4>::CPB : dgk::Cfg<5>::CPB;
-    for (long long c = 0; c < m->ncells; c += cpu) hu.push_back(make_int2(s, (int)c));
-    d.uend = (int)hu.size();
-    sig.push_back(m->N);
-    sig.push_back(m->n);
+    total_dofs += m->ndofs;
+    sig += "_" + std::to_string(m->N) + "x" + std::to_string(m->n);
   }
-  sig.push_back(mode);
-  B.nunits = (int)hu.size();
+  for (int t = 0; t < 3; ++t) {
+    for (int s = 0; s < count; ++s) {
+      SampleDev d = hs[s];
+      const int step = TILES[t] * group_cells(d.n);
+      d.ubeg = (int)hu[t].size();
+      for (long long c = 0; c < d.ncells; c += step) hu[t].push_back(make_int2(s, (int)c));
+      d.uend = (int)hu[t].size();
+      hst3.push_back(d);
+    }
+    B.nunits[t] = (int)hu[t].size();
+    B.unit_off[t] = t == 0 ? 0 : B.unit_off[t - 1] + B.nunits[t - 1];
+  }
   cudaStream_t us = (cudaStream_t)stream;
   // a private non-blocking stream (capture needs one); ordered after the caller's work
   cudaStream_t s = B.meshes[0]->solve_stream;
   DG_CUDA(cudaEventRecord(B.meshes[0]->ev, us));
   DG_CUDA(cudaStreamWaitEvent(s, B.meshes[0]->ev, 0));
-
-  DG_CUDA(cudaMalloc(&B.d_samples, sizeof(SampleDev) * count));
-  DG_CUDA(cudaMalloc(&B.d_units, sizeof(int2) * B.nunits));
+  const int nu_all = B.unit_off[2] + B.nunits[2];
+  DG_CUDA(cudaMalloc(&B.d_samples, sizeof(SampleDev) * 3 * count));
+  DG_CUDA(cudaMalloc(&B.d_units, sizeof(int2) * nu_all));
   DG_CUDA(cudaMalloc(&B.d_state, sizeof(BState) * count));
-  DG_CUDA(cudaMalloc(&B.d_part, sizeof(double) * 3 * B.nunits));
+  DG_CUDA(cudaMalloc(&B.d_part, sizeof(double) * 3 * B.nunits[0]));
+  DG_CUDA(cudaMalloc(&B.d_tickets, sizeof(unsigned) * count));
   DG_CUDA(cudaMalloc(&B.d_ctl, sizeof(BCtl)));
   DG_CUDA(cudaMalloc(&B.d_aux, sizeof(double) * 2 * 1024));
   DG_CUDA(cudaMalloc(&B.d_ticket, sizeof(unsigned)));
   DG_CUDA(cudaMallocHost(&B.h_ctl, sizeof(BCtl)));
   *B.h_ctl = BCtl{};
-  DG_CUDA(cudaMemcpyAsync(B.d_samples, hs.data(), sizeof(SampleDev) * count,
+  DG_CUDA(cudaMemcpyAsync(B.d_samples, hst3.data(), sizeof(SampleDev) * 3 * count,
                           cudaMemcpyHostToDevice, s));
-  DG_CUDA(cudaMemcpyAsync(B.d_units, hu.data(), sizeof(int2) * B.nunits, cudaMemcpyHostToDevice,
-                          s));
+  for (int t = 0; t < 3; ++t)
+    DG_CUDA(cudaMemcpyAsync(B.d_units + B.unit_off[t], hu[t].data(), sizeof(int2) * B.nunits[t],
+                            cudaMemcpyHostToDevice, s));
   DG_CUDA(cudaMemsetAsync(B.d_ticket, 0, sizeof(unsigned), s));
+  DG_CUDA(cudaMemsetAsync(B.d_tickets, 0, sizeof(unsigned) * count, s));
   {
-    DGTab<double> t64[MAXN_B - 1];
+    DGTab<double> t64[DG_MAXN - 1];
     DGTab<float> t32;
-    for (int n = 2; n <= MAXN_B; ++n) dg_build_tables(n, 2.0 * n * n, &t64[n - 2], &t32);
+    for (int n = 2; n <= DG_MAXN; ++n) dg_build_tables(n, 2.0 * n * n, &t64[n - 2], &t32);
     DG_CUDA(cudaMemcpyToSymbolAsync(c_btab, t64, sizeof(t64), 0, cudaMemcpyHostToDevice, s));
   }
-  const size_t smem = persistent_smem();
-  DG_CUDA(cudaFuncSetAttribute(kb_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem));
+  const size_t smem = persistent_smem<MAXN>();
+  DG_CUDA(cudaFuncSetAttribute(kb_persistent<BT, MAXN>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int max_bpsm = 0;
-  DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_bpsm, kb_persistent, BT, smem));
+  DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_bpsm, kb_persistent<BT, MAXN>, BT,
+                                                        smem));
   if (max_bpsm < 1)
     return dg_fail(DG_ERR_CUDA, "dg_cg_solve_batched: persistent kernel cannot be resident");
   const int sms = B.meshes[0]->sm_count;
+  {
+    cudaDeviceProp prop;
+    DG_CUDA(cudaGetDeviceProperties(&prop, B.meshes[0]->device));
+    std::string name(prop.name);
+    for (char& ch : name)
+      if (ch == ' ') ch = '_';
+    sig = name + "_" + sig;
+  }
 
   // bounded barrier waits: ~1 s by default; the test hook shortens it and
   // holds one block back so that the waits expire
@@ -544,6 +682,9 @@ extern "C" int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count,
       limit = 1LL << 12;
     }
   }
+  // iterations per production launch: about LAUNCH_SECONDS of work
+  int iters_launch = (int)(LAUNCH_SECONDS * EST_DOF_RATE / (double)(total_dofs > 0 ? total_dofs : 1));
+  iters_launch = iters_launch < 64 ? 64 : iters_launch > 4096 ? 4096 : iters_launch;
 
   std::vector<int> iters_total(count, 0);
   std::vector<int> status(count, DG_OK);
@@ -551,16 +692,12 @@ extern "C" int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count,
   int first_bad = DG_OK;
   const int max_rounds = 5;
   for (int round = 0; round < max_rounds; ++round) {
-    // (re)start the samples that are not finished: r = b - A x, p = r
+    // (re)start the samples that are not finished
     int nstart = 0;
     for (int i = 0; i < count; ++i) {
       if (round > 0 && status[i] != DG_ERR_NOT_CONVERGED) continue;
-      dg_mesh* m = B.meshes[i];
-      int rc = dg_launch_apply_f64(m, x[i], m->q64, nullptr, s);
+      int rc = start_sample(B, hs[i], B.meshes[i], b[i], x[i], rtol, maxit, iters_total[i], i, s);
       if (rc) return rc;
-      kb_init<<<256, 256, 0, s>>>(b[i], m->q64, m->r64, m->p64, hs[i].dinv, m->ndofs, rtol,
-                                  B.d_aux, B.d_ticket, B.d_state + i, maxit, iters_total[i]);
-      DG_CUDA(cudaGetLastError());
       ++nstart;
     }
     if (round > 0 && nstart == 0) break;
@@ -573,63 +710,71 @@ extern "C" int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count,
                                   s));
         }
     }
+    std::vector<BState> h0(count);
+    DG_CUDA(cudaMemcpyAsync(h0.data(), B.d_state, sizeof(BState) * count, cudaMemcpyDeviceToHost,
+                            s));
     DG_CUDA(cudaStreamSynchronize(s));
     BCtl c0 = {};
-    c0.active = count;
+    for (int i = 0; i < count; ++i) c0.active += h0[i].done ? 0 : 1;
     DG_CUDA(cudaMemcpyAsync(B.d_ctl, &c0, sizeof(BCtl), cudaMemcpyHostToDevice, s));
     DG_CUDA(cudaStreamSynchronize(s));
     *B.h_ctl = c0;
 
-    // autotuned blocks per SM; one captured graph per candidate
-    int bpsm = 0;
-    {
-      std::lock_guard<std::mutex> lk(g_tune_mu);
-      auto it = g_tune.find(sig);
-      if (it != g_tune.end()) bpsm = it->second;
+    // autotuned launch shape: (blocks per SM, tile); one captured graph per candidate
+    std::pair<int, int> chosen = {0, 0};
+    if (const char* e = std::getenv("DG_BATCHED_SHAPE")) {  // "blocks_per_sm,tile_index"
+      int bp = 0, ti = -1;
+      if (std::sscanf(e, "%d,%d", &bp, &ti) == 2 && bp >= 1 && ti >= 0 && ti < 3)
+        chosen = {bp < max_bpsm ? bp : max_bpsm, ti};
     }
-    std::vector<int> cands;
-    if (bpsm > 0) cands.push_back(bpsm);
+    if (chosen.first == 0) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      tune_cache_load();
+      auto it = g_tune.find(sig);
+      if (it != g_tune.end() && it->second.first <= max_bpsm) chosen = it->second;
+    }
+    std::vector<std::pair<int, int>> cands;
+    if (chosen.first > 0) cands.push_back(chosen);
     else
-      for (int c = 1; c <= max_bpsm; ++c) cands.push_back(c);
-    // graphs: [c] = production launch (64 iterations), [max_bpsm + 1 + c] = tuning launch
-    std::vector<cudaGraphExec_t> execs(2 * (max_bpsm + 1), nullptr);
-    auto get_exec = [&](int c, bool tune, cudaGraphExec_t* out) -> int {
-      const int slot = tune ? max_bpsm + 1 + c : c;
-      if (!execs[slot]) {
+      for (int t = 0; t < 3; ++t)
+        for (int c = 1; c <= max_bpsm; ++c) cands.push_back({c, t});
+    std::map<std::pair<int, int>, cudaGraphExec_t> execs;  // key: (candidate index, tuning)
+    auto get_exec = [&](int ci, bool tune, cudaGraphExec_t* out) -> int {
+      const auto key = std::make_pair(ci, tune ? 1 : 0);
+      auto f = execs.find(key);
+      if (f == execs.end()) {
         cudaGraph_t g = nullptr;
+        cudaGraphExec_t ex = nullptr;
         DG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        int rc = launch_persistent(B, count, c * sms, tune ? ITERS_TUNE : ITERS_PER_LAUNCH,
-                                   limit, stall, s);
+        int rc = launch_persistent<BT, MAXN>(B, count, cands[ci].second, cands[ci].first * sms,
+                                             tune ? ITERS_TUNE : iters_launch, limit, stall, s);
         cudaError_t ec = cudaStreamEndCapture(s, &g);
         if (rc) {
           if (g) cudaGraphDestroy(g);
           return rc;
         }
         DG_CUDA(ec);
-        ec = cudaGraphInstantiate(&execs[slot], g, 0);
+        ec = cudaGraphInstantiate(&ex, g, 0);
         cudaGraphDestroy(g);
         DG_CUDA(ec);
+        f = execs.emplace(key, ex).first;
       }
-      *out = execs[slot];
+      *out = f->second;
       return DG_OK;
-    };
-    auto destroy_execs = [&]() {
-      for (auto& e : execs)
-        if (e) cudaGraphExecDestroy(e);
     };
     cudaEvent_t e0, e1;
     DG_CUDA(cudaEventCreate(&e0));
     DG_CUDA(cudaEventCreate(&e1));
     double best_t = 1e300;
-    int best_c = cands[0];
+    int best_ci = 0;
     size_t ci = 0;
     int rc = DG_OK;
     for (;;) {
       const bool tuning = ci < cands.size() && cands.size() > 1;
       if (!tuning && ci < cands.size()) ci = cands.size();  // one candidate: nothing to tune
-      const int c = tuning ? cands[ci] : best_c;
+      const int cidx = tuning ? (int)ci : best_ci;
       cudaGraphExec_t ex;
-      rc = get_exec(c, tuning, &ex);
+      rc = get_exec(cidx, tuning, &ex);
       if (rc) break;
       const unsigned long long before = B.h_ctl->iterations_run;
       cudaError_t ec = cudaEventRecord(e0, s);
@@ -656,20 +801,20 @@ extern "C" int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count,
           const double per = ms / (double)ran;
           if (per < best_t) {
             best_t = per;
-            best_c = c;
+            best_ci = (int)ci;
           }
         }
         ++ci;
         if (ci == cands.size() && best_t < 1e300) {
           std::lock_guard<std::mutex> lk(g_tune_mu);
-          g_tune[sig] = best_c;
+          tune_cache_store(sig, cands[best_ci].first, cands[best_ci].second);
         }
       }
       if (B.h_ctl->active == 0) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    destroy_execs();
+    for (auto& kv : execs) cudaGraphExecDestroy(kv.second);
     if (rc) return rc;
 
     // per-sample outcome, with the residual recomputed in FP64
@@ -717,6 +862,44 @@ extern "C" int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count,
     }
   }
   return first_bad;
+}
+
+}  // namespace
+
+extern "C" int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count,
+                                        const double* const* b, double* const* x, double rtol,
+                                        int maxit, int mode, dg_cg_stats* st, void* stream) {
+  if (mode != DG_CG_FP64 && mode != (DG_CG_FP64 | DG_CG_PRECOND_JACOBI))
+    return dg_fail(DG_ERR_INVALID_ARG,
+                   "dg_cg_solve_batched: mode %d; the batched solver runs DG_CG_FP64, with or "
+                   "without DG_CG_PRECOND_JACOBI", mode);
+  const bool jacobi = (mode & DG_CG_PRECOND_JACOBI) != 0;
+  if (meshes == nullptr || b == nullptr || x == nullptr || count < 1)
+    return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: NULL array or count < 1");
+  if (!(rtol > 0.0) || !(rtol < 1.0))
+    return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: rtol=%g outside (0, 1)", rtol);
+  if (maxit < 1) return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: maxit=%d < 1", maxit);
+  int maxn = 0;
+  for (int s = 0; s < count; ++s) {
+    const dg_mesh* m = meshes[s];
+    if (m == nullptr || b[s] == nullptr || x[s] == nullptr)
+      return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: NULL mesh or vector (sample %d)", s);
+    if (!m->has_coef)
+      return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: sample %d has no coefficient", s);
+    if ((const void*)b[s] == (const void*)x[s])
+      return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: b and x alias (sample %d)", s);
+    if (m->lineop64 == nullptr)
+      return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: sample %d has no line operators", s);
+    for (int t = 0; t < s; ++t)
+      if (meshes[t] == meshes[s])
+        return dg_fail(DG_ERR_INVALID_ARG,
+                       "dg_cg_solve_batched: samples %d and %d share a mesh (its workspaces)", t,
+                       s);
+    maxn = m->n > maxn ? m->n : maxn;
+  }
+  if (maxn <= 5)
+    return solve_batched<128, 5>(meshes, count, b, x, rtol, maxit, jacobi, mode, st, stream);
+  return solve_batched<256, DG_MAXN>(meshes, count, b, x, rtol, maxit, jacobi, mode, st, stream);
 }
 
 extern "C" int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, const double* const* b,

@@ -66,6 +66,7 @@ struct dg_mesh {
   long long ndofs;  // N^3 n^3
   double h;
   double sigma;
+  int dirichlet_mask;  // bit f: boundary side f (x-, x+, y-, y+, z-, z+) is Dirichlet
   int device;
   int sm_count;
   DGTab<double> tab64;
@@ -101,7 +102,7 @@ struct dg_mesh {
   cudaEvent_t hev[3 * DG_HOST_SLABS + 1];
 
   // solver workspaces, lazily allocated
-  double *r64, *p64, *q64, *t64;
+  double *r64, *p64, *q64, *t64, *s64;  // t64, s64: u = M^-1 r and s = A p of the batched solver
   float *d32, *r32, *p32, *q32;
   double* partials;       // reduction partials (DG_RED_BLOCKS doubles x DG_RED_SUMS)
   double* partials_cells; // one partial per cell block (fused FP32 mixed kernels)
@@ -134,9 +135,11 @@ __global__ void k_coef_cells(const double* __restrict__ K, double* __restrict__ 
                              float* __restrict__ kt32, double* __restrict__ kbar,
                              long long ncells, int n, double h, int* flag,
                              const __grid_constant__ DGTab<double> tab);
+// (dmask: bit f set when boundary side f is Dirichlet; the boundary faces of
+// the other sides carry zero flux, gamma = 0)
 __global__ void k_coef_faces(const double* __restrict__ kbar, double* __restrict__ gh64,
                              float* __restrict__ gh32, double* __restrict__ dgam, int Nc,
-                             double h);
+                             double h, int dmask);
 
 // error reporting (dg_mesh.cu)
 int dg_fail(int code, const char* fmt, ...);

@@ -59,10 +59,12 @@ __global__ void k_coef_cells(const double* __restrict__ K, double* __restrict__ 
 }
 
 // One thread per cell: h*gamma (FP64, and FP32 unless gh32 is NULL) and, unless
-// dgam is NULL, d gamma / d log Kbar_c on its six faces.
+// dgam is NULL, d gamma / d log Kbar_c on its six faces.  A boundary face on a
+// side whose bit is clear in dmask carries zero flux (homogeneous Neumann): no
+// face term at all, i.e. gamma = 0 there.
 __global__ void k_coef_faces(const double* __restrict__ kbar, double* __restrict__ gh64,
                              float* __restrict__ gh32, double* __restrict__ dgam, int Nc,
-                             double h) {
+                             double h, int dmask) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nc = (long long)Nc * Nc * Nc;
   if (c >= nc) return;
@@ -78,9 +80,12 @@ __global__ void k_coef_faces(const double* __restrict__ kbar, double* __restrict
       const double kn = kbar[upper ? c + stride[d] : c - stride[d]];
       g = 2.0 * k * kn / (k + kn);
       dg = g * kn / (k + kn);
-    } else {
+    } else if ((dmask >> f) & 1) {
       g = k;
       dg = k;
+    } else {
+      g = 0.0;
+      dg = 0.0;
     }
     gh64[c * 6 + f] = h * g;
     if (gh32 != nullptr) gh32[c * 6 + f] = (float)(h * g);
@@ -100,7 +105,7 @@ static void free_all(dg_mesh* m) {
   void* ptrs[] = {m->kt64, m->kt32, m->gh64, m->gh32, m->dgam, m->kbar, m->dflag, m->fw64, m->fw32, m->lineop64, m->diag64, m->dinv64, m->dinv32,
                   m->U64,  m->X64,  m->TR64, m->U32,  m->X32,  m->TR32, m->U64b,
                   m->X64b, m->TR64b, m->hx_dev, m->hy_dev, m->r64, m->p64, m->q64,
-                  m->t64,  m->d32,  m->r32, m->p32, m->q32, m->partials, m->state,
+                  m->t64,  m->s64, m->d32,  m->r32, m->p32, m->q32, m->partials, m->state,
                   m->partials_cells};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -136,6 +141,7 @@ extern "C" int dg_create_mesh(int n_cells, int degree, dg_mesh** out) {
   m->ndofs = m->ncells * n3;
   m->h = 1.0 / n_cells;
   m->sigma = 2.0 * (degree + 1) * (degree + 1);
+  m->dirichlet_mask = DG_BC_DIRICHLET;
   dg_build_tables(m->n, m->sigma, &m->tab64, &m->tab32);
   cudaError_t e = cudaGetDevice(&m->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, m->device);
@@ -194,6 +200,21 @@ extern "C" int dg_mesh_info(const dg_mesh* m, long long* n_dofs, long long* n_ce
   return DG_OK;
 }
 
+extern "C" int dg_set_boundary(dg_mesh* m, int dirichlet_mask) {
+  if (m == nullptr) return dg_fail(DG_ERR_INVALID_ARG, "dg_set_boundary: mesh is NULL");
+  if (dirichlet_mask < 0 || dirichlet_mask > 0x3F)
+    return dg_fail(DG_ERR_INVALID_ARG, "dg_set_boundary: mask 0x%x outside 0..0x3f",
+                   dirichlet_mask);
+  if (dirichlet_mask == 0)
+    return dg_fail(DG_ERR_INVALID_ARG,
+                   "dg_set_boundary: at least one side must be Dirichlet (the operator would "
+                   "be singular)");
+  m->dirichlet_mask = dirichlet_mask;
+  m->has_coef = false;  // the face weights depend on it: set the coefficient again
+  m->has_diag = false;
+  return DG_OK;
+}
+
 int dg_ensure_grad_ws(dg_mesh* m) {
   if (m->U64b) return DG_OK;
   const size_t nd = (size_t)m->ndofs;
@@ -211,6 +232,7 @@ int dg_ensure_solver_ws(dg_mesh* m) {
   DG_CUDA(dmalloc(&m->p64, nd));
   DG_CUDA(dmalloc(&m->q64, nd));
   DG_CUDA(dmalloc(&m->t64, nd));
+  DG_CUDA(dmalloc(&m->s64, nd));
   DG_CUDA(dmalloc(&m->d32, nd));
   DG_CUDA(dmalloc(&m->r32, nd));
   DG_CUDA(dmalloc(&m->p32, nd));
@@ -244,7 +266,8 @@ extern "C" int dg_set_coefficient(dg_mesh* m, const double* K, void* stream) {
   }
   {
     const unsigned blocks = (unsigned)((m->ncells + 255) / 256);
-    k_coef_faces<<<blocks, 256, 0, s>>>(m->kbar, m->gh64, m->gh32, m->dgam, m->N, m->h);
+    k_coef_faces<<<blocks, 256, 0, s>>>(m->kbar, m->gh64, m->gh32, m->dgam, m->N, m->h,
+                                        m->dirichlet_mask);
     dgk::k_face_weights<double><<<blocks, 256, 0, s>>>(m->gh64, m->fw64, m->N, m->n, m->tab64);
     dgk::k_face_weights<float><<<blocks, 256, 0, s>>>(m->gh64, m->fw32, m->N, m->n, m->tab64);
     DG_CUDA(cudaGetLastError());

@@ -26,6 +26,7 @@
 #include <cstdlib>
 
 #include "dg_apply_impl.cuh"
+#include "dg_pair32.cuh"
 
 namespace dgk {
 
@@ -376,6 +377,325 @@ k_cell32(const float* __restrict__ p, const float* __restrict__ TR, const float*
 
 
 
+// ---------------------------------------------------------------------------
+// k_cell32x2: the same computation as k_cell32 on pairs of consecutive cells
+// (a = c0 + 2j, b = a + 1), each value a packed FP32 pair (dg_pair32.cuh): one
+// FFMA2 / FADD2 / FMUL2, one 64-bit shared-memory access and one address
+// computation serve both cells.  Every lane computes exactly what the scalar
+// kernel computes for its cell, with the same FP32 operations in the same
+// order, so the result is the scalar kernel's.  Per-lane differences (a face on
+// the boundary for one cell of the pair only, a last pair with one cell) are
+// handled with per-lane data instead of branches: a boundary lane's neighbour
+// trace is zero, and its derivative term and derivative weight take the factor
+// e = 2 (e = 1 inside), which turns the interior flux into the one-sided one.
+// The block then works as k_cell32: pass 1 of p in shared memory, the cell
+// phase with own traces formed in the line threads and the neighbours' traces
+// from the direction kernel, and <p, q> folded into the epilogue, where each
+// z-line thread still holds its z-line of p and of q in registers.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+k_cell32x2(const float* __restrict__ pg, const float* __restrict__ TR,
+           const float* __restrict__ kt, const float* __restrict__ gh, float* __restrict__ qg,
+           long long ncells, int Nc, double* __restrict__ partials, DGCGState* st,
+           const __grid_constant__ DGTab<F2> tab) {
+  constexpr int C = Cfg<N>::CPB, N2 = N * N, N3 = N * N * N, NT = Cfg<N>::THREADS;
+  constexpr float S2 = 4.0f * N * N;  // 2 sigma, sigma = 2 (k+1)^2
+  if (st->done || st->iters >= st->maxit) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  F2* su = reinterpret_cast<F2*>(smem_raw);
+  F2* sx = su + C * N3;
+  F2* sr = sx + C * N3;
+  F2* sk = sr + C * N3;
+  __shared__ float rh[NT], rl[NT];
+  __shared__ bool is_last;
+  __shared__ int sbase[3];
+  const long long c0 = (long long)blockIdx.x * (2 * C);
+  const int lc = threadIdx.x / N2;
+  const int t2 = threadIdx.x - lc * N2;
+  const int p = t2 % N, q = t2 / N;
+  const long long ca = c0 + 2 * lc, cb = ca + 1;
+  const bool va = ca < ncells, vb = cb < ncells;
+  const int o = lc * N3;
+  if (threadIdx.x == 0) {
+    const unsigned cu = (unsigned)c0, n = (unsigned)Nc;
+    sbase[0] = (int)(cu % n);
+    sbase[1] = (int)((cu / n) % n);
+    sbase[2] = (int)(cu / n / n);
+  }
+  // h w K of the block's cell pairs into registers (stored to shared memory
+  // after pass 1), in flight together with the z-line loads of p
+  F2 kreg[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int t = threadIdx.x + k * NT;  // < C N3 = N NT
+    const int pr = t / N3, pos = t - pr * N3;
+    const long long c = c0 + 2 * pr;
+    kreg[k] = F2(c < ncells ? kt[c * N3 + pos] : 0.0f, c + 1 < ncells ? kt[(c + 1) * N3 + pos] : 0.0f);
+  }
+  // pass 1 in shared memory.  z-lines: thread owns (i = p, j = q); it loads its
+  // z-line of p (both cells) and keeps it for <p, q>
+  F2 preg[N];
+  {
+    F2 u[N];
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      const int idx = l * N2 + q * N + p;
+      preg[l] = F2(va ? pg[ca * N3 + idx] : 0.0f, vb ? pg[cb * N3 + idx] : 0.0f);
+    }
+    b_fwd<N>(tab, preg, u);
+#pragma unroll
+    for (int e = 0; e < N; ++e) su[o + e * N2 + q * N + p] = u[e];
+  }
+  __syncthreads();
+  {  // y-lines: (i = p, e = q)
+    F2 v[N], u[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = su[o + q * N2 + j * N + p];
+    b_fwd<N>(tab, v, u);
+#pragma unroll
+    for (int b = 0; b < N; ++b) su[o + q * N2 + b * N + p] = u[b];
+  }
+  __syncthreads();
+  {  // x-lines: (b = p, e = q); X (x-modal) kept in sx, nodal values in su
+    F2 X[N], u[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) X[i] = su[o + q * N2 + p * N + i];
+#pragma unroll
+    for (int i = 0; i < N; ++i) sx[o + q * N2 + p * N + i] = X[i];
+    b_fwd<N>(tab, X, u);
+#pragma unroll
+    for (int a = 0; a < N; ++a) su[o + q * N2 + p * N + a] = u[a];
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) sk[threadIdx.x + k * NT] = kreg[k];
+  // cell coordinates of both lanes; interior flags as bits (face f: bit f for
+  // lane a, bit 8 + f for lane b)
+  int cxa = sbase[0] + 2 * lc, cya = sbase[1], cza = sbase[2];
+  while (cxa >= Nc) {
+    cxa -= Nc;
+    if (++cya == Nc) {
+      cya = 0;
+      ++cza;
+    }
+  }
+  int cxb = cxa + 1, cyb = cya, czb = cza;
+  if (cxb == Nc) {
+    cxb = 0;
+    if (++cyb == Nc) {
+      cyb = 0;
+      ++czb;
+    }
+  }
+  const long long sy = Nc, sz = (long long)Nc * Nc;
+  const int pt = p + N * q;
+  const float hw2 = 0.5f * tab.w[pt % N].v.x * tab.w[pt / N].v.x;
+  // face f's neighbour trace (value, derivative) and weight W/2 for both lanes;
+  // zero trace on a boundary lane
+  auto face = [&](int f, bool ina, bool inb, long long cna, long long cnb, F2& un, F2& gn,
+                  F2& wh, F2& e) {
+    float ua = 0.f, ga = 0.f, ub = 0.f, gb = 0.f;
+    if (ina) load_trace<N>(TR, cna, f ^ 1, pt, ua, ga);
+    if (inb) load_trace<N>(TR, cnb, f ^ 1, pt, ub, gb);
+    un = F2(ua, ub);
+    gn = F2(ga, gb);
+    wh = F2(va ? hw2 * gh[ca * 6 + f] : 0.0f, vb ? hw2 * gh[cb * 6 + f] : 0.0f);
+    e = F2(ina ? 1.0f : 2.0f, inb ? 1.0f : 2.0f);
+  };
+  F2 un[4], gn[4], wh[4], ee[4];  // faces z-, z+, y-, y+ (then x-, x+ in slots 0, 1)
+  face(4, cza > 0, czb > 0, ca - sz, cb - sz, un[0], gn[0], wh[0], ee[0]);
+  face(5, cza < Nc - 1, czb < Nc - 1, ca + sz, cb + sz, un[1], gn[1], wh[1], ee[1]);
+  face(2, cya > 0, cyb > 0, ca - sy, cb - sy, un[2], gn[2], wh[2], ee[2]);
+  face(3, cya < Nc - 1, cyb < Nc - 1, ca + sy, cb + sy, un[3], gn[3], wh[3], ee[3]);
+  __syncthreads();
+  // flux of one face point from the own trace (uo, go) and the face data:
+  // cv multiplies the test value, -cd the test derivative
+  auto flux = [&](bool upper, F2 uo, F2 go, F2 unf, F2 gnf, F2 whf, F2 ef, F2& cv, F2& cd) {
+    const F2 J = upper ? uo - unf : unf - uo;
+    const F2 G = fma(ef, go, gnf);
+    const F2 tt = upper ? fma(F2(S2), J, -G) : fma(F2(-S2), J, G);
+    cv = whf * tt;
+    cd = (whf * ef) * J;
+  };
+  // z-lines then y-lines: collocation derivative, h w K, transpose, own and
+  // neighbour face terms
+#pragma unroll
+  for (int dir = 0; dir < 2; ++dir) {
+    const int base = (dir == 0) ? (q * N + p) : (q * N2 + p);
+    const int step = (dir == 0) ? N2 : N;
+    F2 u[N], r[N], kg[N];
+#pragma unroll
+    for (int e = 0; e < N; ++e) u[e] = su[o + base + e * step];
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+      F2 g = tab.D[e][0] * u[0];
+#pragma unroll
+      for (int f = 1; f < N; ++f) g = fma(tab.D[e][f], u[f], g);
+      kg[e] = sk[o + base + e * step] * g;
+    }
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+      F2 acc = (dir == 0) ? tab.D[0][e] * kg[0] : fma(tab.D[0][e], kg[0], sr[o + base + e * step]);
+#pragma unroll
+      for (int f = 1; f < N; ++f) acc = fma(tab.D[f][e], kg[f], acc);
+      r[e] = acc;
+    }
+    F2 vm = tab.l0[0] * u[0], vp = tab.l1[0] * u[0];
+    F2 gm = tab.dl0[0] * u[0], gp = tab.dl1[0] * u[0];
+#pragma unroll
+    for (int e = 1; e < N; ++e) {
+      vm = fma(tab.l0[e], u[e], vm);
+      vp = fma(tab.l1[e], u[e], vp);
+      gm = fma(tab.dl0[e], u[e], gm);
+      gp = fma(tab.dl1[e], u[e], gp);
+    }
+    const int su_ = 2 * dir + 1, sl_ = 2 * dir;  // slots of the upper and lower face
+    F2 cv1, cd1, cv0, cd0;
+    flux(true, vp, gp, un[su_], gn[su_], wh[su_], ee[su_], cv1, cd1);
+    flux(false, vm, gm, un[sl_], gn[sl_], wh[sl_], ee[sl_], cv0, cd0);
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+      F2 acc = fma(tab.l1[e], cv1, r[e]);
+      acc = fma(-tab.dl1[e], cd1, acc);
+      acc = fma(tab.l0[e], cv0, acc);
+      r[e] = fma(-tab.dl0[e], cd0, acc);
+    }
+#pragma unroll
+    for (int e = 0; e < N; ++e) sr[o + base + e * step] = r[e];
+    if (dir == 1) {  // the x-faces' data, in flight during the barrier
+      face(0, cxa > 0, cxb > 0, ca - 1, cb - 1, un[0], gn[0], wh[0], ee[0]);
+      face(1, cxa < Nc - 1, cxb < Nc - 1, ca + 1, cb + 1, un[1], gn[1], wh[1], ee[1]);
+    }
+    __syncthreads();
+  }
+  {  // x-lines: (b = p, e = q); result x-modal, yz-nodal
+    const int base = q * N2 + p * N;
+    F2 X[N], rr[N], R[N], g[N], kg[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      X[i] = sx[o + base + i];
+      rr[i] = sr[o + base + i];
+    }
+    bd_fwd<N>(tab, X, g);
+#pragma unroll
+    for (int a = 0; a < N; ++a) kg[a] = sk[o + base + a] * g[a];
+    bt_bdt<N>(tab, rr, kg, R);
+    F2 Se = X[0], So = tab.a1[1] * X[1], Do = tab.d1[1] * X[1], De = F2(0.0f);
+#pragma unroll
+    for (int i = 2; i < N; i += 2) Se = fma(tab.a1[i], X[i], Se);
+#pragma unroll
+    for (int i = 3; i < N; i += 2) So = fma(tab.a1[i], X[i], So);
+#pragma unroll
+    for (int i = 3; i < N; i += 2) Do = fma(tab.d1[i], X[i], Do);
+    if (N > 2) {
+      De = tab.d1[2] * X[2];
+#pragma unroll
+      for (int i = 4; i < N; i += 2) De = fma(tab.d1[i], X[i], De);
+    }
+    F2 cv1, cd1, cv0, cd0;
+    flux(true, Se + So, Do + De, un[1], gn[1], wh[1], ee[1], cv1, cd1);
+    flux(false, Se - So, Do - De, un[0], gn[0], wh[0], ee[0], cv0, cd0);
+    const F2 spl = cv1 + cv0, smn = cv1 - cv0;
+    const F2 dpl = cd1 + cd0, dmn = cd1 - cd0;
+    R[0] = R[0] + spl;
+#pragma unroll
+    for (int i = 1; i < N; ++i) {
+      if (i % 2 == 0)
+        R[i] = fma(tab.a1[i], spl, fma(-tab.d1[i], dmn, R[i]));
+      else
+        R[i] = fma(tab.a1[i], smn, fma(-tab.d1[i], dpl, R[i]));
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) sx[o + base + i] = R[i];
+  }
+  __syncthreads();
+  {  // back along y: (i = p, e = q)
+    F2 v[N], R[N];
+#pragma unroll
+    for (int b = 0; b < N; ++b) v[b] = sx[o + q * N2 + b * N + p];
+    b_bwd<N>(tab, v, R);
+#pragma unroll
+    for (int j = 0; j < N; ++j) sx[o + q * N2 + j * N + p] = R[j];
+  }
+  __syncthreads();
+  // back along z: (i = p, j = q), the thread's z-line of q: store it and fold
+  // <p, q> over it (exact products, compensated float-float sums per lane)
+  F2 hi = F2(0.0f), lo = F2(0.0f);
+  {
+    F2 v[N], R[N];
+#pragma unroll
+    for (int e = 0; e < N; ++e) v[e] = sx[o + e * N2 + q * N + p];
+    b_bwd<N>(tab, v, R);
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      const int idx = l * N2 + q * N + p;
+      if (va) qg[ca * N3 + idx] = R[l].v.x;
+      if (vb) qg[cb * N3 + idx] = R[l].v.y;
+      const F2 pr = preg[l] * R[l];
+      const F2 er = fma(preg[l], R[l], -pr);  // preg R = pr + er exactly
+      const F2 s1 = hi + pr;
+      const F2 bb = s1 - hi;
+      const F2 t1 = (hi - (s1 - bb)) + (pr - bb);
+      hi = s1;
+      lo = lo + (t1 + er);
+    }
+  }
+  {  // combine the lanes
+    float s1, t1;
+    two_sum_f(hi.v.x, hi.v.y, s1, t1);
+    rh[threadIdx.x] = s1;
+    rl[threadIdx.x] = (lo.v.x + lo.v.y) + t1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float h = rh[threadIdx.x], l = rl[threadIdx.x];
+    for (int i = threadIdx.x + 32; i < NT; i += 32) {
+      float s1, t1;
+      two_sum_f(h, rh[i], s1, t1);
+      h = s1;
+      l += t1 + rl[i];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h, off);
+      const float ol = __shfl_xor_sync(0xffffffffu, l, off);
+      float s1, t1;
+      two_sum_f(h, oh, s1, t1);
+      h = s1;
+      l += ol + t1;
+    }
+    if (threadIdx.x == 0) {
+      partials[blockIdx.x] = (double)h + (double)l;
+      __threadfence();
+      is_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  __shared__ double rd[NT];
+  double a = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) a += ((volatile double*)partials)[b];
+  rd[threadIdx.x] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < NT; ++i) tot += rd[i];
+    st->pq = tot;
+    if (!(tot > 0.0) || !isfinite(tot)) {
+      st->breakdown = 1;
+      st->done = 1;
+      st->ru_skip = 1;
+    } else {
+      const double rho = st->rho_new;  // k_dir32_bulk has used beta; commit the new rho
+      st->rho = rho;
+      st->restart = 0;
+      st->alpha = rho / tot;
+    }
+    st->ticket = 0u;
+  }
+}
+
 template <int N>
 struct Mixed32F {
   template <typename T>
@@ -397,10 +717,20 @@ struct Mixed32F {
       k_dir32_bulk<N, false><<<gb, Dir32Bulk<N, false>::THREADS, Dir32Bulk<N, false>::SMEM, s>>>(
           m->r32, m->p32, m->TR32, dinv, m->ncells, m->state, limit, stall_now ? 1 : 0,
           m->tab32);
-    const size_t sm2 = sizeof(float) * 4 * C * N3;
-    k_cell32<N><<<blocks, Cfg<N>::THREADS, sm2, s>>>(m->p32, m->TR32, m->kt32, m->gh32, m->q32,
-                                                     m->ncells, m->N, m->partials_cells,
-                                                     m->state, m->tab32);
+    const char* pc2 = getenv("DG_FP32_CELL_PAIR");
+    if (pc2 == nullptr || pc2[0] != '1') {
+      const size_t sm2 = sizeof(float) * 4 * C * N3;
+      k_cell32<N><<<blocks, Cfg<N>::THREADS, sm2, s>>>(m->p32, m->TR32, m->kt32, m->gh32,
+                                                       m->q32, m->ncells, m->N,
+                                                       m->partials_cells, m->state, m->tab32);
+    } else {
+      DGTab<F2> tab2;
+      pair_tables(m->tab32, &tab2);
+      const unsigned blocks2 = (unsigned)((m->ncells + 2 * C - 1) / (2 * C));
+      k_cell32x2<N><<<blocks2, Cfg<N>::THREADS, sizeof(F2) * 4 * C * N3, s>>>(
+          m->p32, m->TR32, m->kt32, m->gh32, m->q32, m->ncells, m->N, m->partials_cells,
+          m->state, tab2);
+    }
     return cudaGetLastError();
   }
 };
@@ -412,6 +742,12 @@ struct PrepareMixed32F {
   template <typename T>
   static cudaError_t run(dg_mesh* m) {
     const long long ngroups = (m->ncells + Dir32Bulk<N, false>::G - 1) / Dir32Bulk<N, false>::G;
+    {
+      cudaError_t e = cudaFuncSetAttribute(k_cell32x2<N>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(F2) * 4 * Cfg<N>::CPB * N * N * N));
+      if (e != cudaSuccess) return e;
+    }
     for (int pc = 0; pc < 2; ++pc) {
       const void* fn = pc ? (const void*)k_dir32_bulk<N, true> : (const void*)k_dir32_bulk<N, false>;
       const size_t smem = pc ? Dir32Bulk<N, true>::SMEM : Dir32Bulk<N, false>::SMEM;

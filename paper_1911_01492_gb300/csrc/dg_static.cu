@@ -132,7 +132,7 @@ extern "C" int dg_apply_static(int n_cells, int degree, const double* K, const d
   k_coef_cells<<<(unsigned)((ncells * 32 + 255) / 256), 256, 0, s>>>(K, kt, nullptr, kbar, ncells,
                                                                      n, h, flag, tab);
   k_coef_faces<<<(unsigned)((ncells + 255) / 256), 256, 0, s>>>(kbar, gh, nullptr, nullptr,
-                                                                n_cells, h);
+                                                                n_cells, h, DG_BC_DIRICHLET);
   dgk::k_face_weights<double><<<(unsigned)((ncells + 255) / 256), 256, 0, s>>>(gh, FW, n_cells, n,
                                                                               tab);
   DG_CUDA(cudaGetLastError());

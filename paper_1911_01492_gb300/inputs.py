@@ -114,3 +114,47 @@ def lognormal_coefficient(n_cells: int, degree: int, seed: int,
     g = g.reshape(N, n, N, n, N, n)            # (cx, a, cy, b, cz, e)
     g = g.transpose(4, 2, 0, 5, 3, 1)          # (cz, cy, cx, e, b, a)
     return np.exp(np.ascontiguousarray(g).reshape(-1))
+
+
+def values_at_gauss_points(n_cells: int, degree: int, func) -> np.ndarray:
+    """func(x, y, z) evaluated at every volume Gauss point of the mesh (the
+    n = degree + 1 point Gauss-Legendre rule per direction, mapped to each
+    cell), in the [c][e][b][a] layout of K.  Used for given data such as a
+    source term f or a prescribed coefficient."""
+    N, n = n_cells, degree + 1
+    t, _ = np.polynomial.legendre.leggauss(n)
+    xi = 0.5 * (t + 1.0)
+    h = 1.0 / N
+    pos = (np.arange(N)[:, None] + xi[None, :]).reshape(-1) * h     # slot cx*n + a
+    X = pos[None, None, :]
+    Y = pos[None, :, None]
+    Z = pos[:, None, None]
+    v = np.broadcast_to(func(X, Y, Z), (N * n, N * n, N * n))      # [iz, iy, ix]
+    v = v.reshape(N, n, N, n, N, n)                                  # (cz, e, cy, b, cx, a)
+    v = v.transpose(0, 2, 4, 1, 3, 5)                                # (cz, cy, cx, e, b, a)
+    return np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+
+
+def lognormal_on_levels(levels, seed: int, corr_len: float = 0.1,
+                        variance: float = 1.0):
+    """One lognormal realization K = exp(G) seen by several meshes (the coupled
+    samples of a multilevel Monte-Carlo difference Q_l - Q_{l-1}).
+
+    levels: list of (n_cells, degree).  G is sampled once, on the uniform
+    M^3 grid of the finest level (M = max n_cells * (degree + 1)), and every
+    level's Gauss point takes the value of the grid slot that contains it.
+    Returns one flat float64 array per level in the [c][e][b][a] layout.
+    """
+    M = max(N * (k + 1) for N, k in levels)
+    g, _ = gaussian_random_field(M, seed, corr_len, variance)    # g[ix, iy, iz]
+    out = []
+    for N, k in levels:
+        n = k + 1
+        t, _ = np.polynomial.legendre.leggauss(n)
+        xi = 0.5 * (t + 1.0)
+        pos = (np.arange(N)[:, None] + xi[None, :]).reshape(-1) / N   # cx*n + a
+        slot = np.minimum((pos * M).astype(np.int64), M - 1)
+        v = g[np.ix_(slot, slot, slot)]                  # [ix, iy, iz] over (cx,a),(cy,b),(cz,e)
+        v = v.reshape(N, n, N, n, N, n).transpose(4, 2, 0, 5, 3, 1)   # (cz, cy, cx, e, b, a)
+        out.append(np.exp(np.ascontiguousarray(v).reshape(-1)))
+    return out

@@ -177,3 +177,14 @@ def test_full_size_64cubed_q3_fp32_sampled_cells(dg):
     cells = np.unique(np.concatenate([corners, rng.choice(N ** 3, 193, replace=False)]))
     yref = SIPG(N, k).apply(K, x32.astype(np.float64), cells=cells)
     assert relmax(y[cells], yref) <= TOL32
+
+
+@pytest.mark.parametrize("N,k", [(1, 1), (3, 2), (5, 4), (2, 8), (7, 3)])
+def test_load_vector_matches_oracle(dg, N, k):
+    import torch
+    f = lambda x, y, z: np.sin(np.pi * x) * np.cos(2.0 * y) + z * z * x + 0.5
+    F = inputs.values_at_gauss_points(N, k, f)
+    m = dg.Mesh(N, k)       # no coefficient needed
+    b = m.load_vector(torch.from_numpy(F).cuda()).cpu().numpy()
+    bref = SIPG(N, k).load_vector(f)
+    assert relmax(b, bref) <= TOL64

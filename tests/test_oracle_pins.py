@@ -563,3 +563,104 @@ def test_face_weights_of_a_varying_coefficient_in_closed_form():
     # the matrix-free apply uses the same face weights as the assembly
     x = inputs.uniform_vector(N, k, 3)
     assert np.abs(D.apply(K, x) - A @ x).max() <= 1e-12 * np.abs(A @ x).max()
+
+
+# --------------------------------------------------------------------------
+# The Section 5 flow problem: -div(k grad p) = 0, p = 1 on x = 0, p = 0 on
+# x = 1, zero flux on the other faces; quantity of interest = total flux
+# through the inlet.  For k depending on x only (constant in each layer of
+# cells) the exact solution is piecewise linear in x, lies in the DG space, and
+# satisfies the SWIPDG face terms exactly (the harmonic-mean face weight times
+# the average derivative equals the continuous flux), so the discrete solution
+# equals it and the inlet flux is the series conductance 1 / sum_i (h / k_i).
+# --------------------------------------------------------------------------
+
+def _layered(N, k, kx):
+    n3 = (k + 1) ** 3
+    c = np.arange(N ** 3)
+    return np.repeat(np.asarray(kx)[c % N], n3)
+
+
+@pytest.mark.parametrize("N,k", [(1, 1), (4, 1), (4, 2), (3, 3)])
+def test_flow_layered_coefficient_has_the_series_flux(N, k):
+    rng = np.random.default_rng(N * 10 + k)
+    kx = np.exp(rng.standard_normal(N))
+    K = _layered(N, k, kx)
+    D = SIPG(N, k, bc="flow_x")
+    g = (1.0, 0.0, 0.0, 0.0, 0.0, 0.0)
+    A = D.assemble(K).tocsc()
+    u = spla.spsolve(A, D.dirichlet_rhs(K, g))
+    h = D.h
+    F = 1.0 / np.sum(h / kx)
+    q_in = D.boundary_flux(K, u, 0, 1.0)
+    q_out = D.boundary_flux(K, u, 1, 0.0)
+    assert abs(q_in - F) <= 1e-10 * F
+    assert abs(q_out + F) <= 1e-10 * F
+    # the discrete solution is the exact piecewise-linear pressure
+    p_left = 1.0 - np.concatenate(([0.0], np.cumsum(F * h / kx)))[:-1]
+    t, _ = np.polynomial.legendre.leggauss(k + 1)
+    xi = 0.5 * (t + 1.0)
+    n = k + 1
+    L = np.array([[legendre(i, s) for i in range(n)] for s in xi])
+    uc = u.reshape(N ** 3, n, n, n)                    # [c][l][j][i]
+    vals = np.einsum("clji,ai,bj,el->ceba", uc, L, L, L)   # [c][e][b][a]
+    c = np.arange(N ** 3)
+    cx = c % N
+    exact = p_left[cx][:, None] - (F / kx[cx])[:, None] * h * xi[None, :]
+    assert np.abs(vals - exact[:, None, None, :]).max() <= 1e-10
+
+
+def test_flow_inlet_and_outlet_flux_balance_for_any_coefficient():
+    N, k = 3, 2
+    D = SIPG(N, k, bc="flow_x")
+    K = inputs.lognormal_coefficient(N, k, seed=11, corr_len=0.1 * 64 / N)
+    g = (1.0, 0.0, 0.0, 0.0, 0.0, 0.0)
+    u = spla.spsolve(D.assemble(K).tocsc(), D.dirichlet_rhs(K, g))
+    q_in = D.boundary_flux(K, u, 0, 1.0)
+    q_out = D.boundary_flux(K, u, 1, 0.0)
+    assert q_in > 0.0
+    assert abs(q_in + q_out) <= 1e-10 * q_in
+
+
+def test_zero_flux_sides_carry_no_face_terms():
+    N, k = 4, 2
+    K = inputs.lognormal_coefficient(N, k, seed=12, corr_len=0.1 * 64 / N)
+    ones = np.zeros((N ** 3, (k + 1) ** 3))
+    ones[:, 0] = 1.0                              # the constant function
+    c = np.arange(N ** 3)
+    cx = c % N
+    for bc, inner in (("flow_x", (cx > 0) & (cx < N - 1)),):
+        y = SIPG(N, k, bc=bc).apply(K, ones.reshape(-1)).reshape(N ** 3, -1)
+        assert np.abs(y[inner]).max() <= 1e-12 * np.abs(y).max()
+        assert np.abs(y[~inner]).max() > 0.0
+    # with Dirichlet data on every side the y/z boundary cells do see the constant
+    yd = SIPG(N, k).apply(K, ones.reshape(-1)).reshape(N ** 3, -1)
+    assert np.abs(yd[(cx > 0) & (cx < N - 1)]).max() > 0.0
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_dirichlet_rhs_closed_form(k):
+    """Only the modes (i, 0, 0) of the cells on a Dirichlet x-side see constant
+    data g (orthonormal tangential modes integrate to delta_{j0} delta_{l0}):
+    b = h Kbar g (sigma L_i(s) - o_s L_i'(s)), o_s = -1 at x = 0, +1 at x = 1,
+    with L_i(1) = sqrt(2i+1), L_i(0) = (-1)^i sqrt(2i+1), L_i'(1) = sqrt(2i+1) i(i+1),
+    L_i'(0) = (-1)^(i+1) sqrt(2i+1) i(i+1)."""
+    N = 3
+    D = SIPG(N, k, bc="flow_x")
+    K = inputs.lognormal_coefficient(N, k, seed=13, corr_len=0.1 * 64 / N)
+    kb = D.kbar(K)
+    gl, gr = 0.7, -1.3
+    b = D.dirichlet_rhs(K, (gl, gr, 5.0, 5.0, 5.0, 5.0)).reshape(N ** 3, k + 1, k + 1, k + 1)
+    sigma, h = 2.0 * (k + 1) ** 2, 1.0 / N
+    ref = np.zeros_like(b)
+    for c in range(N ** 3):
+        cx = c % N
+        for i in range(k + 1):
+            a = math.sqrt(2 * i + 1)
+            if cx == 0:
+                Li, dLi = (-1) ** i * a, (-1) ** (i + 1) * a * i * (i + 1)
+                ref[c, 0, 0, i] += h * kb[c] * gl * (sigma * Li + dLi)
+            if cx == N - 1:
+                Li, dLi = a, a * i * (i + 1)
+                ref[c, 0, 0, i] += h * kb[c] * gr * (sigma * Li - dLi)
+    assert np.abs(b - ref).max() <= 1e-12 * np.abs(ref).max()
