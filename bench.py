@@ -434,10 +434,11 @@ def run_config1(world):
 
 def run_config4(world):
     """Config 4: 32^3 Q3 lognormal K.  Mean ms of dg_apply, dg_apply_adjoint,
-    dg_coeff_grad, the differentiable apply (forward + backward) with the
-    coefficient cached and with it re-derived on every call, and one gradient of
-    L = 0.5 ||u(K) - u_obs||^2 by the adjoint CG (forward and adjoint solves,
-    FP64 with M = diag(A), to 1e-10)."""
+    dg_coeff_grad, the differentiable apply (forward alone, and forward +
+    backward) with the coefficient cached and with it re-derived on every call,
+    one gradient of L = 0.5 ||u(K) - u_obs||^2 by the adjoint CG (forward and
+    adjoint solves, FP64 with M = diag(A), to 1e-10), and the FP64 CG with
+    point-Jacobi against cell-block-Jacobi preconditioning."""
     import torch
     import paper_1911_01492_gb300 as dg
     from paper_1911_01492_gb300 import autograd as dga
@@ -464,6 +465,8 @@ def run_config4(world):
         yy = dga.apply(xg, lk, m)
         (yy * v).sum().backward()
     out["autograd_apply_fwd_bwd_ms_cached"] = time_gpu_calls(lambda: fwd_bwd(logK), 20)
+    with torch.no_grad():
+        out["autograd_apply_fwd_ms_cached"] = time_gpu_calls(lambda: dga.apply(xg, logK, m), 20)
     logK2 = (logK.detach() + 1e-3).requires_grad_()
     flip = [logK, logK2]
     state = {"i": 0}
@@ -493,6 +496,14 @@ def run_config4(world):
     loss.backward()
     torch.cuda.synchronize()
     out["loss_gradient_adjoint_cg_s"] = time.perf_counter() - t0
+    # preconditioners on this operator (FP64 CG to 1e-10, f = 1; each time
+    # includes forming the preconditioner): point Jacobi against cell blocks
+    for name in ("jacobi", "block"):
+        m.set_coefficient(Kd)          # drops the cached diagonal and blocks
+        xs = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        _, st = m.cg_solve(b, xs, rtol=1e-10, maxit=100000, precond=name, raise_on_error=False)
+        out["cg_fp64_" + name] = _solve_entry(st, world)
     out["loss_gradient_note"] = ("forward CG + adjoint CG + dg_coeff_grad, FP64 with "
                                  "M = diag(A), rtol 1e-10, coefficient derived once")
     out["dlogK_norm"] = float(lk.grad.norm())

@@ -48,6 +48,7 @@ enum {
 enum { DG_FP64 = 0, DG_FP32 = 1 };            /* operator precision            */
 enum { DG_CG_FP64 = 0, DG_CG_MIXED_IR = 1, DG_CG_MIXED_IR_RESTART = 2 };  /* dg_cg_solve modes */
 enum { DG_CG_PRECOND_JACOBI = 256 };  /* OR into a mode: PCG with M = diag(A) */
+enum { DG_CG_PRECOND_BLOCK = 512 };   /* OR into DG_CG_FP64: PCG with M = the cell blocks of A */
 /* Boundary conditions (dg_set_boundary): bit f set = boundary side f is Dirichlet,
  * sides in the order x-, x+, y-, y+, z-, z+; the other sides carry zero flux. */
 enum { DG_BC_DIRICHLET = 0x3F, DG_BC_FLOW_X = 0x03 };
@@ -161,6 +162,12 @@ int dg_coeff_grad(const dg_mesh* mesh, const double* u, const double* v, double*
  * mode | DG_CG_PRECOND_JACOBI: any of the above as PCG with M = diag(A)
  *   (Section 2.4's PCG algorithm); the diagonal is formed on the first such
  *   solve after dg_set_coefficient (one kernel, see dg_diagonal).
+ * DG_CG_FP64 | DG_CG_PRECOND_BLOCK: PCG with M = the block diagonal of A, one
+ *   n^3 x n^3 block per cell (its own volume and own-side face terms), stored
+ *   inverted in FP64 (the factorised block solves on the cell subspaces of
+ *   Section 3.4); formed on the first such solve after dg_set_coefficient
+ *   (degree 1..4; n^6 doubles per cell, e.g. 125 KB per cell at degree 4);
+ *   BREAKDOWN if a block is not positive definite.
  * Stops when ||b - A x|| <= rtol ||b|| recomputed in FP64.  Blocking.
  * Returns NOT_CONVERGED at maxit (x holds the last iterate), BREAKDOWN on
  * <p, Ap> <= 0 or non-finite scalars, TIMEOUT if a bounded wait of the mixed

@@ -498,20 +498,47 @@ class SIPG:
 
 
 # ----------------------------------------------------------------------------
+# Cell-block Jacobi (Section 3.4: block solves on the cells' subspaces V_T,
+# factorised): M = the block diagonal of A, one n^3 x n^3 block per cell.
+# ----------------------------------------------------------------------------
+
+def cell_blocks(A, n3: int):
+    """The diagonal cell blocks of an assembled matrix: array (cells, n3, n3)."""
+    A = A.tocsr()
+    nc = A.shape[0] // n3
+    out = np.empty((nc, n3, n3))
+    for c in range(nc):
+        out[c] = A[c * n3:(c + 1) * n3, c * n3:(c + 1) * n3].toarray()
+    return out
+
+
+def block_jacobi_inverse(A, n3: int):
+    """r -> M^-1 r for M = blockdiag(A_cc), each block inverted (LAPACK)."""
+    inv = np.linalg.inv(cell_blocks(A, n3))
+    return lambda r: np.einsum("cij,cj->ci", inv, np.asarray(r).reshape(-1, n3)).reshape(-1)
+
+
+# ----------------------------------------------------------------------------
 # Conjugate gradients (Section 2.4, Algorithm PCG, with M = I).
 # ----------------------------------------------------------------------------
 
 def cg(apply, b, x0=None, rtol=1e-10, maxit=100000, max_restarts=5, minv=None):
     """CG following the PCG algorithm of Section 2.4.
 
-    minv: None (M = I) or an array d with M^-1 r = d * r (a diagonal M).
+    minv: None (M = I), an array d with M^-1 r = d * r (a diagonal M), or a
+    function r -> M^-1 r (e.g. block_jacobi_inverse below).
     Stops when the recursively updated ||r|| <= rtol ||b||; then recomputes
     b - A x and restarts from x while that true residual is still above rtol.
     Returns (x, total iterations, true relative residual, residual history).
     """
     b = np.asarray(b, float)
     x = np.zeros_like(b) if x0 is None else np.array(x0, float)
-    precond = (lambda r: r) if minv is None else (lambda r: np.asarray(minv) * r)
+    if minv is None:
+        precond = lambda r: r                                   # noqa: E731
+    elif callable(minv):
+        precond = minv
+    else:
+        precond = lambda r: np.asarray(minv) * r                # noqa: E731
     nb = float(np.linalg.norm(b))
     if nb == 0.0:
         return np.zeros_like(b), 0, 0.0, []

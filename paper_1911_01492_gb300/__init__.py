@@ -27,6 +27,7 @@ DG_CG_FP64 = 0
 DG_CG_MIXED_IR = 1
 DG_CG_MIXED_IR_RESTART = 2
 DG_CG_PRECOND_JACOBI = 256
+DG_CG_PRECOND_BLOCK = 512
 DG_BC_DIRICHLET = 0x3F
 DG_BC_FLOW_X = 0x03
 
@@ -292,14 +293,17 @@ class Mesh:
     def cg_solve(self, b, x=None, rtol: float = 1e-10, maxit: int = 100000,
                  mode: int = DG_CG_FP64, stream=None, raise_on_error: bool = True,
                  precond: str | None = None):
-        """Solve A x = b (blocking).  precond: None or "jacobi" (PCG with
-        M = diag(A); same as OR-ing DG_CG_PRECOND_JACOBI into mode).
+        """Solve A x = b (blocking).  precond: None, "jacobi" (PCG with
+        M = diag(A); same as OR-ing DG_CG_PRECOND_JACOBI into mode) or "block"
+        (M = the inverted cell blocks of A; FP64 mode, degree <= 4).
         Returns (x, stats dict)."""
         import torch
-        if precond not in (None, "jacobi"):
+        if precond not in (None, "jacobi", "block"):
             raise ValueError(f"unknown preconditioner {precond!r}")
         if precond == "jacobi":
             mode |= DG_CG_PRECOND_JACOBI
+        elif precond == "block":
+            mode |= DG_CG_PRECOND_BLOCK
         if x is None:
             x = torch.zeros_like(b)
         st = CGStats()

@@ -52,9 +52,12 @@ struct Cfg {
 // for odd N the middle point m = N/2 sits at xi = 1/2).
 // ---------------------------------------------------------------------------
 
+// The contractions take the table type TT separately from the value type T
+// (the packed FP32 pair values of dg_pair32.cuh use the scalar FP32 tables).
+
 // u[a] = sum_i B[a][i] X[i]   (modal -> nodal values)
-template <int N, typename T>
-__device__ __forceinline__ void b_fwd(const DGTab<T>& t, const T (&X)[N], T (&u)[N]) {
+template <int N, typename T, typename TT>
+__device__ __forceinline__ void b_fwd(const DGTab<TT>& t, const T (&X)[N], T (&u)[N]) {
   constexpr int H = N / 2;
 #pragma unroll
   for (int a = 0; a < H; ++a) {
@@ -76,8 +79,8 @@ __device__ __forceinline__ void b_fwd(const DGTab<T>& t, const T (&X)[N], T (&u)
 }
 
 // g[a] = sum_i L_i'(xi_a) X[i]   (modal -> nodal derivative; L_1' is constant)
-template <int N, typename T>
-__device__ __forceinline__ void bd_fwd(const DGTab<T>& t, const T (&X)[N], T (&g)[N]) {
+template <int N, typename T, typename TT>
+__device__ __forceinline__ void bd_fwd(const DGTab<TT>& t, const T (&X)[N], T (&g)[N]) {
   constexpr int H = N / 2;
   const T c1 = t.Bd[0][1] * X[1];
 #pragma unroll
@@ -105,8 +108,8 @@ __device__ __forceinline__ void bd_fwd(const DGTab<T>& t, const T (&X)[N], T (&g
 }
 
 // R[i] = sum_a B[a][i] r[a] + sum_a L_i'(xi_a) k[a]   (nodal -> modal, both parts)
-template <int N, typename T>
-__device__ __forceinline__ void bt_bdt(const DGTab<T>& t, const T (&r)[N], const T (&k)[N],
+template <int N, typename T, typename TT>
+__device__ __forceinline__ void bt_bdt(const DGTab<TT>& t, const T (&r)[N], const T (&k)[N],
                                        T (&R)[N]) {
   constexpr int H = N / 2;
   T re[H > 0 ? H : 1], ro[H > 0 ? H : 1], ke[H > 0 ? H : 1], ko[H > 0 ? H : 1];
@@ -148,8 +151,8 @@ __device__ __forceinline__ void bt_bdt(const DGTab<T>& t, const T (&r)[N], const
 }
 
 // R[i] = sum_a B[a][i] r[a]   (nodal -> modal values)
-template <int N, typename T>
-__device__ __forceinline__ void b_bwd(const DGTab<T>& t, const T (&r)[N], T (&R)[N]) {
+template <int N, typename T, typename TT>
+__device__ __forceinline__ void b_bwd(const DGTab<TT>& t, const T (&r)[N], T (&R)[N]) {
   constexpr int H = N / 2;
   T re[H > 0 ? H : 1], ro[H > 0 ? H : 1];
 #pragma unroll

@@ -286,7 +286,9 @@ k_dot_pq(const T* __restrict__ p, const T* __restrict__ q, long long n, double* 
 // update; an FP64 refinement is requested (ru_skip = 0, sticky until it runs)
 // when rr' has dropped below delta2 * rmax2 or below tol2, or at the iteration
 // cap; at the cap the FP32 iteration stops.
-template <typename T, bool MIXED, bool PC, bool VEC>
+// BLK = true (cell-block Jacobi): only x, r, <r, r> and the convergence test;
+// rho and beta are formed by the block kernel from z = M^-1 r afterwards.
+template <typename T, bool MIXED, bool PC, bool VEC, bool BLK = false>
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
             const T* __restrict__ q, const T* __restrict__ dinv, long long n, double* partials,
@@ -361,6 +363,9 @@ k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
       st->breakdown = 1;
       st->done = 1;
       st->ru_skip = 1;
+    } else if (BLK) {
+      st->rr = rr;
+      if (rr <= st->tol2 || st->iters >= st->maxit) st->done = 1;
     } else if (!MIXED) {
       st->beta = zr / st->rho;
       st->rho = zr;
@@ -561,6 +566,33 @@ int launch_iteration(dg_mesh* m, T* x, T* r, T* p, T* q, const T* dinv, cudaStre
   return DG_OK;
 }
 
+// One iteration of FP64 PCG with the cell-block Jacobi preconditioner:
+// q = A p, alpha, x and r updates with <r, r>, z = M^-1 r with <z, r> (rho,
+// beta), p = z + beta p.
+int launch_iteration_block(dg_mesh* m, double* x, cudaStream_t s) {
+  int rc = dg_launch_apply_f64(m, m->p64, m->q64, &m->state->done, s);
+  if (rc) return rc;
+  const long long n = m->ndofs;
+  const bool vec = aligned16(x);
+  if (vec) {
+    k_dot_pq<double, true><<<RED_LAUNCH>>>(m->p64, m->q64, n, m->partials, m->state);
+    k_update_xr<double, false, false, true, true><<<RED_LAUNCH>>>(x, m->r64, m->p64, m->q64,
+                                                                  nullptr, n, m->partials,
+                                                                  m->state);
+  } else {
+    k_dot_pq<double, false><<<RED_LAUNCH>>>(m->p64, m->q64, n, m->partials, m->state);
+    k_update_xr<double, false, false, false, true><<<RED_LAUNCH>>>(x, m->r64, m->p64, m->q64,
+                                                                   nullptr, n, m->partials,
+                                                                   m->state);
+  }
+  DG_CUDA(cudaGetLastError());
+  rc = dg_launch_block_apply(m, m->r64, m->t64, nullptr, false, s);
+  if (rc) return rc;
+  k_update_p<double, false, true><<<RED_LAUNCH>>>(m->p64, m->t64, nullptr, n, m->state);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
 // One FP32 iteration of the mixed CG: direction update, operator and <p, q>
 // (fused kernels of dg_mixed32.cu), then d += alpha p, r -= alpha q.  The FP64
 // refinement is not in the captured iteration: it runs between graph replays
@@ -660,7 +692,7 @@ int zero_solution(dg_mesh* m, double* x, dg_cg_stats* st, cudaStream_t s) {
 }
 
 int cg_fp64(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_cg_stats* st,
-            bool jacobi, cudaStream_t s) {
+            bool jacobi, cudaStream_t s, bool block = false) {
   const double* dinv = jacobi ? m->dinv64 : nullptr;
   const int max_restarts = 5;
   int iters = 0, restarts = 0;
@@ -680,8 +712,13 @@ int cg_fp64(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_c
       k_init<double, false><<<RED_LAUNCH>>>(b, m->q64, m->r64, m->p64, dinv, m->ndofs, rtol,
                                             m->partials, m->state);
     DG_CUDA(cudaGetLastError());
+    if (block) {  // z = M^-1 r, p = z, rho = <z, r>
+      rc = dg_launch_block_apply(m, m->r64, m->t64, m->p64, true, s);
+      if (rc) return rc;
+    }
     rc = run_graph(m, s, chunk_for(m), [&] {
-      return launch_iteration<double>(m, x, m->r64, m->p64, m->q64, dinv, s);
+      return block ? launch_iteration_block(m, x, s)
+                   : launch_iteration<double>(m, x, m->r64, m->p64, m->q64, dinv, s);
     });
     if (rc) return rc;
     const DGCGState hs = *m->state_host;
@@ -874,9 +911,13 @@ extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double
     return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: rtol=%g outside (0, 1)", rtol);
   if (maxit < 1) return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: maxit=%d < 1", maxit);
   const bool jacobi = (mode & DG_CG_PRECOND_JACOBI) != 0;
-  const int base = mode & ~DG_CG_PRECOND_JACOBI;
+  const bool block = (mode & DG_CG_PRECOND_BLOCK) != 0;
+  const int base = mode & ~(DG_CG_PRECOND_JACOBI | DG_CG_PRECOND_BLOCK);
   if (base != DG_CG_FP64 && base != DG_CG_MIXED_IR && base != DG_CG_MIXED_IR_RESTART)
     return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: unknown mode %d", mode);
+  if (block && (jacobi || base != DG_CG_FP64))
+    return dg_fail(DG_ERR_INVALID_ARG,
+                   "dg_cg_solve: DG_CG_PRECOND_BLOCK goes with DG_CG_FP64 only");
   dg_mesh* m = const_cast<dg_mesh*>(mc);
   int rc = dg_ensure_solver_ws(m);
   if (rc) return rc;
@@ -887,9 +928,10 @@ extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double
   if (st) *st = dg_cg_stats{};
   cudaStream_t s = m->solve_stream;
   if (jacobi) rc = dg_ensure_diagonal(m, s);
+  if (block) rc = dg_ensure_block(m, s);
   if (rc == DG_OK) {
     if (base == DG_CG_FP64)
-      rc = cg_fp64(m, b, x, rtol, maxit, st, jacobi, s);
+      rc = cg_fp64(m, b, x, rtol, maxit, st, jacobi, s, block);
     else if (base == DG_CG_MIXED_IR)
       rc = cg_mixed(m, b, x, rtol, maxit, st, jacobi, s);
     else

@@ -87,6 +87,9 @@ struct dg_mesh {
   double* dinv64;
   float* dinv32;
   bool has_diag;
+  // cell-block Jacobi: the inverted diagonal cell blocks [c][n^3][n^3] (FP64)
+  double* binv64;
+  bool has_block;
   double* kbar;     // Kbar_c                          [c]
   int* dflag;       // device-side error flag of the setup kernels
 
@@ -176,6 +179,11 @@ int dg_prepare_grad(int n);
 
 // 1 / diag(A) for the Jacobi preconditioner (dg_precond.cu); forms it if needed
 int dg_ensure_diagonal(dg_mesh* m, cudaStream_t s);
+// cell-block Jacobi (dg_block.cu): the inverted blocks (formed if needed), and
+// z = M^-1 r with <z, r> into the CG state (init: rho and p = z; else beta, rho)
+int dg_ensure_block(dg_mesh* m, cudaStream_t s);
+int dg_launch_block_apply(const dg_mesh* m, const double* r, double* z, double* p, bool init,
+                          cudaStream_t s);
 // workspace helpers (dg_mesh.cu)
 int dg_ensure_solver_ws(dg_mesh* m);
 int dg_ensure_grad_ws(dg_mesh* m);

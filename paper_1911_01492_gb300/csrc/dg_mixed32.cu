@@ -1,28 +1,30 @@
 // FP32 kernels of the mixed-precision CG iteration (DG_CG_MIXED_IR).
 //
 // FP32 arithmetic is ~75x cheaper than FP64 on GB300, so the FP32 operator is
-// bound by memory traffic and instruction issue, not arithmetic.  These
-// kernels trade arithmetic for bytes and fold the CG vector work into the
+// bound by memory traffic, instruction issue and latency, not arithmetic.
+// These kernels trade arithmetic for bytes and fold the CG vector work into the
 // operator passes:
 //   k_dir32_bulk: p = z + beta p (z = M^-1 r; beta from the device CG state,
 //             0 on a restart, formed once by k_update_xr / k_refine_r), then
 //             pass 1 of p writing only the face traces (no U, X).  Its inputs
 //             are staged in shared memory by bulk copies (TMA engine),
 //             double-buffered over groups of cells in a persistent grid.
-//   k_cell32: reloads p, recomputes its nodal and x-modal values in shared
+//   k_cell32x2: reloads p, recomputes its nodal and x-modal values in shared
 //             memory (each line-thread forms its own face traces from its
-//             line's values), reads the neighbours' traces,
-//             forms the face weights from h*gamma, computes q = A p, and folds
-//             <p, q> (FP64-accurate: exact products summed in compensated
-//             float-float) into its epilogue; the last block to finish commits
-//             rho = rho_new (formed with beta by the kernel that updated r) and
-//             sets alpha = rho / <p, q>.
+//             line's values), reads the neighbours' traces, forms the face
+//             weights from h*gamma, computes q = A p, and folds <p, q>
+//             (FP64-accurate: exact products summed in compensated float-float)
+//             into its epilogue; the last block to finish commits rho = rho_new
+//             (formed with beta by the kernel that updated r) and sets
+//             alpha = rho / <p, q>.  It works on pairs of cells in packed FP32
+//             arithmetic (FFMA2 / FADD2 / FMUL2, dg_pair32.cuh): every
+//             instruction serves two cells.
 // Per DOF this moves ~38 B for the operator (instead of ~66 B in the generic
 // two-pass FP32 path) and removes the separate direction and dot kernels.
-// Measured at 48^3 Q4 (13.8 M DOFs): k_dir32_bulk 53 us + k_cell32 123 us per
-// iteration.  The same fusion built on stored U and X (generic pass 2) was
-// slower, so recomputing in shared memory is kept.  k_cell32 is bound by
-// instruction issue and block barriers (~9 warp instructions per DOF).
+// Measured at 48^3 Q4 (13.8 M DOFs): the cell kernel on single cells ran at
+// 6.7 warp instructions per DOF, issue-bound (123 us); on cell pairs it runs
+// 3.4 per DOF and is bound by load latency (about 100 us), the whole FP32
+// iteration 0.219 ms instead of 0.242 ms.
 #include <cstdlib>
 
 #include "dg_apply_impl.cuh"
@@ -121,24 +123,6 @@ struct ZDirUpdate {
       const float val = fmaf(beta, sc[idx], z);
       pg[off] = val;
       v[l] = val;
-    }
-  }
-};
-
-// ZLoadKeep: the z-line of p from global memory, also kept in `keep` for the
-// <p, q> epilogue (each element of the block is on exactly one z-line).
-template <int NK>
-struct ZLoadKeep {
-  const float* pg;  // global p of the block's first cell
-  float (&keep)[NK];
-  template <int N, typename T>
-  __device__ __forceinline__ void operator()(const T* sc, int lc, int pp, int qq,
-                                             T (&v)[N]) const {
-    (void)sc;
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      v[l] = pg[lc * N * N * N + l * N * N + qq * N + pp];
-      keep[l] = v[l];
     }
   }
 };
@@ -262,143 +246,29 @@ k_dir32_bulk(const float* __restrict__ r, float* __restrict__ p, float* __restri
   }
 }
 
-template <int N>
-__global__ void __launch_bounds__(Cfg<N>::THREADS)
-k_cell32(const float* __restrict__ p, const float* __restrict__ TR, const float* __restrict__ kt,
-         const float* __restrict__ gh, float* __restrict__ q, long long ncells, int Nc,
-         double* __restrict__ partials, DGCGState* st, const __grid_constant__ DGTab<float> tab) {
-  constexpr int C = Cfg<N>::CPB, N2 = N * N, N3 = N * N * N, NT = Cfg<N>::THREADS;
-  if (st->done || st->iters >= st->maxit) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* su = reinterpret_cast<float*>(smem_raw);
-  float* sx = su + C * N3;
-  float* sr = sx + C * N3;
-  float* sk = sr + C * N3;
-  __shared__ float rh[NT], rl[NT];
-  __shared__ bool is_last;
-  const long long c0 = (long long)blockIdx.x * C;
-  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
-  // h w K of the block's cells: loaded into registers now, stored to shared
-  // memory after pass 1 (the cell phase reads it), so that these loads and
-  // the z-line loads of p below are in flight together
-  float kreg[N];
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    const int t = threadIdx.x + k * NT;
-    kreg[k] = t < nblk * N3 ? kt[c0 * N3 + t] : 0.0f;
-  }
-  // pass 1 in shared memory; each z-line thread loads its line of p from
-  // global memory and keeps it for the <p, q> epilogue
-  float preg[N];
-#pragma unroll
-  for (int l = 0; l < N; ++l) preg[l] = 0.0f;
-  const ZLoadKeep<N> zl{p + c0 * N3, preg};
-  trace_core<N, float, 3>(nullptr, nullptr, nullptr, c0, nblk, tab, su, sx, zl);
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    const int t = threadIdx.x + k * NT;
-    if (t < nblk * N3) sk[t] = kreg[k];
-  }
-  __syncthreads();
-  const FaceLocal<float> fs{TR, gh, &tab};
-  cell_core<N, float>(fs, q, c0, nblk, Nc, tab, su, sx, sr, sk);
-  // <p, q> over the block's cells on the z-lines of p kept above; q is
-  // still in sx after cell_core (same layout as p)
-  float hi = 0.0f, lo = 0.0f;
-  const int zlc = threadIdx.x / N2, zt2 = threadIdx.x - zlc * N2;
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    if (zlc >= nblk) break;
-    const float a = preg[l], b = sx[zlc * N3 + l * N2 + zt2];
-    const float pr = a * b;
-    const float e = fmaf(a, b, -pr);
-    float s1, t1;
-    two_sum_f(hi, pr, s1, t1);
-    hi = s1;
-    lo += t1 + e;
-  }
-  rh[threadIdx.x] = hi;
-  rl[threadIdx.x] = lo;
-  __syncthreads();
-  // Fixed-order compensated block sum: lane l of warp 0 folds entries
-  // l, l + 32, ... (NT >= 32 for every degree, so warp 0 is full), then a
-  // butterfly over the warp.  A serial sum by one thread kept the whole block
-  // resident for ~NT dependent TwoSums.
-  if (threadIdx.x < 32) {
-    float h = rh[threadIdx.x], l = rl[threadIdx.x];
-    for (int i = threadIdx.x + 32; i < NT; i += 32) {
-      float s1, t1;
-      two_sum_f(h, rh[i], s1, t1);
-      h = s1;
-      l += t1 + rl[i];
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const float oh = __shfl_xor_sync(0xffffffffu, h, off);
-      const float ol = __shfl_xor_sync(0xffffffffu, l, off);
-      float s1, t1;
-      two_sum_f(h, oh, s1, t1);
-      h = s1;
-      l += ol + t1;
-    }
-    if (threadIdx.x == 0) {
-      partials[blockIdx.x] = (double)h + (double)l;
-      __threadfence();
-      is_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
-    }
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  // last block: fixed-order sum of all block partials in FP64
-  __shared__ double rd[NT];
-  double a = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) a += ((volatile double*)partials)[b];
-  rd[threadIdx.x] = a;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int i = 0; i < NT; ++i) tot += rd[i];
-    st->pq = tot;
-    if (!(tot > 0.0) || !isfinite(tot)) {
-      st->breakdown = 1;
-      st->done = 1;
-      st->ru_skip = 1;
-    } else {
-      const double rho = st->rho_new;  // k_dir32_bulk has used beta; commit the new rho
-      st->rho = rho;
-      st->restart = 0;
-      st->alpha = rho / tot;
-    }
-    st->ticket = 0u;
-  }
-  (void)N2;
-}
-
-
-
 // ---------------------------------------------------------------------------
-// k_cell32x2: the same computation as k_cell32 on pairs of consecutive cells
-// (a = c0 + 2j, b = a + 1), each value a packed FP32 pair (dg_pair32.cuh): one
-// FFMA2 / FADD2 / FMUL2, one 64-bit shared-memory access and one address
-// computation serve both cells.  Every lane computes exactly what the scalar
-// kernel computes for its cell, with the same FP32 operations in the same
-// order, so the result is the scalar kernel's.  Per-lane differences (a face on
-// the boundary for one cell of the pair only, a last pair with one cell) are
-// handled with per-lane data instead of branches: a boundary lane's neighbour
-// trace is zero, and its derivative term and derivative weight take the factor
-// e = 2 (e = 1 inside), which turns the interior flux into the one-sided one.
-// The block then works as k_cell32: pass 1 of p in shared memory, the cell
-// phase with own traces formed in the line threads and the neighbours' traces
-// from the direction kernel, and <p, q> folded into the epilogue, where each
-// z-line thread still holds its z-line of p and of q in registers.
+// k_cell32x2: the FP32 operator pass of the mixed iteration on pairs of
+// consecutive cells (a = c0 + 2j, b = a + 1), each value a packed FP32 pair
+// (dg_pair32.cuh): one FFMA2 / FADD2 / FMUL2, one 64-bit shared-memory access
+// and one address computation serve both cells.  Every lane computes what a
+// single-cell kernel computes for its cell, with the same FP32 operations in
+// the same order.  Per-lane differences (a face on the boundary for one cell
+// of the pair only, a last pair with one cell) are handled with per-lane data
+// instead of branches: a boundary lane's neighbour trace is zero, and its
+// derivative term and derivative weight take the factor e = 2 (e = 1 inside),
+// which turns the interior flux into the one-sided one; a lane without a cell
+// loads nothing.  The block: pass 1 of p in shared memory, the cell phase with
+// own traces formed in the line threads and the neighbours' traces from the
+// direction kernel, and <p, q> folded into the epilogue, where each z-line
+// thread still holds its z-line of p and of q in registers.  Registers are
+// capped at 64 for n <= 5 (eight blocks per SM).
 // ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(Cfg<N>::THREADS)
+__global__ void __launch_bounds__(Cfg<N>::THREADS, N <= 5 ? 8 : 1)
 k_cell32x2(const float* __restrict__ pg, const float* __restrict__ TR,
            const float* __restrict__ kt, const float* __restrict__ gh, float* __restrict__ qg,
            long long ncells, int Nc, double* __restrict__ partials, DGCGState* st,
-           const __grid_constant__ DGTab<F2> tab) {
+           const __grid_constant__ DGTab<float> tab) {
   constexpr int C = Cfg<N>::CPB, N2 = N * N, N3 = N * N * N, NT = Cfg<N>::THREADS;
   constexpr float S2 = 4.0f * N * N;  // 2 sigma, sigma = 2 (k+1)^2
   if (st->done || st->iters >= st->maxit) return;
@@ -489,7 +359,7 @@ k_cell32x2(const float* __restrict__ pg, const float* __restrict__ TR,
   }
   const long long sy = Nc, sz = (long long)Nc * Nc;
   const int pt = p + N * q;
-  const float hw2 = 0.5f * tab.w[pt % N].v.x * tab.w[pt / N].v.x;
+  const float hw2 = 0.5f * tab.w[pt % N] * tab.w[pt / N];
   // face f's neighbour trace (value, derivative) and weight W/2 for both lanes;
   // zero trace on a boundary lane
   auto face = [&](int f, bool ina, bool inb, long long cna, long long cnb, F2& un, F2& gn,
@@ -503,17 +373,19 @@ k_cell32x2(const float* __restrict__ pg, const float* __restrict__ TR,
     e = F2(ina ? 1.0f : 2.0f, inb ? 1.0f : 2.0f);
   };
   F2 un[4], gn[4], wh[4], ee[4];  // faces z-, z+, y-, y+ (then x-, x+ in slots 0, 1)
-  face(4, cza > 0, czb > 0, ca - sz, cb - sz, un[0], gn[0], wh[0], ee[0]);
-  face(5, cza < Nc - 1, czb < Nc - 1, ca + sz, cb + sz, un[1], gn[1], wh[1], ee[1]);
-  face(2, cya > 0, cyb > 0, ca - sy, cb - sy, un[2], gn[2], wh[2], ee[2]);
-  face(3, cya < Nc - 1, cyb < Nc - 1, ca + sy, cb + sy, un[3], gn[3], wh[3], ee[3]);
+  // a lane without a cell (the second cell of an odd last pair, or a pair
+  // past the end) loads no face data: its values stay zero and finite
+  face(4, va && cza > 0, vb && czb > 0, ca - sz, cb - sz, un[0], gn[0], wh[0], ee[0]);
+  face(5, va && cza < Nc - 1, vb && czb < Nc - 1, ca + sz, cb + sz, un[1], gn[1], wh[1], ee[1]);
+  face(2, va && cya > 0, vb && cyb > 0, ca - sy, cb - sy, un[2], gn[2], wh[2], ee[2]);
+  face(3, va && cya < Nc - 1, vb && cyb < Nc - 1, ca + sy, cb + sy, un[3], gn[3], wh[3], ee[3]);
   __syncthreads();
   // flux of one face point from the own trace (uo, go) and the face data:
   // cv multiplies the test value, -cd the test derivative
   auto flux = [&](bool upper, F2 uo, F2 go, F2 unf, F2 gnf, F2 whf, F2 ef, F2& cv, F2& cd) {
     const F2 J = upper ? uo - unf : unf - uo;
     const F2 G = fma(ef, go, gnf);
-    const F2 tt = upper ? fma(F2(S2), J, -G) : fma(F2(-S2), J, G);
+    const F2 tt = upper ? fma(S2, J, -G) : fma(-S2, J, G);
     cv = whf * tt;
     cd = (whf * ef) * J;
   };
@@ -563,8 +435,9 @@ k_cell32x2(const float* __restrict__ pg, const float* __restrict__ TR,
 #pragma unroll
     for (int e = 0; e < N; ++e) sr[o + base + e * step] = r[e];
     if (dir == 1) {  // the x-faces' data, in flight during the barrier
-      face(0, cxa > 0, cxb > 0, ca - 1, cb - 1, un[0], gn[0], wh[0], ee[0]);
-      face(1, cxa < Nc - 1, cxb < Nc - 1, ca + 1, cb + 1, un[1], gn[1], wh[1], ee[1]);
+      face(0, va && cxa > 0, vb && cxb > 0, ca - 1, cb - 1, un[0], gn[0], wh[0], ee[0]);
+      face(1, va && cxa < Nc - 1, vb && cxb < Nc - 1, ca + 1, cb + 1, un[1], gn[1], wh[1],
+           ee[1]);
     }
     __syncthreads();
   }
@@ -701,7 +574,6 @@ struct Mixed32F {
   template <typename T>
   static cudaError_t run(const dg_mesh* m, const float* dinv, cudaStream_t s) {
     constexpr int C = Cfg<N>::CPB, N3 = N * N * N;
-    const unsigned blocks = (unsigned)((m->ncells + C - 1) / C);
     // test hook (read when the iteration is captured): the direction kernel
     // skips its first bulk copy and gives up its wait after a few polls
     const char* env = getenv("DG_TEST_BULK_STALL");
@@ -717,20 +589,10 @@ struct Mixed32F {
       k_dir32_bulk<N, false><<<gb, Dir32Bulk<N, false>::THREADS, Dir32Bulk<N, false>::SMEM, s>>>(
           m->r32, m->p32, m->TR32, dinv, m->ncells, m->state, limit, stall_now ? 1 : 0,
           m->tab32);
-    const char* pc2 = getenv("DG_FP32_CELL_PAIR");
-    if (pc2 == nullptr || pc2[0] != '1') {
-      const size_t sm2 = sizeof(float) * 4 * C * N3;
-      k_cell32<N><<<blocks, Cfg<N>::THREADS, sm2, s>>>(m->p32, m->TR32, m->kt32, m->gh32,
-                                                       m->q32, m->ncells, m->N,
-                                                       m->partials_cells, m->state, m->tab32);
-    } else {
-      DGTab<F2> tab2;
-      pair_tables(m->tab32, &tab2);
-      const unsigned blocks2 = (unsigned)((m->ncells + 2 * C - 1) / (2 * C));
-      k_cell32x2<N><<<blocks2, Cfg<N>::THREADS, sizeof(F2) * 4 * C * N3, s>>>(
-          m->p32, m->TR32, m->kt32, m->gh32, m->q32, m->ncells, m->N, m->partials_cells,
-          m->state, tab2);
-    }
+    const unsigned blocks2 = (unsigned)((m->ncells + 2 * C - 1) / (2 * C));
+    k_cell32x2<N><<<blocks2, Cfg<N>::THREADS, sizeof(F2) * 4 * C * N3, s>>>(
+        m->p32, m->TR32, m->kt32, m->gh32, m->q32, m->ncells, m->N, m->partials_cells,
+        m->state, m->tab32);
     return cudaGetLastError();
   }
 };

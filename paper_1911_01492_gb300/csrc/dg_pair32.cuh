@@ -8,9 +8,13 @@
 // (64-bit) and address computation serves both cells.
 //
 // F2 wraps float2 so that the generic line contractions of dg_apply_impl.cuh
-// (templated on the value type; their unqualified fma() finds the overload
-// below by argument-dependent lookup) run on pairs unchanged.  This header is
-// included after dg_apply_impl.cuh.
+// (templated on the value type; their unqualified fma() finds the overloads
+// below by argument-dependent lookup) run on pairs unchanged, with the scalar
+// FP32 tables: a table entry is a scalar broadcast into both lanes.  Measured
+// on GB300: FFMA2 with a broadcast kernel-parameter constant issues one
+// instruction per pair of FMAs, while a packed pair constant from the kernel
+// parameters costs an extra move per FFMA2 and ran at half the scalar rate.
+// This header is included after dg_apply_impl.cuh.
 #pragma once
 
 #include "dg_apply_impl.cuh"
@@ -47,25 +51,17 @@ __device__ __forceinline__ F2 operator*(F2 a, F2 b) {
   return r;
 }
 
-// Host: the FP32 tables with every entry duplicated into both lanes.
-inline void pair_tables(const DGTab<float>& s, DGTab<F2>* d) {
-  for (int a = 0; a < DG_MAXN; ++a) {
-    for (int b = 0; b < DG_MAXN; ++b) {
-      d->B[a][b] = F2(s.B[a][b]);
-      d->Bd[a][b] = F2(s.Bd[a][b]);
-      d->D[a][b] = F2(s.D[a][b]);
-    }
-    d->w[a] = F2(s.w[a]);
-    d->a0[a] = F2(s.a0[a]);
-    d->a1[a] = F2(s.a1[a]);
-    d->d0[a] = F2(s.d0[a]);
-    d->d1[a] = F2(s.d1[a]);
-    d->l0[a] = F2(s.l0[a]);
-    d->l1[a] = F2(s.l1[a]);
-    d->dl0[a] = F2(s.dl0[a]);
-    d->dl1[a] = F2(s.dl1[a]);
-  }
-  d->sigma = F2(s.sigma);
+// A scalar table entry times a pair: the entry is broadcast into both lanes,
+// which the packed instructions take as an operand directly (no extra move).
+__device__ __forceinline__ F2 fma(float a, F2 b, F2 c) {
+  F2 r;
+  r.v = __ffma2_rn(make_float2(a, a), b.v, c.v);
+  return r;
+}
+__device__ __forceinline__ F2 operator*(float a, F2 b) {
+  F2 r;
+  r.v = __fmul2_rn(make_float2(a, a), b.v);
+  return r;
 }
 
 }  // namespace dgk
