@@ -12,7 +12,8 @@ a manufactured-solution CG), `config2_cg` (the unpreconditioned FP64 CG on the
 differentiable apply and adjoint-CG gradient), `batched_cg` (the small level
 of the 256-sample batch, one batched solve against one solve per call), `mlmc`
 (one multilevel Monte-Carlo Estimate step for the mean inlet flux of the
-Section 5 flow problem over the three batched levels), and
+Section 5 flow problem over the three batched levels), `affine` (the apply
+and a CG on a sheared mesh, the paper's problem B), and
 `oracle_legs` (the FP64 CPU oracle: one thread and all threads, CSR SpMV and
 CG where the matrix fits, projected CG elsewhere).
 
@@ -613,6 +614,45 @@ def run_batched(world, rank, sequential_samples: int = 1, full: bool = False,
     return out
 
 
+SHEAR = [[1.0, 0.3, 0.1], [0.0, 1.1, -0.2], [0.05, 0.0, 0.9]]
+
+
+def run_affine(world, K64):
+    """Problem B (affine geometry): the FP64 apply of the 64^3 Q3 workload on
+    the sheared mesh x = A xi (A = SHEAR), timed like `value` (8 sweeps), with
+    its per-pass times; and the FP64 CG (M = I, f = 1, rtol 1e-10) on 32^3 Q3
+    on that geometry."""
+    import torch
+    import paper_1911_01492_gb300 as dg
+    from paper_1911_01492_gb300 import inputs
+    N, k = WORKLOAD["n_cells"], WORKLOAD["degree"]
+    m = dg.Mesh(N, k)
+    m.set_geometry(SHEAR)
+    m.set_coefficient(torch.from_numpy(K64).cuda())
+    x = torch.from_numpy(inputs.uniform_vector(N, k, WORKLOAD["x_seed"])).cuda()
+    y = torch.empty_like(x)
+    steps = 8
+    ms, napp, ms1, ms2 = time_applies(m, x, y, steps, 2, world)
+    nd = m.n_dofs
+    out = {"geometry": SHEAR, "workload": f"{N}^3 Q{k}, lognormal K (seed 2)",
+           "apply_gdof_s": world * nd * steps * APPLIES_PER_STEP / (ms * 1e-3) / 1e9,
+           "pass_ms": {"k_trace": ms1 / max(napp, 1), "k_cell_aff": ms2 / max(napp, 1)}}
+    m.close()
+    del x, y
+    N2, k2 = 32, 3
+    m = dg.Mesh(N2, k2)
+    m.set_geometry(SHEAR)
+    m.set_coefficient(torch.from_numpy(inputs.lognormal_coefficient(N2, k2, seed=5)).cuda())
+    b = m.load_vector(torch.ones(m.n_dofs, dtype=torch.float64, device="cuda"))
+    xs = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    _, st = m.cg_solve(b, xs, rtol=1e-10, maxit=200000, raise_on_error=False)
+    out["cg_fp64_32cubed_q3"] = _solve_entry(st, world)
+    m.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_mlmc(world):
     """Section 5: one Estimate step of MLMC for the mean inlet flux of the flow
     problem (p = 1 at x = 0, p = 0 at x = 1, zero flux elsewhere; lognormal k,
@@ -878,6 +918,10 @@ def main(argv=None):
     if not args.no_cg:
         cg2 = _leg(run_config2_cg, m, world)
     m.close()
+    affine = None
+    if not args.no_extra:
+        torch.cuda.empty_cache()
+        affine = _leg(run_affine, world, K)
     del xd, yd, Kd
     torch.cuda.empty_cache()
     if not args.no_cg:
@@ -916,7 +960,7 @@ def main(argv=None):
                 "setup_ms": setup_ms,
                 "clocks": clk.summary(), "cpu_baseline": cpu, "cg": cg,
                 "config2_cg": cg2, "config1": cfg1, "config4": cfg4,
-                "batched_cg": batched, "mlmc": mlmc_r, "oracle_legs": legs,
+                "batched_cg": batched, "mlmc": mlmc_r, "affine": affine, "oracle_legs": legs,
                 "bench_wall_s": time.perf_counter() - t_start}
         print(json.dumps(line), flush=True)
     if world > 1:

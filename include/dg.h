@@ -102,6 +102,19 @@ int dg_mesh_info(const dg_mesh* mesh, long long* n_dofs, long long* n_cells_tota
  * (NULL mesh, mask outside 1..0x3f: at least one side must be Dirichlet). */
 int dg_set_boundary(dg_mesh* mesh, int dirichlet_mask);
 
+/* Affine geometry (the paper's problem B, Section 3.3: affine cells): the mesh
+ * becomes the image of the unit-cube mesh under x = A xi, A a 3x3 matrix (host
+ * array, row-major) with det A > 0; every cell is then a parallelepiped with
+ * Jacobian h A.  The operator is the same SWIPDG form written with the
+ * physical gradients, face normals, face areas and penalty length |T| / |F|.
+ * A = I (the default) is the unit cube.  On a non-identity geometry the FP64
+ * dg_apply / dg_apply_adjoint, dg_load_vector (f at the mapped Gauss points)
+ * and dg_cg_solve with DG_CG_FP64 (no preconditioner) are available; the
+ * other calls return INVALID_ARG.  Drops the coefficient: call
+ * dg_set_coefficient again afterwards.  Errors: INVALID_ARG (NULL pointer,
+ * non-finite entry, det A <= 0), CUDA. */
+int dg_set_geometry(dg_mesh* mesh, const double* A);
+
 /* Set the diffusion coefficient K (device pointer, FP64, layout K[c*n^3 + q],
  * values at the volume Gauss points).  K is the coefficient A = lambda kappa of
  * the Section 4.1 problem -div(A grad p) = f (here a scalar field); Section 5

@@ -568,3 +568,156 @@ def cg(apply, b, x0=None, rtol=1e-10, maxit=100000, max_restarts=5, minv=None):
         if true_rel <= rtol or it >= maxit:
             return x, it, true_rel, hist
     return x, it, true_rel, hist
+
+
+# ----------------------------------------------------------------------------
+# Affine geometry (the paper's problem B, Section 3.3): the domain is the image
+# of the unit cube under x = A xi for a constant matrix A (det A > 0); cell c
+# is the image of its reference cube, x = h A (c + xi_loc), Jacobian J = h A.
+# Everything is written with physical quantities, evaluated at the same Gauss
+# points: grad = J^-T grad_ref, volume weight |det J| w_q; a face with
+# reference axis d has unit normal n = A^-T e_d / |A^-T e_d| (from the
+# lower-index cell to the upper one), area element |det J| |J^-T e_d| w_p, and
+# penalty length h_F = |T| / |F| = 1 / |J^-T e_d|.  The face form is the same
+# SWIPDG form as above with n . grad (all three reference derivatives at the
+# face points).  For A = I this is SIPG exactly.
+# ----------------------------------------------------------------------------
+
+class AffineSIPG:
+    """SIPG on the affine image A [0,1]^3 of the N^3 cube mesh (assembled)."""
+
+    def __init__(self, n_cells: int, degree: int, A, sigma: float | None = None):
+        self.base = SIPG(n_cells, degree, sigma=sigma)      # 1D tables, indices, K-bar
+        self.N, self.k, self.n, self.n3 = n_cells, degree, degree + 1, (degree + 1) ** 3
+        self.h = 1.0 / n_cells
+        self.sigma = self.base.sigma
+        self.A = np.asarray(A, float).reshape(3, 3)
+        if not np.linalg.det(self.A) > 0:
+            raise ValueError("the geometry needs det A > 0")
+        self.J = self.h * self.A
+        self.Jinv = np.linalg.inv(self.J)
+        self.detJ = float(np.linalg.det(self.J))
+        n = self.n
+        xi, w = self.base.xi, self.base.w
+        L = np.array([[legendre(i, t) for i in range(n)] for t in xi])
+        dL = np.array([[legendre_deriv(i, t) for i in range(n)] for t in xi])
+        ends = {s: (np.array([legendre(i, float(s)) for i in range(n)]),
+                    np.array([legendre_deriv(i, float(s)) for i in range(n)])) for s in (0, 1)}
+        idx = np.arange(n)
+        P1, P2 = np.meshgrid(idx, idx, indexing="ij")
+        p1, p2 = P1.T.reshape(-1), P2.T.reshape(-1)
+        # full reference gradients of every basis function at the face points
+        self.face_grad = {}
+        for d in range(3):
+            t1, t2 = [ax for ax in range(3) if ax != d]
+            for s in (0, 1):
+                Ls, dLs = ends[s]
+                G = np.empty((n * n, self.n3, 3))
+                for m in range(self.n3):
+                    mi = (m % n, (m // n) % n, m // (n * n))
+                    f = {d: (Ls[mi[d]], dLs[mi[d]]),
+                         t1: (L[p1, mi[t1]], dL[p1, mi[t1]]),
+                         t2: (L[p2, mi[t2]], dL[p2, mi[t2]])}
+                    for g in range(3):
+                        prod = 1.0
+                        for ax in range(3):
+                            prod = prod * (f[ax][1] if ax == g else f[ax][0])
+                        G[:, m, g] = prod
+                self.face_grad[(d, s)] = G
+
+    @property
+    def n_dofs(self):
+        return self.N ** 3 * self.n3
+
+    def assemble(self, K) -> sp.csr_matrix:
+        B = self.base
+        Nc, n3, sigma = self.N ** 3, self.n3, self.sigma
+        K = np.asarray(K, float).reshape(Nc, n3)
+        Jit = self.Jinv.T
+        rows, cols, vals = [], [], []
+        loc = np.arange(n3)
+        R, C = np.meshgrid(loc, loc, indexing="ij")
+
+        def add(tc, sc, M):
+            rows.append((tc * n3 + R).reshape(-1))
+            cols.append((sc * n3 + C).reshape(-1))
+            vals.append(M.reshape(-1))
+
+        Gp = B.grad @ Jit.T                                   # physical gradients (q, m, 3)
+        for c in range(Nc):
+            wk = self.detJ * B.wq * K[c]
+            add(c, c, np.einsum("qmd,q,qnd->mn", Gp, wk, Gp))
+        Kbar = B.kbar(K)
+        for d in range(3):
+            ed = np.zeros(3)
+            ed[d] = 1.0
+            nrm = Jit @ ed
+            area = self.detJ * float(np.linalg.norm(nrm))      # |det J| |J^-T e_d|
+            nvec = nrm / np.linalg.norm(nrm)
+            hF = 1.0 / float(np.linalg.norm(nrm))
+            wa = area * B.face_w[d]
+            V0, V1 = B.face_val[(d, 0)], B.face_val[(d, 1)]
+            # n . grad at the face points of each side (physical)
+            D0 = self.face_grad[(d, 0)] @ (Jit.T @ nvec)
+            D1 = self.face_grad[(d, 1)] @ (Jit.T @ nvec)
+            side = {"m": (V1, 0.5 * D1), "p": (-V0, 0.5 * D0)}
+            for c in range(Nc):
+                coord = B.cell_coords(c)[d]
+                if coord < self.N - 1:
+                    cp = c + B.stride(d)
+                    g = 2.0 * Kbar[c] * Kbar[cp] / (Kbar[c] + Kbar[cp])
+                    W = g * wa
+                    for tn, tc in (("m", c), ("p", cp)):
+                        Jt, At = side[tn]
+                        for sn, sc in (("m", c), ("p", cp)):
+                            Js, As = side[sn]
+                            add(tc, sc, Jt.T @ (W[:, None] * (-As + (sigma / hF) * Js))
+                                - At.T @ (W[:, None] * Js))
+                if coord == self.N - 1 and B.dirichlet[2 * d + 1]:     # outward +n
+                    W = Kbar[c] * wa
+                    add(c, c, V1.T @ (W[:, None] * (-D1 + (sigma / hF) * V1)) - D1.T @ (W[:, None] * V1))
+                if coord == 0 and B.dirichlet[2 * d]:                  # outward -n
+                    W = Kbar[c] * wa
+                    add(c, c, V0.T @ (W[:, None] * (D0 + (sigma / hF) * V0)) + D0.T @ (W[:, None] * V0))
+        Am = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                           shape=(Nc * n3, Nc * n3))
+        return Am.tocsr()
+
+    def apply(self, K, x):
+        return self.assemble(K) @ np.asarray(x, float)
+
+    def points(self, nq: int):
+        """Physical coordinates of an nq-point Gauss rule in every cell:
+        arrays X, Y, Z of shape (cells, nq, nq, nq) over (a, b, e)."""
+        tq, _ = gauss_points(nq)
+        N, h = self.N, self.h
+        c = np.arange(N ** 3)
+        cx, cy, cz = self.base.cell_coords(c)
+        xi = np.stack(np.broadcast_arrays((cx[:, None, None, None] + tq[None, :, None, None]) * h,
+                                          (cy[:, None, None, None] + tq[None, None, :, None]) * h,
+                                          (cz[:, None, None, None] + tq[None, None, None, :]) * h),
+                      axis=-1)                                   # global reference coords
+        x = xi @ self.A.T
+        return x[..., 0], x[..., 1], x[..., 2]
+
+    def load_vector(self, f, nq: int | None = None):
+        """b_{c,m} = int_T f phi_m dx by an nq-point Gauss rule per direction."""
+        nq = self.n if nq is None else nq
+        tq, wq1 = gauss_points(nq)
+        n = self.n
+        Lq = np.array([[legendre(i, t) for i in range(n)] for t in tq])
+        X, Y, Z = self.points(nq)
+        Fw = f(X, Y, Z) * (wq1[:, None, None] * wq1[None, :, None] * wq1[None, None, :])
+        b = self.detJ * np.einsum("cabe,ai,bj,el->clji", Fw, Lq, Lq, Lq)
+        return b.reshape(-1)
+
+    def l2_error(self, x, u, nq: int | None = None):
+        nq = self.k + 3 if nq is None else nq
+        tq, wq1 = gauss_points(nq)
+        n, N = self.n, self.N
+        Lq = np.array([[legendre(i, t) for i in range(n)] for t in tq])
+        xc = np.asarray(x, float).reshape(N ** 3, n, n, n)
+        uh = np.einsum("clji,ai,bj,el->cabe", xc, Lq, Lq, Lq)
+        X, Y, Z = self.points(nq)
+        W = wq1[:, None, None] * wq1[None, :, None] * wq1[None, None, :]
+        return math.sqrt(self.detJ * float(((uh - u(X, Y, Z)) ** 2 * W[None]).sum()))

@@ -68,6 +68,7 @@ _SIGS = {
     "dg_diagonal": (ctypes.c_int, [_VP, _VP, _VP]),
     "dg_load_vector": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "dg_set_boundary": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "dg_set_geometry": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "dg_dirichlet_rhs": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), _VP, _VP]),
     "dg_boundary_flux": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_double, _VP, _VP]),
     "dg_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _VP]),
@@ -188,6 +189,16 @@ class Mesh:
         Drops the coefficient: call set_coefficient afterwards."""
         mask = {"dirichlet": DG_BC_DIRICHLET, "flow_x": DG_BC_FLOW_X}.get(bc, bc)
         _check(library().dg_set_boundary(self._h, int(mask)), "dg_set_boundary")
+        self._autograd_logK = None
+
+    def set_geometry(self, A):
+        """Affine geometry x = A xi (3x3, det A > 0; identity = the unit cube).
+        Drops the coefficient: call set_coefficient afterwards."""
+        vals = [float(v) for row in A for v in row]
+        if len(vals) != 9:
+            raise ValueError("A must be 3 x 3")
+        _check(library().dg_set_geometry(self._h, (ctypes.c_double * 9)(*vals)),
+               "dg_set_geometry")
         self._autograd_logK = None
 
     def set_coefficient(self, K, stream=None):

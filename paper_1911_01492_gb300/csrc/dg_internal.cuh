@@ -67,6 +67,12 @@ struct dg_mesh {
   double h;
   double sigma;
   int dirichlet_mask;  // bit f: boundary side f (x-, x+, y-, y+, z-, z+) is Dirichlet
+  // affine geometry x = A xi (dg_set_geometry): metric det A A^-1 A^-T, face
+  // penalty factors det A |A^-T e_d|^2, det A; affine = false for A = I
+  bool affine;
+  double geomG[3][3];
+  double geomKappa[3];
+  double geomDet;
   int device;
   int sm_count;
   DGTab<double> tab64;
@@ -163,6 +169,12 @@ int dg_launch_apply_f64(const dg_mesh* m, const double* x, double* y, const int*
                         cudaStream_t s);
 int dg_launch_apply_f32(const dg_mesh* m, const float* x, float* y, const int* skip,
                         cudaStream_t s);
+// FP64 apply on an affine mesh (dg_affine.cu) and its kernel attributes
+int dg_launch_apply_affine(const dg_mesh* m, const double* x, double* y, const int* skip,
+                           cudaStream_t s);
+int dg_prepare_affine(int n);
+// INVALID_ARG if the mesh is affine (for the paths that assume cube faces)
+int dg_require_cube(const dg_mesh* m, const char* who);
 // traces only (used by the coefficient gradient): U, X, TR of x into the given buffers
 int dg_launch_trace_f64(const dg_mesh* m, const double* x, double* U, double* X, double* TR,
                         cudaStream_t s);

@@ -142,6 +142,12 @@ extern "C" int dg_create_mesh(int n_cells, int degree, dg_mesh** out) {
   m->h = 1.0 / n_cells;
   m->sigma = 2.0 * (degree + 1) * (degree + 1);
   m->dirichlet_mask = DG_BC_DIRICHLET;
+  m->affine = false;
+  m->geomDet = 1.0;
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) m->geomG[i][j] = i == j ? 1.0 : 0.0;
+    m->geomKappa[i] = 1.0;
+  }
   dg_build_tables(m->n, m->sigma, &m->tab64, &m->tab32);
   cudaError_t e = cudaGetDevice(&m->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, m->device);
@@ -171,6 +177,7 @@ extern "C" int dg_create_mesh(int n_cells, int degree, dg_mesh** out) {
   }
   int rc = dg_prepare_apply_f64(m->n);
   if (rc == DG_OK) rc = dg_prepare_apply_f32(m->n);
+  if (rc == DG_OK) rc = dg_prepare_affine(m->n);
   if (rc == DG_OK) rc = dg_prepare_grad(m->n);
   if (rc != DG_OK) {
     free_all(m);
@@ -213,6 +220,14 @@ extern "C" int dg_set_boundary(dg_mesh* m, int dirichlet_mask) {
   m->has_coef = false;  // the face weights depend on it: set the coefficient again
   m->has_diag = false;
   m->has_block = false;
+  return DG_OK;
+}
+
+int dg_require_cube(const dg_mesh* m, const char* who) {
+  if (m != nullptr && m->affine)
+    return dg_fail(DG_ERR_INVALID_ARG,
+                   "%s: not available on an affine geometry (FP64 dg_apply, dg_apply_adjoint, "
+                   "dg_load_vector and the FP64 CG without preconditioner are)", who);
   return DG_OK;
 }
 
@@ -306,6 +321,7 @@ static int check_apply_args(const dg_mesh* m, const void* x, const void* y, int 
 extern "C" int dg_apply(const dg_mesh* m, const void* x, void* y, int prec, void* stream) {
   int rc = check_apply_args(m, x, y, prec, "dg_apply");
   if (rc) return rc;
+  if (prec == DG_FP32 && (rc = dg_require_cube(m, "dg_apply(FP32)"))) return rc;
   if (prec == DG_FP64)
     return dg_launch_apply_f64(m, (const double*)x, (double*)y, nullptr, (cudaStream_t)stream);
   return dg_launch_apply_f32(m, (const float*)x, (float*)y, nullptr, (cudaStream_t)stream);
@@ -315,6 +331,7 @@ extern "C" int dg_apply_adjoint(const dg_mesh* m, const void* ybar, void* xbar, 
                                 void* stream) {
   int rc = check_apply_args(m, ybar, xbar, prec, "dg_apply_adjoint");
   if (rc) return rc;
+  if (prec == DG_FP32 && (rc = dg_require_cube(m, "dg_apply_adjoint(FP32)"))) return rc;
   // a(u, v) = a(v, u): the transposed data flow performs the same contractions.
   if (prec == DG_FP64)
     return dg_launch_apply_f64(m, (const double*)ybar, (double*)xbar, nullptr,
@@ -348,6 +365,7 @@ extern "C" int dg_apply_host(const dg_mesh* mc, const void* x_host, void* y_host
                              void* stream) {
   int rc = check_apply_args(mc, x_host, y_host, prec, "dg_apply_host");
   if (rc) return rc;
+  if ((rc = dg_require_cube(mc, "dg_apply_host"))) return rc;
   dg_mesh* m = const_cast<dg_mesh*>(mc);
   cudaStream_t s = (cudaStream_t)stream;
   rc = ensure_host_pipeline(m);
@@ -423,6 +441,7 @@ extern "C" int dg_coeff_grad(const dg_mesh* mc, const double* u, const double* v
   if (u == nullptr || v == nullptr || g == nullptr)
     return dg_fail(DG_ERR_INVALID_ARG, "dg_coeff_grad: NULL vector");
   if (g == u || g == v) return dg_fail(DG_ERR_INVALID_ARG, "dg_coeff_grad: g aliases u or v");
+  if (int rc0 = dg_require_cube(mc, "dg_coeff_grad")) return rc0;
   dg_mesh* m = const_cast<dg_mesh*>(mc);
   int rc = dg_ensure_grad_ws(m);
   if (rc) return rc;

@@ -128,6 +128,7 @@ extern "C" int dg_diagonal(const dg_mesh* mc, double* d, void* stream) {
   if (mc == nullptr || d == nullptr)
     return dg_fail(DG_ERR_INVALID_ARG, "dg_diagonal: NULL mesh or output");
   if (!mc->has_coef) return dg_fail(DG_ERR_INVALID_ARG, "dg_diagonal: coefficient not set");
+  if (int rc0 = dg_require_cube(mc, "dg_diagonal")) return rc0;
   dg_mesh* m = const_cast<dg_mesh*>(mc);
   cudaStream_t s = (cudaStream_t)stream;
   int rc = dg_ensure_diagonal(m, s);

@@ -78,7 +78,7 @@ extern "C" int dg_load_vector(const dg_mesh* m, const double* f, double* b, void
   if (f == nullptr || b == nullptr) return dg_fail(DG_ERR_INVALID_ARG, "dg_load_vector: NULL vector");
   if ((const void*)f == (const void*)b)
     return dg_fail(DG_ERR_INVALID_ARG, "dg_load_vector: f and b alias");
-  const double h3 = m->h * m->h * m->h;
+  const double h3 = m->h * m->h * m->h * m->geomDet;  // |det J| = h^3 det A
   cudaError_t e = dgk::dispatch_n<double, dgk::LoadVectorF>(m->n, f, b, m->ncells, h3,
                                                             (const DGTab<double>*)&m->tab64,
                                                             (cudaStream_t)stream);
@@ -174,6 +174,7 @@ extern "C" int dg_dirichlet_rhs(const dg_mesh* m, const double* g, double* b, vo
   if (!m->has_coef) return dg_fail(DG_ERR_INVALID_ARG, "dg_dirichlet_rhs: coefficient not set");
   if (g == nullptr || b == nullptr)
     return dg_fail(DG_ERR_INVALID_ARG, "dg_dirichlet_rhs: NULL g or b");
+  if (int rc = dg_require_cube(m, "dg_dirichlet_rhs")) return rc;
   DirichletData data;
   for (int f = 0; f < 6; ++f) {
     if (!std::isfinite(g[f]))
@@ -193,6 +194,7 @@ extern "C" int dg_boundary_flux(const dg_mesh* m, const double* u, int side, dou
   if (!m->has_coef) return dg_fail(DG_ERR_INVALID_ARG, "dg_boundary_flux: coefficient not set");
   if (u == nullptr || q == nullptr)
     return dg_fail(DG_ERR_INVALID_ARG, "dg_boundary_flux: NULL u or q");
+  if (int rc = dg_require_cube(m, "dg_boundary_flux")) return rc;
   if (side < 0 || side > 5)
     return dg_fail(DG_ERR_INVALID_ARG, "dg_boundary_flux: side %d outside 0..5", side);
   if (!((m->dirichlet_mask >> side) & 1))

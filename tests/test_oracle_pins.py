@@ -701,3 +701,103 @@ def test_block_jacobi_blocks_are_spd_and_pcg_reaches_the_direct_solution():
     assert rel <= 1e-12 and np.abs(x - xd).max() <= 1e-9 * np.abs(xd).max()
     _, it_p, _, _ = cg(lambda v: A @ v, b, rtol=1e-12, minv=1.0 / D.diagonal(K))
     assert it_b < it_p
+
+
+# --------------------------------------------------------------------------
+# Affine geometry (problem B): x = A xi.  A = I is the cube operator; a
+# diagonal A = diag(al, be, ga) stretches the axes, and the one-cell K = 1
+# operator is the Kronecker sum of the 1D closed form T with the factors
+# be ga / al, al ga / be, al be / ga (volume, face area over normal length and
+# penalty length scale alike); a sheared A keeps symmetry and definiteness,
+# reproduces harmonic polynomials with mixed derivatives on interior cells,
+# and converges at rate k + 1.
+# --------------------------------------------------------------------------
+
+SHEAR = [[1.0, 0.3, 0.1], [0.0, 1.1, -0.2], [0.05, 0.0, 0.9]]
+
+
+def test_affine_identity_is_the_cube_operator():
+    from oracle.dg_oracle import AffineSIPG
+    for N, k in ((2, 2), (3, 1)):
+        K = inputs.lognormal_coefficient(N, k, seed=50, corr_len=0.5)
+        A1 = SIPG(N, k).assemble(K)
+        A2 = AffineSIPG(N, k, np.eye(3)).assemble(K)
+        assert abs(A1 - A2).max() <= 1e-14 * abs(A1).max()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_affine_stretched_one_cell_is_a_scaled_kronecker_sum(k):
+    from oracle.dg_oracle import AffineSIPG
+    al, be, ga = 0.7, 1.3, 2.1
+    D = AffineSIPG(1, k, np.diag([al, be, ga]))
+    A = D.assemble(np.ones(D.n_dofs)).toarray()
+    T = closed_form_T(k)
+    I = np.eye(k + 1)
+    ref = (be * ga / al * np.kron(I, np.kron(I, T)) + al * ga / be * np.kron(I, np.kron(T, I))
+           + al * be / ga * np.kron(T, np.kron(I, I)))
+    assert np.abs(A - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_affine_sheared_operator_is_symmetric_positive_definite():
+    from oracle.dg_oracle import AffineSIPG
+    N, k = 3, 2
+    D = AffineSIPG(N, k, SHEAR)
+    K = inputs.lognormal_coefficient(N, k, seed=51, corr_len=0.1 * 64 / N)
+    A = D.assemble(K).toarray()
+    assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+    assert np.linalg.eigvalsh(A).min() > 0
+
+
+@pytest.mark.parametrize("pname", ["x", "xy", "x2-y2", "yz+2xz"])
+def test_affine_consistency_on_harmonic_polynomials(pname):
+    from oracle.dg_oracle import AffineSIPG
+    p = {"x": lambda x, y, z: 1.0 + 2.0 * x - y + 0.5 * z,
+         "xy": lambda x, y, z: x * y,
+         "x2-y2": lambda x, y, z: x * x - y * y,
+         "yz+2xz": lambda x, y, z: y * z + 2.0 * x * z}[pname]
+    N, k = 4, 2
+    D = AffineSIPG(N, k, SHEAR)
+    K = np.full(D.n_dofs, 1.7)
+    xp = D.load_vector(p, nq=k + 2) / D.detJ          # mass matrix |det J| I
+    y = D.apply(K, xp).reshape(N ** 3, -1)
+    c = np.arange(N ** 3)
+    cx, cy, cz = c % N, (c // N) % N, c // (N * N)
+    inner = (cx > 0) & (cx < N - 1) & (cy > 0) & (cy < N - 1) & (cz > 0) & (cz < N - 1)
+    assert np.abs(y[inner]).max() <= 1e-11 * np.abs(y).max()
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_affine_convergence_rate(k):
+    from oracle.dg_oracle import AffineSIPG
+    A = np.array(SHEAR)
+    Ai = np.linalg.inv(A)
+    M = Ai @ Ai.T
+
+    def ref_coords(x, y, z):
+        X = np.stack(np.broadcast_arrays(x, y, z), axis=-1) @ Ai.T
+        return X[..., 0], X[..., 1], X[..., 2]
+
+    def u(x, y, z):
+        a, b, c = ref_coords(x, y, z)
+        return np.sin(np.pi * a) * np.sin(np.pi * b) * np.sin(np.pi * c)
+
+    def f(x, y, z):
+        a, b, c = ref_coords(x, y, z)
+        s = [np.sin(np.pi * a), np.sin(np.pi * b), np.sin(np.pi * c)]
+        co = [np.cos(np.pi * a), np.cos(np.pi * b), np.cos(np.pi * c)]
+        out = np.pi ** 2 * (M[0, 0] + M[1, 1] + M[2, 2]) * s[0] * s[1] * s[2]
+        for d in range(3):
+            for e in range(3):
+                if d != e:
+                    other = 3 - d - e
+                    out = out - np.pi ** 2 * M[d, e] * co[d] * co[e] * s[other]
+        return out
+
+    errs = []
+    for N in (2, 4):
+        D = AffineSIPG(N, k, A)
+        Am = D.assemble(np.ones(D.n_dofs)).tocsc()
+        x = spla.spsolve(Am, D.load_vector(f, nq=k + 3))
+        errs.append(D.l2_error(x, u))
+    rate = math.log2(errs[0] / errs[1])
+    assert abs(rate - (k + 1)) <= 0.35, (errs, rate)
