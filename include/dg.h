@@ -107,13 +107,28 @@ int dg_set_boundary(dg_mesh* mesh, int dirichlet_mask);
  * array, row-major) with det A > 0; every cell is then a parallelepiped with
  * Jacobian h A.  The operator is the same SWIPDG form written with the
  * physical gradients, face normals, face areas and penalty length |T| / |F|.
- * A = I (the default) is the unit cube.  On a non-identity geometry the FP64
+ * A = I (the default) is the unit cube (and ends a multilinear geometry set
+ * by dg_set_vertices).  On a non-identity geometry the FP64
  * dg_apply / dg_apply_adjoint, dg_load_vector (f at the mapped Gauss points)
  * and dg_cg_solve with DG_CG_FP64 (no preconditioner) are available; the
  * other calls return INVALID_ARG.  Drops the coefficient: call
  * dg_set_coefficient again afterwards.  Errors: INVALID_ARG (NULL pointer,
  * non-finite entry, det A <= 0), CUDA. */
 int dg_set_geometry(dg_mesh* mesh, const double* A);
+
+/* Multilinear geometry (the paper's problem C, Section 3.3: multilinear
+ * geometries): the vertices of the structured mesh moved to the positions X
+ * (host array of (n_cells+1)^3 points x 3 doubles; vertex (i, j, k) along x, y,
+ * z at ((k (N+1) + j) (N+1) + i) * 3); every cell is the trilinear image of its
+ * reference cube.  The operator is the SWIPDG form with the physical gradients
+ * at every quadrature point, the surface normal and area element at every face
+ * point, each side's own Jacobian in its normal derivative, and penalty length
+ * h_F = (|T-| + |T+|) / (2 |F|) (|T| / |F| on the boundary).  Forms the
+ * per-point geometry once (about 8 doubles per DOF).  The same calls as on an
+ * affine geometry are available; dg_set_geometry returns to an affine one.
+ * Drops the coefficient.  Errors: INVALID_ARG (NULL pointer, non-finite
+ * coordinate, a cell with non-positive Jacobian determinant), OOM, CUDA. */
+int dg_set_vertices(dg_mesh* mesh, const double* X);
 
 /* Set the diffusion coefficient K (device pointer, FP64, layout K[c*n^3 + q],
  * values at the volume Gauss points).  K is the coefficient A = lambda kappa of

@@ -721,3 +721,211 @@ class AffineSIPG:
         X, Y, Z = self.points(nq)
         W = wq1[:, None, None] * wq1[None, :, None] * wq1[None, None, :]
         return math.sqrt(self.detJ * float(((uh - u(X, Y, Z)) ** 2 * W[None]).sum()))
+
+
+# ----------------------------------------------------------------------------
+# Multilinear geometry (the paper's problem C): the N^3 mesh with vertices at
+# given positions X[i, j, k] (i, j, k = 0..N along x, y, z); each cell is the
+# trilinear image of its reference cube, so the Jacobian J(xi) varies from
+# point to point.  Volume: sum_q w_q |det J_q| K_q (J_q^-T grad_ref u) .
+# (J_q^-T grad_ref v).  A face of reference axis d: at each face point the unit
+# normal n = J^-T e_d / |J^-T e_d| and the area element |det J| |J^-T e_d| w_p
+# are properties of the shared surface (the same from both cells); the normal
+# derivative of each side uses that side's own Jacobian, n . J_side^-T
+# grad_ref u_side.  Penalty length h_F = (|T-| + |T+|) / (2 |F|) inside and
+# |T| / |F| on the boundary (|T| the cell volume, |F| the face area).  Vertices
+# of an affine map give AffineSIPG exactly.
+# ----------------------------------------------------------------------------
+
+def _trilinear(Xc, xi):
+    """Position and Jacobian of the trilinear map of one cell.  Xc: corner
+    positions [dz][dy][dx][3]; xi: points (P, 3).  Returns x (P, 3), J (P, 3, 3)
+    with J[p, i, j] = d x_i / d xi_j."""
+    xi = np.asarray(xi, float)
+    s = [np.stack([1.0 - xi[:, a], xi[:, a]], axis=-1) for a in range(3)]   # (P, 2)
+    ds = np.array([-1.0, 1.0])
+    x = np.einsum("zyxi,pz,py,px->pi", Xc, s[2], s[1], s[0])
+    J = np.stack([np.einsum("zyxi,pz,py,x->pi", Xc, s[2], s[1], ds),
+                  np.einsum("zyxi,pz,y,px->pi", Xc, s[2], ds, s[0]),
+                  np.einsum("zyxi,z,py,px->pi", Xc, ds, s[1], s[0])], axis=-1)
+    return x, J
+
+
+class MultilinearSIPG:
+    """SIPG on the trilinear mesh with vertex positions X (N+1, N+1, N+1, 3),
+    indexed [i, j, k] along x, y, z (assembled)."""
+
+    def __init__(self, n_cells: int, degree: int, X, sigma: float | None = None):
+        self.base = SIPG(n_cells, degree, sigma=sigma)
+        self.N, self.k, self.n, self.n3 = n_cells, degree, degree + 1, (degree + 1) ** 3
+        self.sigma = self.base.sigma
+        self.X = np.asarray(X, float).reshape(n_cells + 1, n_cells + 1, n_cells + 1, 3)
+        n = self.n
+        xi, w = self.base.xi, self.base.w
+        idx = np.arange(n)
+        A, B, E = np.meshgrid(idx, idx, idx, indexing="ij")
+        flat = lambda T: T.transpose(2, 1, 0).reshape(-1)          # q = a + n(b + n e)
+        self.qxi = np.stack([xi[flat(A)], xi[flat(B)], xi[flat(E)]], axis=-1)
+        P1, P2 = np.meshgrid(idx, idx, indexing="ij")
+        p1, p2 = P1.T.reshape(-1), P2.T.reshape(-1)
+        self.fxi = {}
+        for d in range(3):
+            t1, t2 = [ax for ax in range(3) if ax != d]
+            for s in (0, 1):
+                pts = np.zeros((n * n, 3))
+                pts[:, d] = float(s)
+                pts[:, t1] = xi[p1]
+                pts[:, t2] = xi[p2]
+                self.fxi[(d, s)] = pts
+        self.aff = AffineSIPG(n_cells, degree, np.eye(3), sigma=sigma)   # face gradient tables
+
+    @property
+    def n_dofs(self):
+        return self.N ** 3 * self.n3
+
+    def corners(self, c):
+        cx, cy, cz = (int(v) for v in self.base.cell_coords(c))
+        Xc = np.empty((2, 2, 2, 3))
+        for dz in (0, 1):
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    Xc[dz, dy, dx] = self.X[cx + dx, cy + dy, cz + dz]
+        return Xc
+
+    def cell_volume(self, c):
+        _, J = _trilinear(self.corners(c), self.qxi)
+        return float(np.sum(self.base.wq * np.abs(np.linalg.det(J))))
+
+    def _face(self, c, d, s):
+        """Face data of cell c on its side s of axis d: area element (P,),
+        unit normal (P, 3) (along +e_d), and the operator of the normal
+        derivative on the cell's own side (P, n3)."""
+        _, J = _trilinear(self.corners(c), self.fxi[(d, s)])
+        Jinv = np.linalg.inv(J)
+        ed = np.zeros(3)
+        ed[d] = 1.0
+        nrm = np.einsum("pji,j->pi", Jinv, ed)                   # J^-T e_d
+        lens = np.linalg.norm(nrm, axis=1)
+        area = np.abs(np.linalg.det(J)) * lens * self.base.face_w[d]
+        nvec = nrm / lens[:, None]
+        m = np.einsum("pij,pj->pi", Jinv, nvec)                  # J^-1 n
+        Dn = np.einsum("pmg,pg->pm", self.aff.face_grad[(d, s)], m)
+        return area, nvec, Dn
+
+    def assemble(self, K) -> sp.csr_matrix:
+        B = self.base
+        Nc, n3, sigma = self.N ** 3, self.n3, self.sigma
+        K = np.asarray(K, float).reshape(Nc, n3)
+        rows, cols, vals = [], [], []
+        loc = np.arange(n3)
+        R, C = np.meshgrid(loc, loc, indexing="ij")
+
+        def add(tc, sc, M):
+            rows.append((tc * n3 + R).reshape(-1))
+            cols.append((sc * n3 + C).reshape(-1))
+            vals.append(M.reshape(-1))
+
+        vol = np.empty(Nc)
+        for c in range(Nc):
+            _, J = _trilinear(self.corners(c), self.qxi)
+            Jinv = np.linalg.inv(J)
+            detJ = np.abs(np.linalg.det(J))
+            vol[c] = float(np.sum(B.wq * detJ))
+            Gp = np.einsum("qmg,qgi->qmi", B.grad, Jinv)          # (J^-T grad)_i = sum_g grad_g Jinv[g, i]
+            wk = detJ * B.wq * K[c]
+            add(c, c, np.einsum("qmd,q,qnd->mn", Gp, wk, Gp))
+        Kbar = B.kbar(K)
+        for d in range(3):
+            V0, V1 = B.face_val[(d, 0)], B.face_val[(d, 1)]
+            for c in range(Nc):
+                coord = B.cell_coords(c)[d]
+                if coord < self.N - 1:
+                    cp = c + B.stride(d)
+                    area, _, Dm = self._face(c, d, 1)
+                    _, _, Dp = self._face(cp, d, 0)
+                    hF = 0.5 * (vol[c] + vol[cp]) / area.sum()
+                    g = 2.0 * Kbar[c] * Kbar[cp] / (Kbar[c] + Kbar[cp])
+                    W = g * area
+                    side = {"m": (V1, 0.5 * Dm), "p": (-V0, 0.5 * Dp)}
+                    for tn, tc in (("m", c), ("p", cp)):
+                        Jt, At = side[tn]
+                        for sn, sc in (("m", c), ("p", cp)):
+                            Js, As = side[sn]
+                            add(tc, sc, Jt.T @ (W[:, None] * (-As + (sigma / hF) * Js))
+                                - At.T @ (W[:, None] * Js))
+                if coord == self.N - 1 and B.dirichlet[2 * d + 1]:
+                    area, _, D1 = self._face(c, d, 1)
+                    hF = vol[c] / area.sum()
+                    W = Kbar[c] * area
+                    add(c, c, V1.T @ (W[:, None] * (-D1 + (sigma / hF) * V1)) - D1.T @ (W[:, None] * V1))
+                if coord == 0 and B.dirichlet[2 * d]:
+                    area, _, D0 = self._face(c, d, 0)
+                    hF = vol[c] / area.sum()
+                    W = Kbar[c] * area
+                    add(c, c, V0.T @ (W[:, None] * (D0 + (sigma / hF) * V0)) + D0.T @ (W[:, None] * V0))
+        Am = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                           shape=(Nc * n3, Nc * n3))
+        return Am.tocsr()
+
+    def apply(self, K, x):
+        return self.assemble(K) @ np.asarray(x, float)
+
+    def _cell_points(self, nq):
+        tq, wq1 = gauss_points(nq)
+        P = np.stack(np.meshgrid(tq, tq, tq, indexing="ij"), axis=-1)   # [a, b, e] -> (xi1, xi2, xi3)
+        P = P.transpose(0, 1, 2, 3).reshape(-1, 3)
+        W = (wq1[:, None, None] * wq1[None, :, None] * wq1[None, None, :]).reshape(-1)
+        return tq, P, W
+
+    def load_vector(self, f, nq: int | None = None):
+        """b_{c,m} = int_T f phi_m dx (nq-point Gauss rule per direction)."""
+        nq = self.n + 1 if nq is None else nq
+        tq, P, W = self._cell_points(nq)
+        n = self.n
+        Lq = np.array([[legendre(i, t) for i in range(n)] for t in tq])
+        out = np.empty((self.N ** 3, self.n3))
+        for c in range(self.N ** 3):
+            x, J = _trilinear(self.corners(c), P)
+            fw = (f(x[:, 0], x[:, 1], x[:, 2]) * W * np.abs(np.linalg.det(J))).reshape(nq, nq, nq)
+            out[c] = np.einsum("abe,ai,bj,el->lji", fw, Lq, Lq, Lq).reshape(-1)
+        return out.reshape(-1)
+
+    def interpolate_reference(self, p, nq: int | None = None):
+        """Coefficients of (p o x)(xi) by the L2 projection in reference
+        coordinates (exact when p o x lies in Q_k, e.g. p linear in x)."""
+        nq = self.n + 2 if nq is None else nq
+        tq, P, W = self._cell_points(nq)
+        n = self.n
+        Lq = np.array([[legendre(i, t) for i in range(n)] for t in tq])
+        out = np.empty((self.N ** 3, self.n3))
+        for c in range(self.N ** 3):
+            x, _ = _trilinear(self.corners(c), P)
+            pw = (p(x[:, 0], x[:, 1], x[:, 2]) * W).reshape(nq, nq, nq)
+            out[c] = np.einsum("abe,ai,bj,el->lji", pw, Lq, Lq, Lq).reshape(-1)
+        return out.reshape(-1)
+
+    def l2_error(self, xc, u, nq: int | None = None):
+        nq = self.k + 3 if nq is None else nq
+        tq, P, W = self._cell_points(nq)
+        n = self.n
+        Lq = np.array([[legendre(i, t) for i in range(n)] for t in tq])
+        xc = np.asarray(xc, float).reshape(self.N ** 3, n, n, n)
+        tot = 0.0
+        for c in range(self.N ** 3):
+            x, J = _trilinear(self.corners(c), P)
+            uh = np.einsum("lji,ai,bj,el->abe", xc[c], Lq, Lq, Lq).reshape(-1)
+            tot += float(np.sum((uh - u(x[:, 0], x[:, 1], x[:, 2])) ** 2 * W * np.abs(np.linalg.det(J))))
+        return math.sqrt(tot)
+
+
+def lattice(n_cells: int, A=None, perturb=None):
+    """Vertex positions (N+1, N+1, N+1, 3) of the uniform lattice on [0,1]^3,
+    mapped by x -> A x and then displaced by perturb(x) (a function of the
+    positions returning displacements)."""
+    t = np.linspace(0.0, 1.0, n_cells + 1)
+    X = np.stack(np.meshgrid(t, t, t, indexing="ij"), axis=-1)
+    if A is not None:
+        X = X @ np.asarray(A, float).T
+    if perturb is not None:
+        X = X + perturb(X)
+    return X

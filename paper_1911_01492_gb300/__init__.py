@@ -69,6 +69,7 @@ _SIGS = {
     "dg_load_vector": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "dg_set_boundary": (ctypes.c_int, [_VP, ctypes.c_int]),
     "dg_set_geometry": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "dg_set_vertices": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "dg_dirichlet_rhs": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), _VP, _VP]),
     "dg_boundary_flux": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_double, _VP, _VP]),
     "dg_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _VP]),
@@ -199,6 +200,19 @@ class Mesh:
             raise ValueError("A must be 3 x 3")
         _check(library().dg_set_geometry(self._h, (ctypes.c_double * 9)(*vals)),
                "dg_set_geometry")
+        self._autograd_logK = None
+
+    def set_vertices(self, X):
+        """Multilinear geometry: vertex positions X, an array (N+1, N+1, N+1, 3)
+        indexed [i, j, k] along x, y, z.  Drops the coefficient."""
+        import numpy as np
+        Xa = np.asarray(X, dtype=np.float64)
+        n1 = self.n_cells + 1
+        if Xa.shape != (n1, n1, n1, 3):
+            raise ValueError(f"X must have shape {(n1, n1, n1, 3)}")
+        flat = np.ascontiguousarray(Xa.transpose(2, 1, 0, 3)).reshape(-1)
+        _check(library().dg_set_vertices(self._h, flat.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_double))), "dg_set_vertices")
         self._autograd_logK = None
 
     def set_coefficient(self, K, stream=None):

@@ -380,6 +380,7 @@ extern "C" int dg_set_geometry(dg_mesh* m, const double* A) {
   }
   m->geomDet = det;
   m->affine = !identity;
+  m->multilinear = false;
   m->has_coef = false;  // the coefficient is set again for the new geometry
   m->has_diag = false;
   m->has_block = false;

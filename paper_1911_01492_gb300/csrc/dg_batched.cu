@@ -888,9 +888,10 @@ extern "C" int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count,
       return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: sample %d has no coefficient", s);
     if ((const void*)b[s] == (const void*)x[s])
       return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: b and x alias (sample %d)", s);
-    if (m->affine)
+    if (m->affine || m->multilinear)
       return dg_fail(DG_ERR_INVALID_ARG,
-                     "dg_cg_solve_batched: sample %d has an affine geometry (not batched)", s);
+                     "dg_cg_solve_batched: sample %d has an affine or multilinear geometry (not "
+                     "batched)", s);
     if (m->lineop64 == nullptr)
       return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: sample %d has no line operators", s);
     for (int t = 0; t < s; ++t)

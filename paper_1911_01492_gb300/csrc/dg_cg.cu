@@ -918,9 +918,10 @@ extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double
   if (block && (jacobi || base != DG_CG_FP64))
     return dg_fail(DG_ERR_INVALID_ARG,
                    "dg_cg_solve: DG_CG_PRECOND_BLOCK goes with DG_CG_FP64 only");
-  if (mc->affine && mode != DG_CG_FP64)
+  if ((mc->affine || mc->multilinear) && mode != DG_CG_FP64)
     return dg_fail(DG_ERR_INVALID_ARG,
-                   "dg_cg_solve: on an affine geometry only DG_CG_FP64 without preconditioner");
+                   "dg_cg_solve: on an affine or multilinear geometry only DG_CG_FP64 without "
+                   "preconditioner");
   dg_mesh* m = const_cast<dg_mesh*>(mc);
   int rc = dg_ensure_solver_ws(m);
   if (rc) return rc;

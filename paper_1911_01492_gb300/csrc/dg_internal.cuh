@@ -28,6 +28,8 @@ struct DGTab {
 
 // Host-side construction of the FP64 tables (dg_tables.cpp) and rounding to FP32.
 void dg_build_tables(int n, double sigma, DGTab<double>* t64, DGTab<float>* t32);
+// the n Gauss-Legendre points and weights on [0,1] of those tables
+void dg_gauss_points(int n, double* xi, double* w);
 
 // CG scalar state kept on the device (one per solve / per batched sample).
 struct DGCGState {
@@ -73,6 +75,12 @@ struct dg_mesh {
   double geomG[3][3];
   double geomKappa[3];
   double geomDet;
+  // multilinear geometry (dg_set_vertices): per volume point the metric
+  // |det J| J^-1 J^-T / h (6 values: xx, yy, zz, xy, xz, yz) [c][6][n^3] and
+  // |det J| [c][n^3]; per face point of every cell face the area element / h
+  // and the own-side vector J^-1 n [c][6][4][n^2]; per cell face sigma / h_F [c][6]
+  bool multilinear;
+  double *geo_vol, *geo_det, *geo_face, *geo_pen;
   int device;
   int sm_count;
   DGTab<double> tab64;
@@ -173,6 +181,8 @@ int dg_launch_apply_f32(const dg_mesh* m, const float* x, float* y, const int* s
 int dg_launch_apply_affine(const dg_mesh* m, const double* x, double* y, const int* skip,
                            cudaStream_t s);
 int dg_prepare_affine(int n);
+int dg_launch_apply_multilinear(const dg_mesh* m, const double* x, double* y, const int* skip,
+                                cudaStream_t s);
 // INVALID_ARG if the mesh is affine (for the paths that assume cube faces)
 int dg_require_cube(const dg_mesh* m, const char* who);
 // traces only (used by the coefficient gradient): U, X, TR of x into the given buffers

@@ -102,7 +102,7 @@ static cudaError_t dmalloc(P** p, size_t count) {
 }
 
 static void free_all(dg_mesh* m) {
-  void* ptrs[] = {m->kt64, m->kt32, m->gh64, m->gh32, m->dgam, m->kbar, m->dflag, m->fw64, m->fw32, m->lineop64, m->diag64, m->dinv64, m->dinv32, m->binv64,
+  void* ptrs[] = {m->kt64, m->kt32, m->gh64, m->gh32, m->dgam, m->kbar, m->dflag, m->fw64, m->fw32, m->lineop64, m->diag64, m->dinv64, m->dinv32, m->binv64, m->geo_vol, m->geo_det, m->geo_face, m->geo_pen,
                   m->U64,  m->X64,  m->TR64, m->U32,  m->X32,  m->TR32, m->U64b,
                   m->X64b, m->TR64b, m->hx_dev, m->hy_dev, m->r64, m->p64, m->q64,
                   m->t64,  m->s64, m->d32,  m->r32, m->p32, m->q32, m->partials, m->state,
@@ -224,10 +224,11 @@ extern "C" int dg_set_boundary(dg_mesh* m, int dirichlet_mask) {
 }
 
 int dg_require_cube(const dg_mesh* m, const char* who) {
-  if (m != nullptr && m->affine)
+  if (m != nullptr && (m->affine || m->multilinear))
     return dg_fail(DG_ERR_INVALID_ARG,
-                   "%s: not available on an affine geometry (FP64 dg_apply, dg_apply_adjoint, "
-                   "dg_load_vector and the FP64 CG without preconditioner are)", who);
+                   "%s: not available on an affine or multilinear geometry (FP64 dg_apply, "
+                   "dg_apply_adjoint, dg_load_vector and the FP64 CG without preconditioner "
+                   "are)", who);
   return DG_OK;
 }
 

@@ -16,7 +16,7 @@ namespace dgk {
 template <int N>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_load_vector(const double* __restrict__ f, double* __restrict__ b, long long ncells, double h3,
-              const __grid_constant__ DGTab<double> tab) {
+              const double* __restrict__ pw, const __grid_constant__ DGTab<double> tab) {
   constexpr int C = Cfg<N>::CPB, N2 = N * N, N3 = N * N * N;
   __shared__ double s[C * N3];
   const long long c0 = (long long)blockIdx.x * C;
@@ -32,7 +32,11 @@ k_load_vector(const double* __restrict__ f, double* __restrict__ b, long long nc
     const double wbe = h3 * tab.w[p] * tab.w[q];
     double v[N], R[N];
 #pragma unroll
-    for (int a = 0; a < N; ++a) v[a] = wbe * tab.w[a] * fc[q * N2 + p * N + a];
+    for (int a = 0; a < N; ++a) {
+      const int idx = q * N2 + p * N + a;
+      // |det J| per point on a multilinear mesh, the constant h^3 det A otherwise
+      v[a] = (pw != nullptr ? wbe * pw[(c0 + lc) * N3 + idx] : wbe) * tab.w[a] * fc[idx];
+    }
     b_bwd<N>(tab, v, R);
 #pragma unroll
     for (int i = 0; i < N; ++i) sc[q * N2 + p * N + i] = R[i];
@@ -64,9 +68,9 @@ template <int N>
 struct LoadVectorF {
   template <typename T>
   static cudaError_t run(const double* f, double* b, long long ncells, double h3,
-                         const DGTab<double>* tab, cudaStream_t s) {
+                         const double* pw, const DGTab<double>* tab, cudaStream_t s) {
     const unsigned blocks = (unsigned)((ncells + Cfg<N>::CPB - 1) / Cfg<N>::CPB);
-    k_load_vector<N><<<blocks, Cfg<N>::THREADS, 0, s>>>(f, b, ncells, h3, *tab);
+    k_load_vector<N><<<blocks, Cfg<N>::THREADS, 0, s>>>(f, b, ncells, h3, pw, *tab);
     return cudaGetLastError();
   }
 };
@@ -78,8 +82,10 @@ extern "C" int dg_load_vector(const dg_mesh* m, const double* f, double* b, void
   if (f == nullptr || b == nullptr) return dg_fail(DG_ERR_INVALID_ARG, "dg_load_vector: NULL vector");
   if ((const void*)f == (const void*)b)
     return dg_fail(DG_ERR_INVALID_ARG, "dg_load_vector: f and b alias");
-  const double h3 = m->h * m->h * m->h * m->geomDet;  // |det J| = h^3 det A
-  cudaError_t e = dgk::dispatch_n<double, dgk::LoadVectorF>(m->n, f, b, m->ncells, h3,
+  // |det J| = h^3 det A (cube, affine) or per point (multilinear)
+  const double h3 = m->multilinear ? 1.0 : m->h * m->h * m->h * m->geomDet;
+  const double* pw = m->multilinear ? m->geo_det : nullptr;
+  cudaError_t e = dgk::dispatch_n<double, dgk::LoadVectorF>(m->n, f, b, m->ncells, h3, pw,
                                                             (const DGTab<double>*)&m->tab64,
                                                             (cudaStream_t)stream);
   if (e != cudaSuccess) return dg_cuda_fail(e, "dg_load_vector: launch");

@@ -174,3 +174,6 @@ void dg_build_tables(int n, double sigma, DGTab<double>* t, DGTab<float>* t32) {
   t->sigma = sigma;
   copy_round<float, double>(*t, t32);
 }
+
+// Gauss-Legendre points and weights on [0,1] (the rule the tables use).
+void dg_gauss_points(int n, double* xi, double* w) { gauss_01(n, xi, w); }

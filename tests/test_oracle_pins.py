@@ -801,3 +801,81 @@ def test_affine_convergence_rate(k):
         errs.append(D.l2_error(x, u))
     rate = math.log2(errs[0] / errs[1])
     assert abs(rate - (k + 1)) <= 0.35, (errs, rate)
+
+
+# --------------------------------------------------------------------------
+# Multilinear geometry (problem C): trilinear cells from perturbed vertices.
+# Affine vertices give the affine operator; on a perturbed mesh the operator
+# stays symmetric positive definite, reproduces linear functions on interior
+# cells exactly (a linear function of x is trilinear in xi, and every integrand
+# of the consistency identity is then a polynomial the Gauss rule integrates
+# exactly), and converges at rate k + 1 on a mesh of the unit cube whose
+# boundary vertices stay on the faces.
+# --------------------------------------------------------------------------
+
+def _perturbed(N, eps, seed, keep_boundary=True):
+    from oracle.dg_oracle import lattice
+    rng = np.random.default_rng(seed)
+    X = lattice(N)
+    D = eps / N * rng.uniform(-1.0, 1.0, X.shape)
+    if keep_boundary:
+        for ax in range(3):
+            on = (np.isclose(X[..., ax], 0.0)) | (np.isclose(X[..., ax], 1.0))
+            D[..., ax] = np.where(on, 0.0, D[..., ax])
+    return X + D
+
+
+def test_multilinear_affine_vertices_give_the_affine_operator():
+    from oracle.dg_oracle import AffineSIPG, MultilinearSIPG, lattice
+    for N, k in ((2, 2), (3, 1)):
+        K = inputs.lognormal_coefficient(N, k, seed=52, corr_len=0.5)
+        A1 = AffineSIPG(N, k, SHEAR).assemble(K)
+        A2 = MultilinearSIPG(N, k, lattice(N, SHEAR)).assemble(K)
+        assert abs(A1 - A2).max() <= 1e-13 * abs(A1).max()
+
+
+def test_multilinear_perturbed_operator_is_symmetric_positive_definite():
+    from oracle.dg_oracle import MultilinearSIPG
+    N, k = 3, 2
+    D = MultilinearSIPG(N, k, _perturbed(N, 0.25, 53))
+    K = inputs.lognormal_coefficient(N, k, seed=54, corr_len=0.1 * 64 / N)
+    A = D.assemble(K).toarray()
+    assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+    assert np.linalg.eigvalsh(A).min() > 0
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_multilinear_consistency_on_linear_functions(k):
+    from oracle.dg_oracle import MultilinearSIPG
+    N = 4
+    D = MultilinearSIPG(N, k, _perturbed(N, 0.3, 55))
+    p = lambda x, y, z: 0.5 + 1.5 * x - 2.0 * y + 0.75 * z
+    xp = D.interpolate_reference(p)
+    y = D.apply(np.full(D.n_dofs, 2.3), xp).reshape(N ** 3, -1)
+    c = np.arange(N ** 3)
+    cx, cy, cz = c % N, (c // N) % N, c // (N * N)
+    inner = (cx > 0) & (cx < N - 1) & (cy > 0) & (cy < N - 1) & (cz > 0) & (cz < N - 1)
+    assert np.abs(y[inner]).max() <= 1e-11 * np.abs(y).max()
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_multilinear_convergence_rate(k):
+    from oracle.dg_oracle import MultilinearSIPG, lattice
+
+    def mesh(N):   # a smooth displacement that keeps every face of the cube in place
+        return lattice(N, perturb=lambda X: 0.08 * np.stack(
+            [np.sin(np.pi * X[..., 0]) * np.sin(2 * np.pi * X[..., 1]) * np.sin(np.pi * X[..., 2]),
+             np.sin(2 * np.pi * X[..., 0]) * np.sin(np.pi * X[..., 1]) * np.sin(np.pi * X[..., 2]),
+             np.sin(np.pi * X[..., 0]) * np.sin(np.pi * X[..., 1]) * np.sin(2 * np.pi * X[..., 2])],
+            axis=-1))
+
+    u = lambda x, y, z: np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+    f = lambda x, y, z: 3 * np.pi ** 2 * u(x, y, z)
+    errs = []
+    for N in (4, 6):     # N = 2 is pre-asymptotic (its vertices barely move)
+        D = MultilinearSIPG(N, k, mesh(N))
+        Am = D.assemble(np.ones(D.n_dofs)).tocsc()
+        x = spla.spsolve(Am, D.load_vector(f, nq=k + 3))
+        errs.append(D.l2_error(x, u))
+    rate = math.log(errs[0] / errs[1]) / math.log(6 / 4)
+    assert abs(rate - (k + 1)) <= 0.35, (errs, rate)
