@@ -618,10 +618,10 @@ SHEAR = [[1.0, 0.3, 0.1], [0.0, 1.1, -0.2], [0.05, 0.0, 0.9]]
 
 
 def run_affine(world, K64):
-    """Problem B (affine geometry): the FP64 apply of the 64^3 Q3 workload on
-    the sheared mesh x = A xi (A = SHEAR), timed like `value` (8 sweeps), with
-    its per-pass times; and the FP64 CG (M = I, f = 1, rtol 1e-10) on 32^3 Q3
-    on that geometry."""
+    """Problems B and C: the FP64 apply of the 64^3 Q3 workload on the sheared
+    mesh x = A xi (A = SHEAR) and on a multilinear mesh (perturbed vertices),
+    timed like `value` (8 sweeps), with per-pass times; and the FP64 CG (M = I,
+    f = 1, rtol 1e-10) on 32^3 Q3 on the sheared geometry."""
     import torch
     import paper_1911_01492_gb300 as dg
     from paper_1911_01492_gb300 import inputs
@@ -637,6 +637,23 @@ def run_affine(world, K64):
     out = {"geometry": SHEAR, "workload": f"{N}^3 Q{k}, lognormal K (seed 2)",
            "apply_gdof_s": world * nd * steps * APPLIES_PER_STEP / (ms * 1e-3) / 1e9,
            "pass_ms": {"k_trace": ms1 / max(napp, 1), "k_cell_aff": ms2 / max(napp, 1)}}
+    m.close()
+    # problem C: the same workload on a multilinear mesh, every interior
+    # vertex moved by up to 0.2 h in each direction (seed 7)
+    rng = np.random.default_rng(7)
+    t = np.linspace(0.0, 1.0, N + 1)
+    V = np.stack(np.meshgrid(t, t, t, indexing="ij"), axis=-1)
+    inner = np.zeros(V.shape[:3], bool)
+    inner[1:-1, 1:-1, 1:-1] = True
+    V = V + np.where(inner[..., None], 0.2 / N * rng.uniform(-1, 1, V.shape), 0.0)
+    m = dg.Mesh(N, k)
+    m.set_vertices(V)
+    m.set_coefficient(torch.from_numpy(K64).cuda())
+    ms, napp, ms1, ms2 = time_applies(m, x, y, steps, 2, world)
+    out["multilinear"] = {"perturbation": "interior vertices moved by up to 0.2 h (seed 7)",
+                          "apply_gdof_s": world * nd * steps * APPLIES_PER_STEP / (ms * 1e-3) / 1e9,
+                          "pass_ms": {"k_trace": ms1 / max(napp, 1),
+                                      "k_cell_ml": ms2 / max(napp, 1)}}
     m.close()
     del x, y
     N2, k2 = 32, 3
