@@ -512,6 +512,50 @@ def run_config4(world):
     return out
 
 
+def run_resilience(world):
+    """Backup and recovery of the CG (Section 2.3) on the 32^3 Q3 lognormal
+    operator, FP64 PCG with M = diag(A) to 1e-10, f = 1: the fault-free solve;
+    the overhead of backups every 32 iterations into pinned host memory (full
+    state, x, x rounded to FP32) without a loss; and, with the DOFs of the
+    first eighth of the cells (four z-planes) lost at half the fault-free
+    iteration count, the iterations and seconds of each recovery."""
+    import torch
+    import paper_1911_01492_gb300 as dg
+    from paper_1911_01492_gb300 import inputs
+    c = CONFIG4
+    N, k = c["n_cells"], c["degree"]
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(inputs.lognormal_coefficient(N, k, seed=c["K_seed"]))
+                      .cuda())
+    b = torch.from_numpy(inputs.constant_load_vector(N, k)).cuda()
+    out = {"workload": f"{N}^3 Q{k}, lognormal K (seed 5), f = 1, FP64 PCG (Jacobi) to 1e-10",
+           "interval": 32, "lost_cells": [0, N ** 3 // 8]}
+    m.cg_solve(b, rtol=1e-10, precond="jacobi")            # diagonal and graphs warm
+    _, st0 = m.cg_solve(b, rtol=1e-10, precond="jacobi")
+    out["fault_free"] = _solve_entry(st0, world)
+    fault = st0["iterations"] // 2
+
+    def entry(st):
+        e = _solve_entry(st, world)
+        e.update({key: st[key] for key in ("fault_injected_at", "backup_iteration",
+                                            "backups_taken", "aux_iterations", "backup_bytes")})
+        return e
+    for backup in ("full", "x64", "x32"):
+        _, st = m.cg_solve_resilient(b, rtol=1e-10, backup=backup, interval=32,
+                                     precond="jacobi", raise_on_error=False)
+        out["no_loss_" + backup] = entry(st)
+    for backup, recovery in (("full", "global"), ("x64", "global"), ("x32", "global"),
+                             ("x64", "local"), ("none", "local"), ("x64", "local_aux"),
+                             ("none", "local_aux")):
+        _, st = m.cg_solve_resilient(b, rtol=1e-10, backup=backup, recovery=recovery,
+                                     interval=32, fault_iteration=fault,
+                                     fault_cells=(0, N ** 3 // 8), aux_rtol=1e-6,
+                                     precond="jacobi", raise_on_error=False)
+        out[f"loss_{backup}_{recovery}"] = entry(st)
+    m.close()
+    return out
+
+
 def _batch_meshes(levels, seed0=1000):
     import torch
     import paper_1911_01492_gb300 as dg
@@ -945,10 +989,11 @@ def main(argv=None):
         r = _leg(run_cg, world)
         cg, K48 = r if isinstance(r, tuple) else (r, None)
 
-    cfg1 = cfg4 = batched = mlmc_r = None
+    cfg1 = cfg4 = batched = mlmc_r = resil = None
     if not args.no_extra:
         cfg1 = _leg(run_config1, world)
         cfg4 = _leg(run_config4, world)
+        resil = _leg(run_resilience, world)
         batched = _leg(run_batched, world, rank, args.batched_sequential, args.batched_full,
                        larger_levels=args.batched)
         mlmc_r = _leg(run_mlmc, world)
@@ -977,7 +1022,8 @@ def main(argv=None):
                 "setup_ms": setup_ms,
                 "clocks": clk.summary(), "cpu_baseline": cpu, "cg": cg,
                 "config2_cg": cg2, "config1": cfg1, "config4": cfg4,
-                "batched_cg": batched, "mlmc": mlmc_r, "affine": affine, "oracle_legs": legs,
+                "batched_cg": batched, "mlmc": mlmc_r, "affine": affine, "resilience": resil,
+                "oracle_legs": legs,
                 "bench_wall_s": time.perf_counter() - t_start}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -204,6 +204,61 @@ int dg_coeff_grad(const dg_mesh* mesh, const double* u, const double* v, double*
 int dg_cg_solve(const dg_mesh* mesh, const double* b, double* x, double rtol, int maxit,
                 int mode, dg_cg_stats* st, void* stream);
 
+/* Backup and recovery of the CG (Section 2.3, compressed in-memory
+ * checkpointing, on one GPU).  The solver copies a backup into pinned host
+ * memory every backup_interval iterations: DG_BACKUP_FULL (x, r, p and the CG
+ * scalars; lossless), DG_BACKUP_X64 (x), DG_BACKUP_X32 (x rounded to FP32, a
+ * lossy compression to half the bytes) or DG_BACKUP_NONE (zero recovery).  A
+ * data loss is injected on the host at the first backup check at or after
+ * fault_iteration: x, r and p of the cells [fault_cell_begin, fault_cell_end)
+ * (lexicographic cell index, x fastest) are set to zero, as if the rank
+ * holding them had failed; -1: no loss.  Recovery:
+ *   DG_RECOVER_GLOBAL     every DOF rolls back to the backup.  With the full
+ *                         state the iteration resumes exactly, so the solution
+ *                         is bit-identical to the fault-free one; with an x
+ *                         backup CG restarts from it.
+ *   DG_RECOVER_LOCAL      only the lost cells take the backup's x (zero
+ *                         without a backup); CG restarts.
+ *   DG_RECOVER_LOCAL_AUX  as LOCAL, then the local auxiliary problem
+ *                         A(F,F) e = (b - A x)(F) on the lost DOFs F, every
+ *                         other DOF held fixed (the Dirichlet layer), solved
+ *                         by CG to aux_rtol (relative to its initial residual)
+ *                         or aux_maxit iterations; x(F) += e; CG restarts.
+ * With no backup yet at the loss, every recovery restarts from the current x
+ * with the lost cells zero (plus the auxiliary solve for LOCAL_AUX). */
+enum { DG_BACKUP_NONE = 0, DG_BACKUP_FULL = 1, DG_BACKUP_X64 = 2, DG_BACKUP_X32 = 3 };
+enum { DG_RECOVER_GLOBAL = 0, DG_RECOVER_LOCAL = 1, DG_RECOVER_LOCAL_AUX = 2 };
+typedef struct {
+  int backup_interval;         /* in: iterations between backups (>= 1)                  */
+  int backup;                  /* in: DG_BACKUP_*                                        */
+  int recovery;                /* in: DG_RECOVER_*                                       */
+  int fault_iteration;         /* in: inject the loss at this iteration or later; -1 none */
+  long long fault_cell_begin;  /* in: first lost cell                                    */
+  long long fault_cell_end;    /* in: one past the last lost cell                        */
+  double aux_rtol;             /* in: LOCAL_AUX tolerance (> 0)                          */
+  int aux_maxit;               /* in: LOCAL_AUX iteration cap (>= 1)                     */
+  int fault_injected_at;       /* out: iteration of the loss (-1: none)                  */
+  int backup_iteration;        /* out: iteration of the backup used (-1: none)           */
+  int backups_taken;           /* out                                                    */
+  int aux_iterations;          /* out: iterations of the auxiliary solve                 */
+  long long backup_bytes;      /* out: bytes of one backup                               */
+} dg_resilience;
+
+/* Solve A(K) x = b by FP64 CG (mode DG_CG_FP64, optionally | DG_CG_PRECOND_JACOBI)
+ * with the backups, the injected loss and the recovery of *res (the paper's
+ * Section 2.3).  b, x: caller-owned FP64 device arrays of n_dofs values (x in:
+ * initial guess, out: solution), as for dg_cg_solve; res: caller-owned host
+ * struct, in and out fields as above.  The pinned host backup (backup_bytes)
+ * is allocated by the call and freed before it returns.  st->iterations
+ * counts every iteration run, the rolled-back ones included;
+ * st->outer_iterations the restarts (recoveries included).  Blocking; ordered
+ * after the work already on `stream`.  Errors as dg_cg_solve; INVALID_ARG for
+ * a NULL res, bad options, another mode or a non-cube mesh; DG_ERR_CUDA if
+ * the pinned backup cannot be allocated. */
+int dg_cg_solve_resilient(const dg_mesh* mesh, const double* b, double* x, double rtol,
+                          int maxit, int mode, dg_resilience* res, dg_cg_stats* st,
+                          void* stream);
+
 /* d = diag(A(K)) (FP64 device pointer, n_dofs values in the layout of x,
  * overwritten): the diagonal the Jacobi preconditioner uses (Section 2.4's
  * PCG with M = diag(A)).  Entry (c, m) is a(phi_{c,m}, phi_{c,m}) of the

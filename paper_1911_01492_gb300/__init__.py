@@ -30,6 +30,13 @@ DG_CG_PRECOND_JACOBI = 256
 DG_CG_PRECOND_BLOCK = 512
 DG_BC_DIRICHLET = 0x3F
 DG_BC_FLOW_X = 0x03
+DG_BACKUP_NONE = 0
+DG_BACKUP_FULL = 1
+DG_BACKUP_X64 = 2
+DG_BACKUP_X32 = 3
+DG_RECOVER_GLOBAL = 0
+DG_RECOVER_LOCAL = 1
+DG_RECOVER_LOCAL_AUX = 2
 
 ERROR_NAMES = {
     DG_ERR_INVALID_ARG: "DG_ERR_INVALID_ARG",
@@ -57,6 +64,8 @@ _SIGS = {
     "dg_coeff_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "dg_cg_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                    _VP, _VP]),
+    "dg_cg_solve_resilient": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_int, _VP, _VP, _VP]),
     "dg_cg_solve_batched": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int,
                                            ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                            ctypes.c_double, ctypes.c_int, _VP, _VP]),
@@ -95,6 +104,26 @@ class CGStats(ctypes.Structure):
                 ("rel_residual_rec", ctypes.c_double),
                 ("seconds", ctypes.c_double),
                 ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Resilience(ctypes.Structure):
+    """dg_resilience: backup, injected loss and recovery of the resilient CG."""
+    _fields_ = [("backup_interval", ctypes.c_int),
+                ("backup", ctypes.c_int),
+                ("recovery", ctypes.c_int),
+                ("fault_iteration", ctypes.c_int),
+                ("fault_cell_begin", ctypes.c_longlong),
+                ("fault_cell_end", ctypes.c_longlong),
+                ("aux_rtol", ctypes.c_double),
+                ("aux_maxit", ctypes.c_int),
+                ("fault_injected_at", ctypes.c_int),
+                ("backup_iteration", ctypes.c_int),
+                ("backups_taken", ctypes.c_int),
+                ("aux_iterations", ctypes.c_int),
+                ("backup_bytes", ctypes.c_longlong)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -338,6 +367,43 @@ class Mesh:
         if raise_on_error:
             _check(rc, "dg_cg_solve")
         return x, st.as_dict()
+
+    def cg_solve_resilient(self, b, x=None, rtol: float = 1e-10, maxit: int = 100000,
+                           backup: str = "full", interval: int = 32, recovery: str = "global",
+                           fault_iteration: int = -1, fault_cells=(0, 0),
+                           aux_rtol: float = 1e-2, aux_maxit: int = 1000,
+                           precond: str | None = None, stream=None,
+                           raise_on_error: bool = True):
+        """FP64 CG with in-memory backups every `interval` iterations
+        (backup "full", "x64", "x32" or "none"), a data loss of the cells
+        fault_cells = (begin, end) injected at the first check at or after
+        fault_iteration (-1: none) and recovery "global", "local" or
+        "local_aux" (local plus the auxiliary problem on the lost cells, to
+        aux_rtol or aux_maxit iterations).  Returns (x, stats dict with the
+        resilience fields added)."""
+        import torch
+        kinds = {"none": DG_BACKUP_NONE, "full": DG_BACKUP_FULL, "x64": DG_BACKUP_X64,
+                 "x32": DG_BACKUP_X32}
+        recs = {"global": DG_RECOVER_GLOBAL, "local": DG_RECOVER_LOCAL,
+                "local_aux": DG_RECOVER_LOCAL_AUX}
+        if precond not in (None, "jacobi"):
+            raise ValueError(f"unknown preconditioner {precond!r}")
+        mode = DG_CG_FP64 | (DG_CG_PRECOND_JACOBI if precond == "jacobi" else 0)
+        if x is None:
+            x = torch.zeros_like(b)
+        res = Resilience(int(interval), kinds[backup], recs[recovery], int(fault_iteration),
+                         int(fault_cells[0]), int(fault_cells[1]), float(aux_rtol),
+                         int(aux_maxit), -1, -1, 0, 0, 0)
+        st = CGStats()
+        rc = library().dg_cg_solve_resilient(self._h, _ptr(b, _f64(), self.n_dofs, "b"),
+                                             _ptr(x, _f64(), self.n_dofs, "x"), float(rtol),
+                                             int(maxit), mode, ctypes.byref(res),
+                                             ctypes.byref(st), _stream(stream))
+        if raise_on_error:
+            _check(rc, "dg_cg_solve_resilient")
+        out = st.as_dict()
+        out.update(res.as_dict())
+        return x, out
 
 
 def cg_solve_batched(meshes, bs, xs, rtol: float = 1e-8, maxit: int = 100000, stream=None,

@@ -530,14 +530,19 @@ double now_s() {
 
 bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
-// One iteration of plain CG on FP64 or FP32 vectors.
+// One iteration of plain CG on FP64 or FP32 vectors.  With f0 <= f1 the
+// operator is restricted to the DOFs [f0, f1): q = A p is set to zero outside
+// them (p, r and x then stay zero there too).
 template <typename T>
-int launch_iteration(dg_mesh* m, T* x, T* r, T* p, T* q, const T* dinv, cudaStream_t s) {
+int launch_iteration(dg_mesh* m, T* x, T* r, T* p, T* q, const T* dinv, cudaStream_t s,
+                     long long f0 = -1, long long f1 = -1) {
   int rc = (sizeof(T) == 8)
                ? dg_launch_apply_f64(m, (const double*)p, (double*)q, &m->state->done, s)
                : dg_launch_apply_f32(m, (const float*)p, (float*)q, &m->state->done, s);
   if (rc) return rc;
   const long long n = m->ndofs;
+  if (f0 > 0) DG_CUDA(cudaMemsetAsync(q, 0, sizeof(T) * (size_t)f0, s));
+  if (f0 >= 0 && f1 < n) DG_CUDA(cudaMemsetAsync(q + f1, 0, sizeof(T) * (size_t)(n - f1), s));
   // 16-byte vector kernels when every operand allows it (x is the caller's)
   const bool vec = aligned16(x) && aligned16(r) && aligned16(p) && aligned16(q) &&
                    aligned16(dinv);
@@ -899,6 +904,275 @@ int cg_mixed_restart(dg_mesh* m, const double* b, double* x, double rtol, int ma
   }
 }
 
+// ---------------------------------------------------------------------------
+// Resilient FP64 CG: the in-memory backup and recovery of Section 2.3 on one
+// GPU.  Every `backup_interval` iterations the solver copies a backup into
+// pinned host memory (the stand-in for the remote rank's memory): the full
+// state (x, r, p and the CG scalars: lossless), x in FP64, or x rounded to
+// FP32 (a lossy compression to half the bytes).  A data loss is injected on
+// the host (x, r and p of a range of cells set to zero, as if the rank that
+// held them had failed) at the first check at or after `fault_iteration`.
+// Recovery: global rollback (every DOF back to the backup: with the full state
+// the iteration resumes exactly and the result is bit-identical to the
+// fault-free solve; with an x backup CG restarts from it), or local recovery
+// (only the lost cells take the backup's x, or zero without a backup, and CG
+// restarts), optionally followed by the local auxiliary problem on the lost
+// cells (aux_solve).  FP64 operator, M = I or M = diag(A).
+// ---------------------------------------------------------------------------
+
+__global__ void k_zero_range(double* __restrict__ a, double* __restrict__ b,
+                             double* __restrict__ c, long long i0, long long i1) {
+  for (long long i = i0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < i1;
+       i += (long long)gridDim.x * blockDim.x) {
+    a[i] = 0.0;
+    b[i] = 0.0;
+    c[i] = 0.0;
+  }
+}
+
+// x[i] = src[i] (FP32 -> FP64) for i in [i0, i1)
+__global__ void k_restore_x32(double* __restrict__ x, const float* __restrict__ src, long long i0,
+                              long long i1) {
+  for (long long i = i0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < i1;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = (double)src[i];
+}
+
+__global__ void k_round_f32(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  GRID_STRIDE(i, n) y[i] = (float)x[i];
+}
+
+__global__ void k_add_range(double* __restrict__ x, const double* __restrict__ e, long long i0,
+                            long long i1) {
+  for (long long i = i0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < i1;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] += e[i];
+}
+
+// The local auxiliary problem of the third recovery method: with F the DOFs
+// [i0, i1) of the lost cells and every other DOF held at its current value
+// (the Dirichlet layer), solve A(F,F) e = (b - A x)(F) by (P)CG to aux_rtol
+// relative to the initial local residual, then x(F) += e.  The backup (or
+// zero) already in x(F) is the initial guess.  Vectors: s64 the local
+// right-hand side, t64 the correction e.
+int aux_solve(dg_mesh* m, const double* b, double* x, const double* dinv, long long i0,
+              long long i1, double aux_rtol, int aux_maxit, int* its, cudaStream_t s) {
+  const long long n = m->ndofs;
+  *its = 0;
+  if (i1 <= i0) return DG_OK;
+  double res2 = 0, b2 = 0;
+  int rc = true_residual(m, b, x, s, &res2, &b2);  // r64 = b - A x
+  if (rc) return rc;
+  DG_CUDA(cudaMemsetAsync(m->s64, 0, sizeof(double) * (size_t)n, s));
+  DG_CUDA(cudaMemcpyAsync(m->s64 + i0, m->r64 + i0, sizeof(double) * (size_t)(i1 - i0),
+                          cudaMemcpyDeviceToDevice, s));
+  DG_CUDA(cudaMemsetAsync(m->t64, 0, sizeof(double) * (size_t)n, s));
+  DG_CUDA(cudaMemsetAsync(m->q64, 0, sizeof(double) * (size_t)n, s));
+  rc = set_state(m, aux_maxit, 0, s);
+  if (rc) return rc;
+  if (dinv)
+    k_init<double, true><<<RED_LAUNCH>>>(m->s64, m->q64, m->r64, m->p64, dinv, n, aux_rtol,
+                                         m->partials, m->state);
+  else
+    k_init<double, false><<<RED_LAUNCH>>>(m->s64, m->q64, m->r64, m->p64, dinv, n, aux_rtol,
+                                          m->partials, m->state);
+  DG_CUDA(cudaGetLastError());
+  rc = run_graph(m, s, chunk_for(m), [&] {
+    return launch_iteration<double>(m, m->t64, m->r64, m->p64, m->q64, dinv, s, i0, i1);
+  });
+  if (rc) return rc;
+  const DGCGState hs = *m->state_host;
+  *its = hs.iters;
+  if (hs.breakdown)
+    return dg_fail(DG_ERR_BREAKDOWN, "dg_cg_solve_resilient: auxiliary problem broke down");
+  k_add_range<<<(unsigned)(m->sm_count * 8), 256, 0, s>>>(x, m->t64, i0, i1);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+int cg_fp64_resilient(dg_mesh* m, const double* b, double* x, double rtol, int maxit,
+                      bool jacobi, dg_resilience* o, dg_cg_stats* st, cudaStream_t s) {
+  const double* dinv = jacobi ? m->dinv64 : nullptr;
+  const long long n = m->ndofs, n3 = (long long)m->n * m->n * m->n;
+  const int kind = o->backup;
+  const size_t bytes64 = sizeof(double) * (size_t)n;
+  o->fault_injected_at = -1;
+  o->backup_iteration = -1;
+  o->backups_taken = 0;
+  o->aux_iterations = 0;
+  o->backup_bytes = kind == DG_BACKUP_FULL ? (long long)(3 * bytes64 + sizeof(DGCGState))
+                  : kind == DG_BACKUP_X64  ? (long long)bytes64
+                  : kind == DG_BACKUP_X32  ? (long long)(bytes64 / 2) : 0;
+  // pinned host backups
+  void *hx = nullptr, *hr = nullptr, *hp = nullptr;
+  DGCGState hstate = {};
+  auto release = [&]() {
+    if (hx) cudaFreeHost(hx);
+    if (hr) cudaFreeHost(hr);
+    if (hp) cudaFreeHost(hp);
+  };
+  if (kind != DG_BACKUP_NONE) {
+    DG_CUDA(cudaMallocHost(&hx, kind == DG_BACKUP_X32 ? bytes64 / 2 : bytes64));
+    if (kind == DG_BACKUP_FULL) {
+      cudaError_t e = cudaMallocHost(&hr, bytes64);
+      if (e == cudaSuccess) e = cudaMallocHost(&hp, bytes64);
+      if (e != cudaSuccess) {
+        release();
+        return dg_cuda_fail(e, "dg_cg_solve_resilient: host backup");
+      }
+    }
+  }
+  double res2 = 0, b2 = 0;
+  int rc = true_residual(m, b, x, s, &res2, &b2);
+  if (rc || b2 == 0.0) {
+    release();
+    return rc ? rc : zero_solution(m, x, st, s);
+  }
+  // (re)start the recurrence from x with `iters` iterations already counted
+  auto start = [&](int iters) -> int {
+    int r = set_state(m, maxit, iters, s);
+    if (r) return r;
+    r = dg_launch_apply_f64(m, x, m->q64, nullptr, s);
+    if (r) return r;
+    if (dinv)
+      k_init<double, true><<<RED_LAUNCH>>>(b, m->q64, m->r64, m->p64, dinv, n, rtol, m->partials,
+                                           m->state);
+    else
+      k_init<double, false><<<RED_LAUNCH>>>(b, m->q64, m->r64, m->p64, dinv, n, rtol,
+                                            m->partials, m->state);
+    DG_CUDA(cudaGetLastError());
+    return DG_OK;
+  };
+  rc = start(0);
+  if (rc) {
+    release();
+    return rc;
+  }
+  const int chunk = o->backup_interval;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  DG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < chunk && rc == DG_OK; ++i)
+    rc = launch_iteration<double>(m, x, m->r64, m->p64, m->q64, dinv, s);
+  cudaError_t ec = cudaStreamEndCapture(s, &graph);
+  if (rc == DG_OK && ec == cudaSuccess) ec = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (rc || ec != cudaSuccess) {
+    release();
+    return rc ? rc : dg_cuda_fail(ec, "dg_cg_solve_resilient: graph");
+  }
+  long long executed = 0;  // iterations actually run, rolled-back ones included
+  int restarts = 0, last_it = 0;
+  const unsigned vblocks = (unsigned)(m->sm_count * 8);
+  // the loop returns through DG_CUDA on a CUDA error; the graph and the host
+  // backups are released after it on every path
+  rc = [&]() -> int {
+    int rc = DG_OK;
+    for (;;) {
+      ec = cudaGraphLaunch(exec, s);
+      if (ec == cudaSuccess)
+        ec = cudaMemcpyAsync(m->state_host, m->state, sizeof(DGCGState), cudaMemcpyDeviceToHost, s);
+      if (ec == cudaSuccess) ec = cudaStreamSynchronize(s);
+      if (ec != cudaSuccess) {
+        rc = dg_cuda_fail(ec, "dg_cg_solve_resilient: iteration");
+        break;
+      }
+      const DGCGState hs = *m->state_host;
+      executed += hs.iters - last_it;
+      last_it = hs.iters;
+      if (hs.breakdown) {
+        rc = dg_fail(DG_ERR_BREAKDOWN, "dg_cg_solve_resilient: breakdown at iteration %d",
+                     hs.iters);
+        break;
+      }
+      if (hs.done) {
+        rc = true_residual(m, b, x, s, &res2, &b2);
+        if (rc) break;
+        const double rel = std::sqrt(res2 / b2);
+        if (st) {
+          st->iterations = (int)executed;
+          st->outer_iterations = restarts;
+          st->rel_residual = rel;
+          st->rel_residual_rec = hs.bnorm2 > 0 ? std::sqrt(hs.rr / hs.bnorm2) : 0.0;
+        }
+        if (rel <= rtol) break;
+        if (hs.iters >= maxit || restarts >= 5) {
+          rc = dg_fail(DG_ERR_NOT_CONVERGED,
+                       "dg_cg_solve_resilient: relative residual %.3e > rtol %.3e", rel, rtol);
+          break;
+        }
+        ++restarts;
+        rc = start(hs.iters);
+        if (rc) break;
+        continue;
+      }
+      if (o->fault_iteration >= 0 && o->fault_injected_at < 0 && hs.iters >= o->fault_iteration) {
+        // the data loss: x, r and p of the lost cells are gone
+        long long c0 = o->fault_cell_begin, c1 = o->fault_cell_end;
+        c0 = c0 < 0 ? 0 : c0;
+        c1 = c1 > m->ncells ? m->ncells : c1;
+      c1 = c1 < c0 ? c0 : c1;  // an empty or reversed range loses nothing
+        k_zero_range<<<vblocks, 256, 0, s>>>(x, m->r64, m->p64, c0 * n3, c1 * n3);
+        o->fault_injected_at = hs.iters;
+        const bool have = o->backups_taken > 0;
+        if (have) o->backup_iteration = hstate.iters;
+        if (kind == DG_BACKUP_FULL && o->recovery == DG_RECOVER_GLOBAL && have) {
+          DG_CUDA(cudaMemcpyAsync(x, hx, bytes64, cudaMemcpyHostToDevice, s));
+          DG_CUDA(cudaMemcpyAsync(m->r64, hr, bytes64, cudaMemcpyHostToDevice, s));
+          DG_CUDA(cudaMemcpyAsync(m->p64, hp, bytes64, cudaMemcpyHostToDevice, s));
+          *m->state_host = hstate;
+          DG_CUDA(cudaMemcpyAsync(m->state, m->state_host, sizeof(DGCGState),
+                                  cudaMemcpyHostToDevice, s));
+          DG_CUDA(cudaStreamSynchronize(s));
+          last_it = hstate.iters;
+          continue;  // resumes exactly at the backup's iteration
+        }
+        if (have) {  // the backup's x: everywhere (global) or on the lost cells (local)
+          const long long i0 = o->recovery == DG_RECOVER_GLOBAL ? 0 : c0 * n3;
+          const long long i1 = o->recovery == DG_RECOVER_GLOBAL ? n : c1 * n3;
+          if (kind == DG_BACKUP_X32) {
+            DG_CUDA(cudaMemcpyAsync(m->d32 + i0, (float*)hx + i0, sizeof(float) * (size_t)(i1 - i0),
+                                    cudaMemcpyHostToDevice, s));
+            k_restore_x32<<<vblocks, 256, 0, s>>>(x, m->d32, i0, i1);
+          } else {
+            DG_CUDA(cudaMemcpyAsync(x + i0, (double*)hx + i0, sizeof(double) * (size_t)(i1 - i0),
+                                    cudaMemcpyHostToDevice, s));
+          }
+        }
+        if (o->recovery == DG_RECOVER_LOCAL_AUX) {
+          rc = aux_solve(m, b, x, dinv, c0 * n3, c1 * n3, o->aux_rtol, o->aux_maxit,
+                         &o->aux_iterations, s);
+          if (rc) break;
+        }
+        rc = start(hs.iters);  // CG restarts from the recovered x
+        if (rc) break;
+        ++restarts;
+        continue;
+      }
+      if (kind != DG_BACKUP_NONE) {  // backup of the state after this chunk
+        if (kind == DG_BACKUP_X32) {
+          k_round_f32<<<vblocks, 256, 0, s>>>(x, m->d32, n);
+          DG_CUDA(cudaMemcpyAsync(hx, m->d32, bytes64 / 2, cudaMemcpyDeviceToHost, s));
+        } else {
+          DG_CUDA(cudaMemcpyAsync(hx, x, bytes64, cudaMemcpyDeviceToHost, s));
+        }
+        if (kind == DG_BACKUP_FULL) {
+          DG_CUDA(cudaMemcpyAsync(hr, m->r64, bytes64, cudaMemcpyDeviceToHost, s));
+          DG_CUDA(cudaMemcpyAsync(hp, m->p64, bytes64, cudaMemcpyDeviceToHost, s));
+        }
+        DG_CUDA(cudaStreamSynchronize(s));
+        hstate = hs;
+        o->backups_taken += 1;
+      }
+    }
+    return rc;
+  }();
+  cudaGraphExecDestroy(exec);
+  release();
+  if (st) st->status = rc;
+  return rc;
+}
+
 }  // namespace
 
 extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double rtol, int maxit,
@@ -943,6 +1217,45 @@ extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double
   }
   cudaError_t e = cudaStreamSynchronize(s);
   if (rc == DG_OK && e != cudaSuccess) rc = dg_cuda_fail(e, "dg_cg_solve: synchronize");
+  if (st) {
+    st->seconds = now_s() - t0;
+    st->status = rc;
+  }
+  return rc;
+}
+
+extern "C" int dg_cg_solve_resilient(const dg_mesh* mc, const double* b, double* x, double rtol,
+                                     int maxit, int mode, dg_resilience* res, dg_cg_stats* st,
+                                     void* stream) {
+  if (mc == nullptr || res == nullptr)
+    return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_resilient: NULL mesh or options");
+  if (!mc->has_coef)
+    return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_resilient: coefficient not set");
+  if (b == nullptr || x == nullptr || b == x)
+    return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_resilient: NULL or aliased b, x");
+  if (mode != DG_CG_FP64 && mode != (DG_CG_FP64 | DG_CG_PRECOND_JACOBI))
+    return dg_fail(DG_ERR_INVALID_ARG,
+                   "dg_cg_solve_resilient: mode %d; DG_CG_FP64 with or without Jacobi", mode);
+  if (!(rtol > 0.0) || !(rtol < 1.0) || maxit < 1)
+    return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_resilient: rtol or maxit out of range");
+  if (res->backup_interval < 1 || res->backup < DG_BACKUP_NONE || res->backup > DG_BACKUP_X32 ||
+      res->recovery < DG_RECOVER_GLOBAL || res->recovery > DG_RECOVER_LOCAL_AUX ||
+      (res->recovery == DG_RECOVER_LOCAL_AUX && (!(res->aux_rtol > 0.0) || res->aux_maxit < 1)))
+    return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_resilient: bad backup options");
+  if (int rc0 = dg_require_cube(mc, "dg_cg_solve_resilient")) return rc0;
+  dg_mesh* m = const_cast<dg_mesh*>(mc);
+  int rc = dg_ensure_solver_ws(m);
+  if (rc) return rc;
+  const double t0 = now_s();
+  DG_CUDA(cudaEventRecord(m->ev, (cudaStream_t)stream));
+  DG_CUDA(cudaStreamWaitEvent(m->solve_stream, m->ev, 0));
+  if (st) *st = dg_cg_stats{};
+  cudaStream_t s = m->solve_stream;
+  const bool jacobi = (mode & DG_CG_PRECOND_JACOBI) != 0;
+  if (jacobi) rc = dg_ensure_diagonal(m, s);
+  if (rc == DG_OK) rc = cg_fp64_resilient(m, b, x, rtol, maxit, jacobi, res, st, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (rc == DG_OK && e != cudaSuccess) rc = dg_cuda_fail(e, "dg_cg_solve_resilient: synchronize");
   if (st) {
     st->seconds = now_s() - t0;
     st->status = rc;
