@@ -661,7 +661,77 @@ def run_batched(world, rank, sequential_samples: int = 1, full: bool = False,
 SHEAR = [[1.0, 0.3, 0.1], [0.0, 1.1, -0.2], [0.05, 0.0, 0.9]]
 
 
-def run_affine(world, K64):
+def run_fp32_apply(m, xd, world, steps=8):
+    """The FP32 apply (dg_apply with DG_FP32) of the benchmark workload, timed
+    like `value` (CUDA events over `steps` sweeps after two warm-up sweeps),
+    with per-pass times."""
+    import torch
+    x32 = xd.float()
+    y32 = torch.empty_like(x32)
+    ms, napp, ms1, ms2 = time_applies(m, x32, y32, steps, 2, world)
+    ms = max_over_ranks(ms, world)
+    nd = m.n_dofs
+    return {"workload": "the benchmark workload in FP32 (x rounded from the FP64 x)",
+            "apply_gdof_s": world * nd * steps * APPLIES_PER_STEP / (ms * 1e-3) / 1e9,
+            "pass_ms": {"pass1": ms1 / max(napp, 1), "pass2": ms2 / max(napp, 1)}}
+
+
+def perturbed_vertices(N, seed=7):
+    """Vertices of the N^3 unit-cube mesh with every interior vertex moved by
+    up to 0.2 h in each direction (uniform, seeded): a multilinear mesh."""
+    rng = np.random.default_rng(seed)
+    t = np.linspace(0.0, 1.0, N + 1)
+    V = np.stack(np.meshgrid(t, t, t, indexing="ij"), axis=-1)
+    inner = np.zeros(V.shape[:3], bool)
+    inner[1:-1, 1:-1, 1:-1] = True
+    return V + np.where(inner[..., None], 0.2 / N * rng.uniform(-1, 1, V.shape), 0.0)
+
+
+def run_geometry_probe(n_cells: int, applies: int = 4):
+    """A few FP64 applies of the n_cells^3 Q3 lognormal operator on the
+    sheared affine mesh and on the perturbed multilinear mesh (for kernel
+    profiles), with wall times."""
+    import torch
+    import paper_1911_01492_gb300 as dg
+    from paper_1911_01492_gb300 import inputs
+    N, k = n_cells, 3
+    K = torch.from_numpy(inputs.lognormal_coefficient(N, k, seed=WORKLOAD["K_seed"])).cuda()
+    x = torch.from_numpy(inputs.uniform_vector(N, k, WORKLOAD["x_seed"])).cuda()
+    y = torch.empty_like(x)
+    for name in ("affine", "multilinear"):
+        m = dg.Mesh(N, k)
+        if name == "affine":
+            m.set_geometry(SHEAR)
+        else:
+            m.set_vertices(perturbed_vertices(N))
+        m.set_coefficient(K)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(applies):
+            m.apply(x, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"geometry": name, "n_cells": N,
+                          "ms_per_apply": 1e3 * (time.perf_counter() - t0) / applies}),
+              flush=True)
+        m.close()
+
+
+# Executed FP64 operations per DOF of the geometry pass-2 kernels at Q3 (ncu
+# instruction counters, DFMA x2 + DADD + DMUL): k_cell_aff 11,056 per cell at
+# 32^3 and 40^3 alike, k_cell_ml 12,571 per cell at 32^3
+EXEC_FP64_GEOMETRY_Q3 = {"k_cell_aff": 11056 / 64, "k_cell_ml": 12571 / 64}
+
+
+def _geometry_roofline(kernel, n, nd, ms, peak_fp64):
+    if n != 4 or not peak_fp64:
+        return None
+    achieved = EXEC_FP64_GEOMETRY_Q3[kernel] * nd / (ms * 1e-3) / 1e12
+    return {"kernel": kernel, "bound": "alu", "unit": "TFLOP/s", "achieved": achieved,
+            "peak": peak_fp64, "frac": achieved / peak_fp64,
+            "executed_flops_per_dof": EXEC_FP64_GEOMETRY_Q3[kernel]}
+
+
+def run_affine(world, K64, peak_fp64=None):
     """Problems B and C: the FP64 apply of the 64^3 Q3 workload on the sheared
     mesh x = A xi (A = SHEAR) and on a multilinear mesh (perturbed vertices),
     timed like `value` (8 sweeps), with per-pass times; and the FP64 CG (M = I,
@@ -680,24 +750,21 @@ def run_affine(world, K64):
     nd = m.n_dofs
     out = {"geometry": SHEAR, "workload": f"{N}^3 Q{k}, lognormal K (seed 2)",
            "apply_gdof_s": world * nd * steps * APPLIES_PER_STEP / (ms * 1e-3) / 1e9,
-           "pass_ms": {"k_trace": ms1 / max(napp, 1), "k_cell_aff": ms2 / max(napp, 1)}}
+           "pass_ms": {"k_trace": ms1 / max(napp, 1), "k_cell_aff": ms2 / max(napp, 1)},
+           "roofline": _geometry_roofline("k_cell_aff", k + 1, nd, ms2 / max(napp, 1),
+                                          peak_fp64)}
     m.close()
-    # problem C: the same workload on a multilinear mesh, every interior
-    # vertex moved by up to 0.2 h in each direction (seed 7)
-    rng = np.random.default_rng(7)
-    t = np.linspace(0.0, 1.0, N + 1)
-    V = np.stack(np.meshgrid(t, t, t, indexing="ij"), axis=-1)
-    inner = np.zeros(V.shape[:3], bool)
-    inner[1:-1, 1:-1, 1:-1] = True
-    V = V + np.where(inner[..., None], 0.2 / N * rng.uniform(-1, 1, V.shape), 0.0)
+    # problem C: the same workload on a multilinear mesh
     m = dg.Mesh(N, k)
-    m.set_vertices(V)
+    m.set_vertices(perturbed_vertices(N))
     m.set_coefficient(torch.from_numpy(K64).cuda())
     ms, napp, ms1, ms2 = time_applies(m, x, y, steps, 2, world)
     out["multilinear"] = {"perturbation": "interior vertices moved by up to 0.2 h (seed 7)",
                           "apply_gdof_s": world * nd * steps * APPLIES_PER_STEP / (ms * 1e-3) / 1e9,
                           "pass_ms": {"k_trace": ms1 / max(napp, 1),
-                                      "k_cell_ml": ms2 / max(napp, 1)}}
+                                      "k_cell_ml": ms2 / max(napp, 1)},
+                          "roofline": _geometry_roofline("k_cell_ml", k + 1, nd,
+                                                         ms2 / max(napp, 1), peak_fp64)}
     m.close()
     del x, y
     N2, k2 = 32, 3
@@ -919,6 +986,9 @@ def main(argv=None):
                          "(for kernel profiles) and exit")
     ap.add_argument("--cg-probe-cells", type=int, default=0, metavar="N",
                     help="with --cg-probe: run it on an N^3 Q4 mesh instead of 48^3")
+    ap.add_argument("--geometry-probe", type=int, default=0, metavar="N",
+                    help="only run a few applies on the affine and multilinear N^3 Q3 "
+                         "meshes (for kernel profiles) and exit")
     ap.add_argument("--batched-full", action="store_true",
                     help="with --batched: also solve the whole 256-sample batch (minutes)")
     ap.add_argument("--n-cells", type=int, default=WORKLOAD["n_cells"],
@@ -933,6 +1003,9 @@ def main(argv=None):
         oracle_leg_main(args)
         return
     world, rank, local = dist_setup()
+    if args.geometry_probe:
+        run_geometry_probe(args.geometry_probe)
+        return
     if args.cg_probe:
         run_cg_probe(args.cg_probe, args.cg_probe_cells)
         return
@@ -975,6 +1048,9 @@ def main(argv=None):
                "steps": e2e_steps}
         del xh, yh
 
+    fp32 = None
+    if not args.no_extra:
+        fp32 = _leg(run_fp32_apply, m, xd, world)
     cg2 = cg = K48 = None
     if not args.no_cg:
         cg2 = _leg(run_config2_cg, m, world)
@@ -982,7 +1058,7 @@ def main(argv=None):
     affine = None
     if not args.no_extra:
         torch.cuda.empty_cache()
-        affine = _leg(run_affine, world, K)
+        affine = _leg(run_affine, world, K, peak_fp64)
     del xd, yd, Kd
     torch.cuda.empty_cache()
     if not args.no_cg:
@@ -1023,6 +1099,7 @@ def main(argv=None):
                 "clocks": clk.summary(), "cpu_baseline": cpu, "cg": cg,
                 "config2_cg": cg2, "config1": cfg1, "config4": cfg4,
                 "batched_cg": batched, "mlmc": mlmc_r, "affine": affine, "resilience": resil,
+                "fp32_apply": fp32,
                 "oracle_legs": legs,
                 "bench_wall_s": time.perf_counter() - t_start}
         print(json.dumps(line), flush=True)
