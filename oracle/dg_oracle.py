@@ -33,7 +33,9 @@ Parity status: every public function is pinned by tests/test_oracle_pins.py
 positive definiteness and the continuum eigenvalue, consistency on harmonic
 polynomials, L2 convergence rates, Euler homogeneity and finite differences of
 the gradient, CG against a direct solve, and the per-cell face coefficient and
-face weights in closed form for a log K quadratic inside the cells).
+face weights in closed form for a log K quadratic inside the cells; the
+Kronecker cell blocks against the assembled blocks of cell-wise constant
+fields and their volume coefficient in closed form).
 """
 from __future__ import annotations
 
@@ -515,6 +517,67 @@ def cell_blocks(A, n3: int):
 def block_jacobi_inverse(A, n3: int):
     """r -> M^-1 r for M = blockdiag(A_cc), each block inverted (LAPACK)."""
     inv = np.linalg.inv(cell_blocks(A, n3))
+    return lambda r: np.einsum("cij,cj->ci", inv, np.asarray(r).reshape(-1, n3)).reshape(-1)
+
+
+# ----------------------------------------------------------------------------
+# Kronecker cell blocks (a reading of Section 3.4's factorised block solves):
+# the cell block of A with K replaced by one number per cell, kvol (by default
+# the Gauss-weighted arithmetic mean of K over the cell).  For a cell-wise
+# constant K the volume part of a cell block is, in the orthonormal basis
+# (mass matrix h^3 I), h K (S1 (+) S1 (+) S1) with the 1D stiffness
+# S1[i][j] = int_0^1 L_i' L_j', and the own-side part of each face is a 1D
+# matrix in the face's normal direction:
+#   lower face (xi = 0): h gamma (sigma a0 a0^T + e (d0 a0^T + a0 d0^T)),
+#   upper face (xi = 1): h gamma (sigma a1 a1^T - e (d1 a1^T + a1 d1^T)),
+# a_s = L(s), d_s = L'(s), e = 1/2 on interior faces (the average) and 1 on
+# Dirichlet boundary faces; zero-flux sides contribute nothing.  So the block
+# is the Kronecker sum S_x (+) S_y (+) S_z of three n x n matrices.
+# ----------------------------------------------------------------------------
+
+def kron_cell_matrices(D, K, kvol=None):
+    """Per cell and direction the 1D matrix S_d (array (cells, 3, n, n)) of the
+    Kronecker cell block; kvol: one volume coefficient per cell (default: the
+    Gauss-weighted arithmetic mean of K over the cell)."""
+    n, h, sigma = D.n, D.h, D.sigma
+    nc = D.n_cells_total
+    dL = np.array([[legendre_deriv(i, t) for i in range(n)] for t in D.xi])   # [a, i]
+    S1 = dL.T @ (D.w[:, None] * dL)
+    a = {s: np.array([legendre(i, float(s)) for i in range(n)]) for s in (0, 1)}
+    d = {s: np.array([legendre_deriv(i, float(s)) for i in range(n)]) for s in (0, 1)}
+    Kc = np.asarray(K, float).reshape(nc, D.n3)
+    kv = Kc @ D.wq if kvol is None else np.asarray(kvol, float)
+    kb = D.kbar(K)
+    cells = np.arange(nc)
+    S = np.empty((nc, 3, n, n))
+    for ax in range(3):
+        S[:, ax] = h * kv[:, None, None] * S1[None]
+        for upper in (False, True):
+            s = 1 if upper else 0
+            gamma, interior, _ = D.face_gamma(kb, cells, ax, upper)
+            active = interior | D.dirichlet[2 * ax + s]
+            e = np.where(interior, 0.5, 1.0)
+            sign = -1.0 if upper else 1.0
+            sym = np.outer(d[s], a[s]) + np.outer(a[s], d[s])
+            F = (sigma * np.outer(a[s], a[s]))[None] + (sign * e)[:, None, None] * sym[None]
+            S[:, ax] += np.where(active, h * gamma, 0.0)[:, None, None] * F
+    return S
+
+
+def kron_sum(Sc):
+    """The n^3 x n^3 Kronecker sum S_x (+) S_y (+) S_z of one cell (x index
+    fastest, as the DOFs)."""
+    n = Sc.shape[-1]
+    eye = np.eye(n)
+    return (np.kron(eye, np.kron(eye, Sc[0])) + np.kron(eye, np.kron(Sc[1], eye))
+            + np.kron(Sc[2], np.kron(eye, eye)))
+
+
+def kron_block_inverse(D, K, kvol=None):
+    """r -> M^-1 r for M = the Kronecker cell blocks, each inverted densely."""
+    S = kron_cell_matrices(D, K, kvol)
+    inv = np.linalg.inv(np.array([kron_sum(S[c]) for c in range(S.shape[0])]))
+    n3 = D.n3
     return lambda r: np.einsum("cij,cj->ci", inv, np.asarray(r).reshape(-1, n3)).reshape(-1)
 
 
