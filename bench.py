@@ -340,7 +340,8 @@ def _solve_entry(st, world):
 
 def run_cg(world, modes=None):
     """Config 3: 48^3 Q4 lognormal K, f = 1; FP64 CG against the mixed CG to
-    a 1e-10 FP64-recomputed residual, without and with M = diag(A)."""
+    a 1e-10 FP64-recomputed residual, without preconditioner, with M = diag(A)
+    and with the Kronecker cell blocks (setup included in the time)."""
     import torch
     import paper_1911_01492_gb300 as dg
     from paper_1911_01492_gb300 import inputs
@@ -357,10 +358,12 @@ def run_cg(world, modes=None):
                       ("mixed_ir_jacobi", dg.DG_CG_MIXED_IR | dg.DG_CG_PRECOND_JACOBI),
                       ("fp64_jacobi", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_JACOBI),
                       ("mixed_ir_restart_jacobi",
-                       dg.DG_CG_MIXED_IR_RESTART | dg.DG_CG_PRECOND_JACOBI))
+                       dg.DG_CG_MIXED_IR_RESTART | dg.DG_CG_PRECOND_JACOBI),
+                      ("mixed_ir_kron", dg.DG_CG_MIXED_IR | dg.DG_CG_PRECOND_KRON),
+                      ("fp64_kron", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_KRON))
     for name, mode in modes:
-        if mode & dg.DG_CG_PRECOND_JACOBI:
-            m.set_coefficient(Kd)  # drops the cached diagonal: the solve forms it
+        if mode & (dg.DG_CG_PRECOND_JACOBI | dg.DG_CG_PRECOND_KRON):
+            m.set_coefficient(Kd)  # drops the cached preconditioner: the solve forms it
         x = torch.zeros_like(b)
         torch.cuda.synchronize()
         barrier(world)
@@ -372,6 +375,9 @@ def run_cg(world, modes=None):
     if out["fp64_jacobi"]["status"] == 0 and out["mixed_ir_jacobi"]["status"] == 0:
         out["speedup_mixed_vs_fp64_jacobi"] = (out["fp64_jacobi"]["seconds"]
                                                / out["mixed_ir_jacobi"]["seconds"])
+    if "mixed_ir_kron" in out and out["mixed_ir_kron"]["status"] == 0:
+        out["speedup_mixed_kron_vs_fp64_jacobi"] = (out["fp64_jacobi"]["seconds"]
+                                                    / out["mixed_ir_kron"]["seconds"])
     m.close()
     return out, K
 
@@ -499,7 +505,7 @@ def run_config4(world):
     out["loss_gradient_adjoint_cg_s"] = time.perf_counter() - t0
     # preconditioners on this operator (FP64 CG to 1e-10, f = 1; each time
     # includes forming the preconditioner): point Jacobi against cell blocks
-    for name in ("jacobi", "block"):
+    for name in ("jacobi", "block", "kron"):
         m.set_coefficient(Kd)          # drops the cached diagonal and blocks
         xs = torch.zeros_like(b)
         torch.cuda.synchronize()
@@ -901,7 +907,9 @@ def run_cg_probe(iters: int, n_cells: int = 0):
     b = torch.from_numpy(inputs.constant_load_vector(N, k)).cuda()
     for name, mode in (("mixed_ir", dg.DG_CG_MIXED_IR), ("fp64", dg.DG_CG_FP64),
                        ("mixed_ir_jacobi", dg.DG_CG_MIXED_IR | dg.DG_CG_PRECOND_JACOBI),
-                       ("fp64_jacobi", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_JACOBI)):
+                       ("fp64_jacobi", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_JACOBI),
+                       ("mixed_ir_kron", dg.DG_CG_MIXED_IR | dg.DG_CG_PRECOND_KRON),
+                       ("fp64_kron", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_KRON)):
         x = torch.zeros_like(b)
         _, st = m.cg_solve(b, x, rtol=1e-12, maxit=iters, mode=mode, raise_on_error=False)
         print(json.dumps({"mode": name, "iterations": st["iterations"],

@@ -49,6 +49,7 @@ enum { DG_FP64 = 0, DG_FP32 = 1 };            /* operator precision            *
 enum { DG_CG_FP64 = 0, DG_CG_MIXED_IR = 1, DG_CG_MIXED_IR_RESTART = 2 };  /* dg_cg_solve modes */
 enum { DG_CG_PRECOND_JACOBI = 256 };  /* OR into a mode: PCG with M = diag(A) */
 enum { DG_CG_PRECOND_BLOCK = 512 };   /* OR into DG_CG_FP64: PCG with M = the cell blocks of A */
+enum { DG_CG_PRECOND_KRON = 1024 };   /* OR into DG_CG_FP64 or DG_CG_MIXED_IR: Kronecker cell blocks */
 /* Boundary conditions (dg_set_boundary): bit f set = boundary side f is Dirichlet,
  * sides in the order x-, x+, y-, y+, z-, z+; the other sides carry zero flux. */
 enum { DG_BC_DIRICHLET = 0x3F, DG_BC_FLOW_X = 0x03 };
@@ -196,6 +197,17 @@ int dg_coeff_grad(const dg_mesh* mesh, const double* u, const double* v, double*
  *   Section 3.4); formed on the first such solve after dg_set_coefficient
  *   (degree 1..4; n^6 doubles per cell, e.g. 125 KB per cell at degree 4);
  *   BREAKDOWN if a block is not positive definite.
+ * DG_CG_FP64 or DG_CG_MIXED_IR | DG_CG_PRECOND_KRON: PCG with M = the
+ *   Kronecker cell blocks: each cell block of the operator with K replaced by
+ *   its Gauss-weighted mean over the cell, which in the orthonormal basis is
+ *   the Kronecker sum S_x (+) S_y (+) S_z of three n x n matrices (1D
+ *   stiffness times h Kmean plus the own-side terms of the two faces of that
+ *   direction, Section 4.1); applied by fast diagonalisation (per cell three
+ *   eigenbases and eigenvalues, 3n^2 + 3n values; 12n flops per DOF), in FP32
+ *   inside the mixed mode.  A reading of the factorised cell-block solves of
+ *   Section 3.4 that costs O(n) per DOF instead of O(n^3).  Formed on the
+ *   first such solve after dg_set_coefficient (any degree); BREAKDOWN if a 1D
+ *   factor is not positive definite.
  * Stops when ||b - A x|| <= rtol ||b|| recomputed in FP64.  Blocking.
  * Returns NOT_CONVERGED at maxit (x holds the last iterate), BREAKDOWN on
  * <p, Ap> <= 0 or non-finite scalars, TIMEOUT if a bounded wait of the mixed

@@ -28,6 +28,7 @@ DG_CG_MIXED_IR = 1
 DG_CG_MIXED_IR_RESTART = 2
 DG_CG_PRECOND_JACOBI = 256
 DG_CG_PRECOND_BLOCK = 512
+DG_CG_PRECOND_KRON = 1024
 DG_BC_DIRICHLET = 0x3F
 DG_BC_FLOW_X = 0x03
 DG_BACKUP_NONE = 0
@@ -348,16 +349,19 @@ class Mesh:
                  mode: int = DG_CG_FP64, stream=None, raise_on_error: bool = True,
                  precond: str | None = None):
         """Solve A x = b (blocking).  precond: None, "jacobi" (PCG with
-        M = diag(A); same as OR-ing DG_CG_PRECOND_JACOBI into mode) or "block"
-        (M = the inverted cell blocks of A; FP64 mode, degree <= 4).
+        M = diag(A); same as OR-ing DG_CG_PRECOND_JACOBI into mode), "block"
+        (M = the inverted cell blocks of A; FP64 mode, degree <= 4) or "kron"
+        (M = the Kronecker cell blocks, fast diagonalisation; FP64 or mixed).
         Returns (x, stats dict)."""
         import torch
-        if precond not in (None, "jacobi", "block"):
+        if precond not in (None, "jacobi", "block", "kron"):
             raise ValueError(f"unknown preconditioner {precond!r}")
         if precond == "jacobi":
             mode |= DG_CG_PRECOND_JACOBI
         elif precond == "block":
             mode |= DG_CG_PRECOND_BLOCK
+        elif precond == "kron":
+            mode |= DG_CG_PRECOND_KRON
         if x is None:
             x = torch.zeros_like(b)
         st = CGStats()

@@ -384,6 +384,7 @@ extern "C" int dg_set_geometry(dg_mesh* m, const double* A) {
   m->has_coef = false;  // the coefficient is set again for the new geometry
   m->has_diag = false;
   m->has_block = false;
+  m->has_kron = false;
   return dg_prepare_affine(m->n);
 }
 

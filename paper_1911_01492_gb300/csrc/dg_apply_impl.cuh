@@ -39,6 +39,34 @@
 
 namespace dgk {
 
+// Sum of partials[0 .. count) in the last block of a grid reduction, by all
+// NT threads of the block in a fixed order: each thread keeps four
+// independent chains of L2 loads (ld.global.cg: the other blocks' partials,
+// published before their ticket increment), then warp 0 adds the threads'
+// sums with a fixed tree.  Valid in warp 0; every thread of the block calls it.
+template <int NT>
+__device__ __forceinline__ double last_block_total(const double* __restrict__ partials,
+                                                   int count, double* scratch) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int b = threadIdx.x;
+  for (; b + 3 * NT < count; b += 4 * NT) {
+    a0 += __ldcg(partials + b);
+    a1 += __ldcg(partials + b + NT);
+    a2 += __ldcg(partials + b + 2 * NT);
+    a3 += __ldcg(partials + b + 3 * NT);
+  }
+  for (; b < count; b += NT) a0 += __ldcg(partials + b);
+  scratch[threadIdx.x] = (a0 + a1) + (a2 + a3);
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    for (int i = threadIdx.x; i < NT; i += 32) t += scratch[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  }
+  return t;
+}
+
 template <int N>
 struct Cfg {
   // cells per block, chosen so a block has ~128-256 threads

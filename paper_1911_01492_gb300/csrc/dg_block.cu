@@ -164,9 +164,9 @@ k_block_apply(const double* __restrict__ binv, const double* __restrict__ r,
   __syncthreads();
   if (!last) return;
   __threadfence();
+  __shared__ double rd[128];
+  const double tot = dgk::last_block_total<128>(partials, (int)gridDim.x, rd);
   if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) tot += ((volatile double*)partials)[b];
     if (!isfinite(tot)) {
       st->breakdown = 1;
       st->done = 1;

@@ -286,8 +286,9 @@ k_dot_pq(const T* __restrict__ p, const T* __restrict__ q, long long n, double* 
 // update; an FP64 refinement is requested (ru_skip = 0, sticky until it runs)
 // when rr' has dropped below delta2 * rmax2 or below tol2, or at the iteration
 // cap; at the cap the FP32 iteration stops.
-// BLK = true (cell-block Jacobi): only x, r, <r, r> and the convergence test;
-// rho and beta are formed by the block kernel from z = M^-1 r afterwards.
+// BLK = true (cell blocks, Kronecker blocks): only x, r, <r, r> and the
+// convergence test (MIXED: the refinement request); rho and beta (MIXED:
+// rho_new and beta) are formed from z = M^-1 r by the kernel that follows.
 template <typename T, bool MIXED, bool PC, bool VEC, bool BLK = false>
 __global__ void __launch_bounds__(DG_RED_THREADS)
 k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
@@ -363,7 +364,7 @@ k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
       st->breakdown = 1;
       st->done = 1;
       st->ru_skip = 1;
-    } else if (BLK) {
+    } else if (BLK && !MIXED) {
       st->rr = rr;
       if (rr <= st->tol2 || st->iters >= st->maxit) st->done = 1;
     } else if (!MIXED) {
@@ -372,9 +373,11 @@ k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
       st->rr = rr;
       if (rr <= st->tol2 || st->iters >= st->maxit) st->done = 1;
     } else {
-      st->rho_new = zr;
       st->rr = rr;
-      st->beta = zr / st->rho;  // next direction update (k_dir32_bulk)
+      if (!BLK) {
+        st->rho_new = zr;
+        st->beta = zr / st->rho;  // next direction update (k_dir32_bulk)
+      }
       if (rr <= st->delta2 * st->rmax2 || rr <= st->tol2 || st->iters >= st->maxit)
         st->ru_skip = 0;
     }
@@ -602,10 +605,19 @@ int launch_iteration_block(dg_mesh* m, double* x, cudaStream_t s) {
 // (fused kernels of dg_mixed32.cu), then d += alpha p, r -= alpha q.  The FP64
 // refinement is not in the captured iteration: it runs between graph replays
 // when an iteration has requested it (refine_mixed).
-int launch_iteration_mixed(dg_mesh* m, const float* dinv, cudaStream_t s) {
+int launch_iteration_mixed(dg_mesh* m, const float* dinv, cudaStream_t s, bool kron = false) {
   const long long n = m->ndofs;
-  int rc = dg_launch_mixed32_dir_cell(m, dinv, s);
+  // with Kronecker blocks the direction update reads z = M^-1 r from q32
+  // (formed after the previous update; q32 is free until the cell kernel)
+  int rc = dg_launch_mixed32_dir_cell(m, kron ? m->q32 : m->r32, dinv, s);
   if (rc) return rc;
+  if (kron) {
+    k_update_xr<float, true, false, true, true><<<RED_LAUNCH>>>(m->d32, m->r32, m->p32, m->q32,
+                                                                nullptr, n, m->partials,
+                                                                m->state);
+    DG_CUDA(cudaGetLastError());
+    return dg_launch_kron_apply(m, m->r32, m->q32, nullptr, DG_KRON_FP32, s);
+  }
   // all operands are the mesh's own allocations (256-byte aligned)
   if (dinv)
     k_update_xr<float, true, true, true><<<RED_LAUNCH>>>(m->d32, m->r32, m->p32, m->q32, dinv,
@@ -617,8 +629,34 @@ int launch_iteration_mixed(dg_mesh* m, const float* dinv, cudaStream_t s) {
   return DG_OK;
 }
 
+// One FP64 PCG iteration with the Kronecker cell blocks: q = A p, alpha, x and
+// r updates with <r, r>, z = M^-1 r with <z, r> (rho, beta), p = z + beta p.
+int launch_iteration_kron(dg_mesh* m, double* x, cudaStream_t s) {
+  int rc = dg_launch_apply_f64(m, m->p64, m->q64, &m->state->done, s);
+  if (rc) return rc;
+  const long long n = m->ndofs;
+  if (aligned16(x)) {
+    k_dot_pq<double, true><<<RED_LAUNCH>>>(m->p64, m->q64, n, m->partials, m->state);
+    k_update_xr<double, false, false, true, true><<<RED_LAUNCH>>>(x, m->r64, m->p64, m->q64,
+                                                                  nullptr, n, m->partials,
+                                                                  m->state);
+  } else {
+    k_dot_pq<double, false><<<RED_LAUNCH>>>(m->p64, m->q64, n, m->partials, m->state);
+    k_update_xr<double, false, false, false, true><<<RED_LAUNCH>>>(x, m->r64, m->p64, m->q64,
+                                                                   nullptr, n, m->partials,
+                                                                   m->state);
+  }
+  DG_CUDA(cudaGetLastError());
+  rc = dg_launch_kron_apply(m, m->r64, m->t64, nullptr, DG_KRON_FP64, s);
+  if (rc) return rc;
+  k_update_p<double, false, true><<<RED_LAUNCH>>>(m->p64, m->t64, nullptr, n, m->state);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
 // FP64 refinement: x += d, r = b - A x (FP64), r32 = (float) r.
-int refine_mixed(dg_mesh* m, const double* b, double* x, const double* dinv, cudaStream_t s) {
+int refine_mixed(dg_mesh* m, const double* b, double* x, const double* dinv, cudaStream_t s,
+                 bool kron = false) {
   const long long n = m->ndofs;
   k_refine_x<<<RED_LAUNCH>>>(x, m->d32, n, m->state);
   int rc = dg_launch_apply_f64(m, x, m->q64, nullptr, s);
@@ -628,6 +666,7 @@ int refine_mixed(dg_mesh* m, const double* b, double* x, const double* dinv, cud
   else
     k_refine_r<false><<<RED_LAUNCH>>>(b, m->q64, m->r64, m->r32, dinv, n, m->partials, m->state);
   DG_CUDA(cudaGetLastError());
+  if (kron) return dg_launch_kron_apply(m, m->r32, m->q32, nullptr, DG_KRON_FP32, s);
   return DG_OK;
 }
 
@@ -697,7 +736,7 @@ int zero_solution(dg_mesh* m, double* x, dg_cg_stats* st, cudaStream_t s) {
 }
 
 int cg_fp64(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_cg_stats* st,
-            bool jacobi, cudaStream_t s, bool block = false) {
+            bool jacobi, cudaStream_t s, bool block = false, bool kron = false) {
   const double* dinv = jacobi ? m->dinv64 : nullptr;
   const int max_restarts = 5;
   int iters = 0, restarts = 0;
@@ -721,9 +760,14 @@ int cg_fp64(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_c
       rc = dg_launch_block_apply(m, m->r64, m->t64, m->p64, true, s);
       if (rc) return rc;
     }
+    if (kron) {
+      rc = dg_launch_kron_apply(m, m->r64, m->t64, m->p64, DG_KRON_FP64_INIT, s);
+      if (rc) return rc;
+    }
     rc = run_graph(m, s, chunk_for(m), [&] {
       return block ? launch_iteration_block(m, x, s)
-                   : launch_iteration<double>(m, x, m->r64, m->p64, m->q64, dinv, s);
+             : kron ? launch_iteration_kron(m, x, s)
+                    : launch_iteration<double>(m, x, m->r64, m->p64, m->q64, dinv, s);
     });
     if (rc) return rc;
     const DGCGState hs = *m->state_host;
@@ -751,7 +795,7 @@ int cg_fp64(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_c
 
 // FP32 CG recurrence with FP64 residual refinement (search direction kept).
 int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_cg_stats* st,
-             bool jacobi, cudaStream_t s) {
+             bool jacobi, cudaStream_t s, bool kron = false) {
   const double* dinv = jacobi ? m->dinv64 : nullptr;
   const float* dinv32 = jacobi ? m->dinv32 : nullptr;
   // refine when the FP32 residual has dropped 5x: measured at 48^3 Q4 to 1e-10,
@@ -794,13 +838,17 @@ int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_
     DG_CUDA(cudaMemcpyAsync(m->state, m->state_host, sizeof(DGCGState), cudaMemcpyHostToDevice,
                             s));
   }
+  if (kron) {  // z = M^-1 r into q32, rho_new = <z, r>, beta = 0 (restart)
+    rc = dg_launch_kron_apply(m, m->r32, m->q32, nullptr, DG_KRON_FP32, s);
+    if (rc) return rc;
+  }
   // replay a graph of FP32 iterations; refine in FP64 whenever one asked for it
   {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     DG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < chunk_for(m) && rc == DG_OK; ++i)
-      rc = launch_iteration_mixed(m, dinv32, s);
+      rc = launch_iteration_mixed(m, dinv32, s, kron);
     cudaError_t ec = cudaStreamEndCapture(s, &graph);
     if (rc) {
       if (graph) cudaGraphDestroy(graph);
@@ -816,7 +864,7 @@ int cg_mixed(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_
       if (ec != cudaSuccess) break;
       if (m->state_host->done) break;
       if (m->state_host->ru_skip == 0) {
-        rc = refine_mixed(m, b, x, dinv, s);
+        rc = refine_mixed(m, b, x, dinv, s, kron);
         if (rc) break;
         continue;
       }
@@ -1186,12 +1234,17 @@ extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double
   if (maxit < 1) return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: maxit=%d < 1", maxit);
   const bool jacobi = (mode & DG_CG_PRECOND_JACOBI) != 0;
   const bool block = (mode & DG_CG_PRECOND_BLOCK) != 0;
-  const int base = mode & ~(DG_CG_PRECOND_JACOBI | DG_CG_PRECOND_BLOCK);
+  const bool kron = (mode & DG_CG_PRECOND_KRON) != 0;
+  const int base = mode & ~(DG_CG_PRECOND_JACOBI | DG_CG_PRECOND_BLOCK | DG_CG_PRECOND_KRON);
   if (base != DG_CG_FP64 && base != DG_CG_MIXED_IR && base != DG_CG_MIXED_IR_RESTART)
     return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: unknown mode %d", mode);
-  if (block && (jacobi || base != DG_CG_FP64))
+  if (block && (jacobi || kron || base != DG_CG_FP64))
     return dg_fail(DG_ERR_INVALID_ARG,
                    "dg_cg_solve: DG_CG_PRECOND_BLOCK goes with DG_CG_FP64 only");
+  if (kron && (jacobi || base == DG_CG_MIXED_IR_RESTART))
+    return dg_fail(DG_ERR_INVALID_ARG,
+                   "dg_cg_solve: DG_CG_PRECOND_KRON goes with DG_CG_FP64 or DG_CG_MIXED_IR "
+                   "only");
   if ((mc->affine || mc->multilinear) && mode != DG_CG_FP64)
     return dg_fail(DG_ERR_INVALID_ARG,
                    "dg_cg_solve: on an affine or multilinear geometry only DG_CG_FP64 without "
@@ -1207,11 +1260,12 @@ extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double
   cudaStream_t s = m->solve_stream;
   if (jacobi) rc = dg_ensure_diagonal(m, s);
   if (block) rc = dg_ensure_block(m, s);
+  if (kron) rc = dg_ensure_kron(m, s);
   if (rc == DG_OK) {
     if (base == DG_CG_FP64)
-      rc = cg_fp64(m, b, x, rtol, maxit, st, jacobi, s, block);
+      rc = cg_fp64(m, b, x, rtol, maxit, st, jacobi, s, block, kron);
     else if (base == DG_CG_MIXED_IR)
-      rc = cg_mixed(m, b, x, rtol, maxit, st, jacobi, s);
+      rc = cg_mixed(m, b, x, rtol, maxit, st, jacobi, s, kron);
     else
       rc = cg_mixed_restart(m, b, x, rtol, maxit, st, jacobi, s);
   }

@@ -104,6 +104,11 @@ struct dg_mesh {
   // cell-block Jacobi: the inverted diagonal cell blocks [c][n^3][n^3] (FP64)
   double* binv64;
   bool has_block;
+  // Kronecker cell blocks: per cell Q_x, Q_y, Q_z (n x n) and their eigenvalues
+  // [c][3n^2 + 3n], FP64 and FP32
+  double* kron64;
+  float* kron32;
+  bool has_kron;
   double* kbar;     // Kbar_c                          [c]
   int* dflag;       // device-side error flag of the setup kernels
 
@@ -190,7 +195,9 @@ int dg_launch_trace_f64(const dg_mesh* m, const double* x, double* U, double* X,
                         cudaStream_t s);
 int dg_launch_coeff_grad(const dg_mesh* m, double* g, cudaStream_t s);
 // fused FP32 kernels of the mixed CG iteration (dg_mixed32.cu)
-int dg_launch_mixed32_dir_cell(const dg_mesh* m, const float* dinv, cudaStream_t s);
+// rin: r32 (z = r, or z = dinv r with dinv), or z = M^-1 r already formed
+int dg_launch_mixed32_dir_cell(const dg_mesh* m, const float* rin, const float* dinv,
+                               cudaStream_t s);
 long long dg_mixed32_blocks(int n, long long ncells);
 // attributes and persistent grid of the mixed kernels (before any capture)
 int dg_prepare_mixed32(dg_mesh* m);
@@ -204,6 +211,13 @@ int dg_ensure_diagonal(dg_mesh* m, cudaStream_t s);
 // cell-block Jacobi (dg_block.cu): the inverted blocks (formed if needed), and
 // z = M^-1 r with <z, r> into the CG state (init: rho and p = z; else beta, rho)
 int dg_ensure_block(dg_mesh* m, cudaStream_t s);
+// Kronecker cell-block preconditioner (dg_kron.cu): factors formed once per
+// coefficient; z = M^-1 r with <z, r> into the CG state (mode: FP64 iteration,
+// FP64 initialisation with p = z, FP32 mixed iteration)
+enum { DG_KRON_FP64 = 0, DG_KRON_FP64_INIT = 1, DG_KRON_FP32 = 2 };
+int dg_ensure_kron(dg_mesh* m, cudaStream_t s);
+int dg_launch_kron_apply(const dg_mesh* m, const void* r, void* z, void* p, int mode,
+                         cudaStream_t s);
 int dg_launch_block_apply(const dg_mesh* m, const double* r, double* z, double* p, bool init,
                           cudaStream_t s);
 // workspace helpers (dg_mesh.cu)

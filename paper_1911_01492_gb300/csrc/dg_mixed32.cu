@@ -547,13 +547,8 @@ k_cell32x2(const float* __restrict__ pg, const float* __restrict__ TR,
   if (!is_last) return;
   __threadfence();
   __shared__ double rd[NT];
-  double a = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += NT) a += ((volatile double*)partials)[b];
-  rd[threadIdx.x] = a;
-  __syncthreads();
+  const double tot = last_block_total<NT>(partials, (int)gridDim.x, rd);
   if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int i = 0; i < NT; ++i) tot += rd[i];
     st->pq = tot;
     if (!(tot > 0.0) || !isfinite(tot)) {
       st->breakdown = 1;
@@ -572,7 +567,8 @@ k_cell32x2(const float* __restrict__ pg, const float* __restrict__ TR,
 template <int N>
 struct Mixed32F {
   template <typename T>
-  static cudaError_t run(const dg_mesh* m, const float* dinv, cudaStream_t s) {
+  static cudaError_t run(const dg_mesh* m, const float* rin, const float* dinv,
+                         cudaStream_t s) {
     constexpr int C = Cfg<N>::CPB, N3 = N * N * N;
     // test hook (read when the iteration is captured): the direction kernel
     // skips its first bulk copy and gives up its wait after a few polls
@@ -583,11 +579,11 @@ struct Mixed32F {
     const unsigned gb = (unsigned)m->dir_bulk_grid[pc];
     if (pc)
       k_dir32_bulk<N, true><<<gb, Dir32Bulk<N, true>::THREADS, Dir32Bulk<N, true>::SMEM, s>>>(
-          m->r32, m->p32, m->TR32, dinv, m->ncells, m->state, limit, stall_now ? 1 : 0,
+          rin, m->p32, m->TR32, dinv, m->ncells, m->state, limit, stall_now ? 1 : 0,
           m->tab32);
     else
       k_dir32_bulk<N, false><<<gb, Dir32Bulk<N, false>::THREADS, Dir32Bulk<N, false>::SMEM, s>>>(
-          m->r32, m->p32, m->TR32, dinv, m->ncells, m->state, limit, stall_now ? 1 : 0,
+          rin, m->p32, m->TR32, dinv, m->ncells, m->state, limit, stall_now ? 1 : 0,
           m->tab32);
     const unsigned blocks2 = (unsigned)((m->ncells + 2 * C - 1) / (2 * C));
     k_cell32x2<N><<<blocks2, Cfg<N>::THREADS, sizeof(F2) * 4 * C * N3, s>>>(
@@ -636,8 +632,9 @@ int dg_prepare_mixed32(dg_mesh* m) {
   return DG_OK;
 }
 
-int dg_launch_mixed32_dir_cell(const dg_mesh* m, const float* dinv, cudaStream_t s) {
-  cudaError_t e = dgk::dispatch_n<float, dgk::Mixed32F>(m->n, m, dinv, s);
+int dg_launch_mixed32_dir_cell(const dg_mesh* m, const float* rin, const float* dinv,
+                               cudaStream_t s) {
+  cudaError_t e = dgk::dispatch_n<float, dgk::Mixed32F>(m->n, m, rin, dinv, s);
   if (e != cudaSuccess) return dg_cuda_fail(e, "mixed-precision FP32 kernels launch");
   return DG_OK;
 }

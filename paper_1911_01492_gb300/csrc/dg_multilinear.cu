@@ -522,5 +522,6 @@ extern "C" int dg_set_vertices(dg_mesh* m, const double* X) {
   m->has_coef = false;
   m->has_diag = false;
   m->has_block = false;
+  m->has_kron = false;
   return DG_OK;
 }
