@@ -171,31 +171,19 @@ __device__ __forceinline__ void kron_finish(double part, double* __restrict__ pa
   }
 }
 
-// MODE: 0 FP64 PCG iteration (beta = <z,r> / rho, rho = <z,r>); 1 FP64
-// initialisation (rho = <z,r>, p = z, runs even when done); 2 FP32 mixed
-// iteration (rho_new = <z,r>, beta = 0 on a restart, else <z,r> / rho).
-// Thread (cell lc, plane t) contracts the N lines of plane t in each phase,
-// in place in shared memory, with the cell's 1D factor held in registers.
-// <z, r> = sum over the transformed values t of t^2 / (lx + ly + lz), formed
-// where the scaling is applied; the terms are positive, so the per-thread
-// sums (FP32 in the FP32 kernel) stay within n u relative, and threads and
-// blocks are added in FP64.  The FP32 kernel scales with a fast reciprocal
-// (two ulps: the preconditioner only needs to be a fixed symmetric positive
-// definite operator).
-template <int N, typename T, int MODE>
-__global__ void __launch_bounds__(KronCfg<N, T>::THREADS)
-k_kron_apply(const T* __restrict__ KD, const T* __restrict__ r, T* __restrict__ z,
-             T* __restrict__ p, long long ncells, double* __restrict__ partials, DGCGState* st) {
-  using KC = KronCfg<N, T>;
-  constexpr int C = KC::C, N2 = N * N, N3 = N * N * N, NT = KC::THREADS, KS = KC::KS;
-  if (MODE != 1 && st->done) return;
-  __shared__ T sw[C * N3], sq[C * KS];
-  __shared__ double rd[NT];
-  const long long c0 = (long long)blockIdx.x * C;
-  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
-  for (int i = threadIdx.x; i < nblk * N3; i += NT) sw[i] = r[c0 * N3 + i];
-  for (int i = threadIdx.x; i < nblk * KS; i += NT) sq[i] = KD[c0 * KS + i];
-  __syncthreads();
+// z = M^-1 r on the block's cells, in place in sw (the cells' values in their
+// own order; sq holds their factors): thread (cell lc, plane t) contracts the
+// N lines of plane t in each phase with the cell's 1D factor in registers.
+// Returns the thread's part of <z, r> = sum over the transformed values t of
+// t^2 / (lx + ly + lz), formed where the scaling is applied; the terms are
+// positive, so per-thread sums (FP32 in the FP32 kernels) stay within n u
+// relative, and threads and blocks are added in FP64.  In FP32 the scaling
+// uses a fast reciprocal (two ulps: the preconditioner only needs to be a
+// fixed symmetric positive definite operator).  Every thread of the block
+// calls it; it synchronises before returning.
+template <int N, typename T>
+__device__ __forceinline__ T kron_solve_cells(T* sw, const T* sq, int nblk) {
+  constexpr int N2 = N * N, N3 = N * N * N, KS = 3 * N2 + 3 * N;
   const int lc = threadIdx.x / N;
   const int t = threadIdx.x - lc * N;
   const bool active = lc < nblk;
@@ -236,7 +224,7 @@ k_kron_apply(const T* __restrict__ KD, const T* __restrict__ r, T* __restrict__ 
     for (int i = 0; i < N; ++i) line(t * N2 + i, N, true);
   }
   __syncthreads();
-  T acc = T(0);  // positive terms: FP32 sums stay within n u relative
+  T acc = T(0);
   if (active) {  // z-lines (i, j = t): (Q_z)^T, the scaling, Q_z
     load_q(Qz);
 #pragma unroll
@@ -278,20 +266,48 @@ k_kron_apply(const T* __restrict__ KD, const T* __restrict__ r, T* __restrict__ 
     for (int j = 0; j < N; ++j) line(t * N2 + j * N, 1, false);
   }
   __syncthreads();
+  return acc;
+}
+
+// Sum of one double per thread over the block, fixed order; valid in warp 0.
+template <int NT>
+__device__ __forceinline__ double block_total(double v, double* rd) {
+  rd[threadIdx.x] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    for (int i = threadIdx.x; i < NT; i += 32) s += rd[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  }
+  __syncthreads();
+  return s;
+}
+
+// MODE: 0 FP64 PCG iteration (beta = <z,r> / rho, rho = <z,r>); 1 FP64
+// initialisation (rho = <z,r>, p = z, runs even when done); 2 FP32 mixed
+// iteration (rho_new = <z,r>, beta = 0 on a restart, else <z,r> / rho).
+template <int N, typename T, int MODE>
+__global__ void __launch_bounds__(KronCfg<N, T>::THREADS)
+k_kron_apply(const T* __restrict__ KD, const T* __restrict__ r, T* __restrict__ z,
+             T* __restrict__ p, long long ncells, double* __restrict__ partials, DGCGState* st) {
+  using KC = KronCfg<N, T>;
+  constexpr int C = KC::C, N3 = N * N * N, NT = KC::THREADS, KS = KC::KS;
+  if (MODE != 1 && st->done) return;
+  __shared__ T sw[C * N3], sq[C * KS];
+  __shared__ double rd[NT];
+  const long long c0 = (long long)blockIdx.x * C;
+  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
+  for (int i = threadIdx.x; i < nblk * N3; i += NT) sw[i] = r[c0 * N3 + i];
+  for (int i = threadIdx.x; i < nblk * KS; i += NT) sq[i] = KD[c0 * KS + i];
+  __syncthreads();
+  const T acc = kron_solve_cells<N, T>(sw, sq, nblk);
   for (int i = threadIdx.x; i < nblk * N3; i += NT) {
     const T zv = sw[i];
     z[c0 * N3 + i] = zv;
     if (MODE == 1) p[c0 * N3 + i] = zv;
   }
-  rd[threadIdx.x] = (double)acc;
-  __syncthreads();
-  double part = 0.0;
-  if (threadIdx.x < 32) {
-    for (int i = threadIdx.x; i < NT; i += 32) part += rd[i];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-  }
-  __syncthreads();  // rd is reused by the last block
+  const double part = block_total<NT>((double)acc, rd);
   kron_finish<NT, MODE>(part, partials, st, rd);
 }
 

@@ -34,7 +34,7 @@ import time
 
 import numpy as np
 
-from . import DG_BC_FLOW_X, Mesh, cg_solve_batched
+from . import DG_BC_FLOW_X, DG_CG_MIXED_IR, Mesh, cg_solve_batched
 from . import inputs
 
 G_FLOW = (1.0, 0.0, 0.0, 0.0, 0.0, 0.0)   # p = 1 at x = 0, p = 0 at x = 1
@@ -65,13 +65,20 @@ class FlowLevels:
     """Pooled meshes of the flow problem for a list of levels [(n_cells, degree)]."""
 
     def __init__(self, levels, pool: int = 16, corr_len: float = 0.1, variance: float = 1.0,
-                 rtol: float = 1e-10, precond: str | None = "jacobi"):
+                 rtol: float = 1e-10, precond: str | None = "jacobi", solver: str = "batched"):
+        """solver: "batched" (the lock-step batched FP64 CG over the pooled
+        samples, with precond None or "jacobi") or "mixed" (one mixed-precision
+        CG per sample, FP32 iterations with FP64 refinement, with the
+        Kronecker cell blocks)."""
+        if solver not in ("batched", "mixed"):
+            raise ValueError(f"unknown solver {solver!r}")
         self.levels = [tuple(l) for l in levels]
         self.pool = pool
         self.corr_len = corr_len
         self.variance = variance
         self.rtol = rtol
         self.precond = precond
+        self.solver = solver
         self._meshes = {}
 
     def _mesh(self, level: int, slot: int) -> Mesh:
@@ -114,8 +121,12 @@ class FlowLevels:
             torch.cuda.synchronize()
             t_gen += time.perf_counter() - t0
             t0 = time.perf_counter()
-            st = cg_solve_batched(meshes, bs, xs, rtol=self.rtol, maxit=200000,
-                                  precond=self.precond)
+            if self.solver == "batched":
+                st = cg_solve_batched(meshes, bs, xs, rtol=self.rtol, maxit=200000,
+                                      precond=self.precond)
+            else:
+                st = [m.cg_solve(b, x, rtol=self.rtol, maxit=200000, mode=DG_CG_MIXED_IR,
+                                 precond="kron")[1] for m, b, x in zip(meshes, bs, xs)]
             q = [m.boundary_flux(x, 0, G_FLOW[0]) for m, x in zip(meshes, xs)]
             qv = torch.cat(q).cpu().numpy()
             t_solve += time.perf_counter() - t0

@@ -46,3 +46,10 @@ def test_coupled_fields_share_one_realization():
     assert set(np.round(np.log(Kc), 12)) <= set(np.round(np.log(Kf), 12))
     Kc2, _ = inputs.lognormal_on_levels([(2, 1), (4, 1)], seed=4)
     assert np.abs(Kc - Kc2).max() > 0
+
+
+def test_flow_levels_rejects_unknown_solver():
+    import pytest
+    from paper_1911_01492_gb300 import mlmc
+    with pytest.raises(ValueError, match="solver"):
+        mlmc.FlowLevels([(2, 1)], solver="direct")
