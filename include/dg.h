@@ -207,7 +207,8 @@ int dg_coeff_grad(const dg_mesh* mesh, const double* u, const double* v, double*
  *   inside the mixed mode.  A reading of the factorised cell-block solves of
  *   Section 3.4 that costs O(n) per DOF instead of O(n^3).  Formed on the
  *   first such solve after dg_set_coefficient (any degree); BREAKDOWN if a 1D
- *   factor is not positive definite.
+ *   factor has a negative eigenvalue (a direction with only zero-flux faces,
+ *   one cell across, has a singular factor, which is allowed).
  * Stops when ||b - A x|| <= rtol ||b|| recomputed in FP64.  Blocking.
  * Returns NOT_CONVERGED at maxit (x holds the last iterate), BREAKDOWN on
  * <p, Ap> <= 0 or non-finite scalars, TIMEOUT if a bounded wait of the mixed

@@ -283,9 +283,9 @@ k_dot_pq(const T* __restrict__ p, const T* __restrict__ q, long long n, double* 
 // with z = M^-1 r (= rr' without M).
 // MIXED = false: convergence test on rr', beta = rho'/rho, rho = rho'.
 // MIXED = true: rho' goes to rho_new and beta is formed for the direction
-// update; an FP64 refinement is requested (ru_skip = 0, sticky until it runs)
-// when rr' has dropped below delta2 * rmax2 or below tol2, or at the iteration
-// cap; at the cap the FP32 iteration stops.
+// update; an FP64 refinement is requested (ru_skip = 0, until it runs) when
+// rr' has dropped below delta2 * rmax2 or below tol2, or at the iteration
+// cap; the FP32 iteration kernels then skip until the refinement has run.
 // BLK = true (cell blocks, Kronecker blocks): only x, r, <r, r> and the
 // convergence test (MIXED: the refinement request); rho and beta (MIXED:
 // rho_new and beta) are formed from z = M^-1 r by the kernel that follows.
@@ -294,7 +294,11 @@ __global__ void __launch_bounds__(DG_RED_THREADS)
 k_update_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
             const T* __restrict__ q, const T* __restrict__ dinv, long long n, double* partials,
             DGCGState* st) {
-  if (st->done || (MIXED && st->iters >= st->maxit)) return;
+  // MIXED: the FP32 iterations stop once an FP64 refinement is pending
+  // (ru_skip = 0) until it has run: iterating on in FP32 after the FP32
+  // residual has converged corrupts the search direction that the refinement
+  // keeps (seen on systems of 64 DOFs, which converge within one graph chunk)
+  if (st->done || (MIXED && (st->iters >= st->maxit || st->ru_skip == 0))) return;
   const T a = (T)st->alpha;
   using A = typename AccOf<T>::type;
   A a4[4], z4[4];

@@ -110,8 +110,13 @@ k_kron_setup(const double* __restrict__ kt, const double* __restrict__ gh,
       o64[d * N2 + i * N + j] = V[i][j];
       o32[d * N2 + i * N + j] = (float)V[i][j];
     }
-    const double lam = A[i][i];
-    ok = ok && lam > 0.0 && isfinite(lam);
+    // a direction whose two faces are both zero-flux boundary faces (one cell
+    // across) has the singular factor h Kmean S1: its zero eigenvalue, up to
+    // rounding, is kept at zero (the sum over the three directions stays
+    // positive as long as another direction has a face with gamma > 0)
+    double lam = A[i][i];
+    if (lam < 0.0 && lam > -1e-12 * sqrt(scale)) lam = 0.0;
+    ok = ok && lam >= 0.0 && isfinite(lam);
     o64[3 * N2 + d * N + i] = lam;
     o32[3 * N2 + d * N + i] = (float)lam;
   }
@@ -294,6 +299,7 @@ k_kron_apply(const T* __restrict__ KD, const T* __restrict__ r, T* __restrict__ 
   using KC = KronCfg<N, T>;
   constexpr int C = KC::C, N3 = N * N * N, NT = KC::THREADS, KS = KC::KS;
   if (MODE != 1 && st->done) return;
+  if (MODE == 2 && st->ru_skip == 0) return;  // an FP64 refinement is pending
   __shared__ T sw[C * N3], sq[C * KS];
   __shared__ double rd[NT];
   const long long c0 = (long long)blockIdx.x * C;
@@ -371,7 +377,8 @@ int dg_ensure_kron(dg_mesh* m, cudaStream_t s) {
   DG_CUDA(cudaMemcpyAsync(&flag, m->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
   DG_CUDA(cudaStreamSynchronize(s));
   if (flag)
-    return dg_fail(DG_ERR_BREAKDOWN, "Kronecker cell blocks: a 1D factor is not positive definite");
+    return dg_fail(DG_ERR_BREAKDOWN,
+                   "Kronecker cell blocks: a 1D factor has a negative eigenvalue");
   m->has_kron = true;
   return DG_OK;
 }

@@ -160,7 +160,8 @@ k_dir32_bulk(const float* __restrict__ r, float* __restrict__ p, float* __restri
              long long limit, int stall_test, const __grid_constant__ DGTab<float> tab) {
   using B = Dir32Bulk<N, PC>;
   constexpr int N3 = B::N3, G = B::G, NT = B::THREADS;
-  if (st->done || st->iters >= st->maxit) return;
+  // nothing to do once done, at the cap, or with an FP64 refinement pending
+  if (st->done || st->iters >= st->maxit || st->ru_skip == 0) return;
   const float beta = (float)st->beta;  // set once by the kernel that formed rho_new
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);
@@ -271,7 +272,8 @@ k_cell32x2(const float* __restrict__ pg, const float* __restrict__ TR,
            const __grid_constant__ DGTab<float> tab) {
   constexpr int C = Cfg<N>::CPB, N2 = N * N, N3 = N * N * N, NT = Cfg<N>::THREADS;
   constexpr float S2 = 4.0f * N * N;  // 2 sigma, sigma = 2 (k+1)^2
-  if (st->done || st->iters >= st->maxit) return;
+  // nothing to do once done, at the cap, or with an FP64 refinement pending
+  if (st->done || st->iters >= st->maxit || st->ru_skip == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   F2* su = reinterpret_cast<F2*>(smem_raw);
   F2* sx = su + C * N3;

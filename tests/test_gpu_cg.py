@@ -314,3 +314,27 @@ def test_cg_first_iterates_full_size_48cubed_q4(dg, mode, precond):
     tol = 1e-10 if mode == 0 else 1e-4
     assert relmax(x.cpu().numpy(), xref) <= tol
     m.close()
+
+
+@pytest.mark.parametrize("N,k", [(1, 1), (2, 1), (1, 2), (2, 2), (1, 4)])
+@pytest.mark.parametrize("bc", ["dirichlet", "flow_x"])
+@pytest.mark.parametrize("precond", [None, "jacobi", "kron"])
+def test_mixed_cg_converges_on_tiny_meshes(dg, N, k, bc, precond):
+    """Systems of 8 to 512 DOFs, which the FP32 iteration converges within one
+    graph chunk: the FP32 kernels must stop at the refinement request (an
+    iteration on FP32 noise corrupted the kept search direction, or made
+    <p, Ap> <= 0), and the solve reaches 1e-11 with the oracle's residual."""
+    import torch
+    D = SIPG(N, k, bc=bc)
+    K = inputs.lognormal_coefficient(N, k, seed=31, corr_len=0.5)
+    m = dg.Mesh(N, k)
+    m.set_boundary(bc)
+    m.set_coefficient(torch.from_numpy(K).cuda())
+    if bc == "flow_x":
+        b = D.dirichlet_rhs(K, (1.0, 0.0, 0.0, 0.0, 0.0, 0.0))
+    else:
+        b = inputs.uniform_vector(N, k, 32)
+    x, st = m.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-11, maxit=20000, mode=1,
+                       precond=precond)
+    assert st["status"] == 0 and st["iterations"] < 2000, st
+    assert np.linalg.norm(b - D.apply(K, x.cpu().numpy())) <= 1.05e-11 * np.linalg.norm(b)
