@@ -33,9 +33,10 @@ Parity status: every public function is pinned by tests/test_oracle_pins.py
 positive definiteness and the continuum eigenvalue, consistency on harmonic
 polynomials, L2 convergence rates, Euler homogeneity and finite differences of
 the gradient, CG against a direct solve, and the per-cell face coefficient and
-face weights in closed form for a log K quadratic inside the cells; the
-Kronecker cell blocks against the assembled blocks of cell-wise constant
-fields and their volume coefficient in closed form).
+face weights in closed form for a log K quadratic inside the cells), and by
+tests/test_oracle_kron_pins.py (the Kronecker cell blocks against the
+assembled blocks of cell-wise constant fields and their volume coefficient in
+closed form).
 """
 from __future__ import annotations
 

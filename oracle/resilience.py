@@ -32,7 +32,7 @@ The stopping rule is the one of dg_oracle.cg: recursive ||r|| <= rtol ||b||,
 then the true residual, restarting from x while it is above rtol (at most
 max_restarts restarts, recovery restarts included).
 
-Parity status: pinned by tests/test_oracle_pins.py (no loss equals the plain
+Parity status: pinned by tests/test_oracle_resilience_pins.py (no loss equals the plain
 PCG bit for bit; the full-state global rollback equals the fault-free solve
 bit for bit and costs exactly the rolled-back iterations; the auxiliary
 problem against a dense direct solve of the assembled A(F,F); the FP32 backup
