@@ -60,11 +60,16 @@ NOMINAL_FP64_TFLOPS = 1.25   # GB300 FP64 rate: 152 SMs x 2 DFMA/clk x 2 flop x 
 # exactly (profiles/apply_fp64_q3_executed_flops.md).  Set an entry to None
 # when its kernel changes until it is counted again.
 EXEC_FP64_Q3 = {"k_trace": (1792.0, 0.0), "k_cell_lo": (3440.0, 64.0)}
+# The same counters as FP64 instructions (DFMA, DADD and DMUL one each: every
+# one takes an issue slot of the FP64 pipe, whatever its flops), per cell and
+# per interior face side, exact at both sizes
+EXEC_FP64_INSTR_Q3 = {"k_trace": (1136.0, 0.0), "k_cell_lo": (1984.0, 48.0)}
 
 
-def executed_fp64_per_dof(kernel: str, N: int, n: int):
-    """Executed FP64 operations per DOF of one launch on an N^3 mesh (Q3 only)."""
-    e = EXEC_FP64_Q3.get(kernel) if n == 4 else None
+def executed_fp64_per_dof(kernel: str, N: int, n: int, table=None):
+    """Executed FP64 operations (or, with table=EXEC_FP64_INSTR_Q3, FP64
+    instructions) per DOF of one launch on an N^3 mesh (Q3 only)."""
+    e = (table or EXEC_FP64_Q3).get(kernel) if n == 4 else None
     if e is None:
         return None
     per_cell, per_face_side = e
@@ -726,15 +731,20 @@ def run_geometry_probe(n_cells: int, applies: int = 4):
 # instruction counters, DFMA x2 + DADD + DMUL): k_cell_aff 11,056 per cell at
 # 32^3 and 40^3 alike, k_cell_ml 12,571 per cell at 32^3
 EXEC_FP64_GEOMETRY_Q3 = {"k_cell_aff": 11056 / 64, "k_cell_ml": 12571 / 64}
+# and as FP64 instructions (DFMA + DADD + DMUL) per DOF: 6,528 and 7,281 per cell
+EXEC_FP64_INSTR_GEOMETRY_Q3 = {"k_cell_aff": 6528 / 64, "k_cell_ml": 7281 / 64}
 
 
 def _geometry_roofline(kernel, n, nd, ms, peak_fp64):
     if n != 4 or not peak_fp64:
         return None
     achieved = EXEC_FP64_GEOMETRY_Q3[kernel] * nd / (ms * 1e-3) / 1e12
+    issue = EXEC_FP64_INSTR_GEOMETRY_Q3[kernel] * nd / (ms * 1e-3) / 1e12
     return {"kernel": kernel, "bound": "alu", "unit": "TFLOP/s", "achieved": achieved,
             "peak": peak_fp64, "frac": achieved / peak_fp64,
-            "executed_flops_per_dof": EXEC_FP64_GEOMETRY_Q3[kernel]}
+            "executed_flops_per_dof": EXEC_FP64_GEOMETRY_Q3[kernel],
+            "fp64_issue": {"fp64_instructions_per_dof": EXEC_FP64_INSTR_GEOMETRY_Q3[kernel],
+                           "achieved_tinst_s": issue, "frac": issue / (peak_fp64 / 2)}}
 
 
 def run_affine(world, K64, peak_fp64=None):
@@ -959,6 +969,17 @@ def roofline_entry(N, n, nd, napp, ms1, ms2, ms_step, peak_fp64):
         r.update({"achieved": alg_tflops, "peak": peak_fp64, "frac": alg_tflops / peak_fp64,
                   "achieved_source": "algorithmic flops (no executed-operation count for "
                                      "this kernel build)"})
+    # the FP64 pipe's issue rate: instructions per launch over the launch time,
+    # against the DFMA instruction rate of the probe (its flops / 2)
+    issue = {}
+    for name, t in (("k_trace", t1), ("k_cell_lo", t2)):
+        ipd = executed_fp64_per_dof(name, N, n, EXEC_FP64_INSTR_Q3)
+        if ipd is not None and t > 0:
+            rate = ipd * nd / (t * 1e-3) / 1e12
+            issue[name] = {"fp64_instructions_per_dof": ipd, "achieved_tinst_s": rate,
+                           "peak_tinst_s": peak_fp64 / 2, "frac": rate / (peak_fp64 / 2)}
+    if issue:
+        r["fp64_issue"] = issue
     if exec_other is not None:
         t_other = t1 if other == "k_trace" else t2
         r["other_kernel"] = {"kernel": other, "executed_flops_per_dof": exec_other,
