@@ -36,7 +36,10 @@ the gradient, CG against a direct solve, and the per-cell face coefficient and
 face weights in closed form for a log K quadratic inside the cells), and by
 tests/test_oracle_kron_pins.py (the Kronecker cell blocks against the
 assembled blocks of cell-wise constant fields and their volume coefficient in
-closed form).
+closed form), and by tests/test_oracle_collocation_pins.py (the scaled
+Gauss-point basis: orthogonality, single modes in closed form, the one-cell
+K = 1 operator and its diagonal as transformed closed-form Kronecker sums, and
+CG's invariance under the change of basis).
 """
 from __future__ import annotations
 
@@ -339,6 +342,41 @@ class SIPG:
                     f_bnd = np.zeros_like(f_bnd)
                 dg += gamma[:, None] * np.where(interior[:, None], f_int[None, :], f_bnd[None, :])
         return dg.reshape(-1) if full else dg
+
+    # -- scaled Gauss-point (collocation) basis ----------------------------------
+    # The per-cell map Q = W^{1/2} Phi, (Q x)_q = sqrt(w_q) u_h(xi_q), takes the
+    # Legendre coefficients of a cell to its Gauss-point values scaled by the
+    # square roots of the 3D Gauss weights.  The n-point Gauss rule integrates
+    # L_i L_j exactly (degree 2n - 2), so Phi^T W Phi = I and Q is orthogonal:
+    # the operator Q A Q^T has the spectrum of A, and CG on
+    # (Q A Q^T) (Q x) = Q b produces Q times the iterates of CG on A x = b
+    # (Section 2.4's PCG with M = I is invariant under orthogonal changes of
+    # basis).  Not a construction of the paper: a reformulation of its
+    # Section 4.1 operator in another orthonormal basis of the same space.
+    def collocation_matrix(self):
+        """Q of one cell, shape (n^3 points, n^3 modes)."""
+        return np.sqrt(self.wq)[:, None] * self.phi
+
+    def to_collocation(self, x):
+        """x_hat = Q x on every cell (Legendre coefficients -> scaled point values)."""
+        X = np.asarray(x, float).reshape(self.n_cells_total, self.n3)
+        return (X @ self.collocation_matrix().T).reshape(-1)
+
+    def from_collocation(self, xh):
+        """x = Q^T x_hat on every cell (the inverse map)."""
+        Xh = np.asarray(xh, float).reshape(self.n_cells_total, self.n3)
+        return (Xh @ self.collocation_matrix()).reshape(-1)
+
+    def collocation_apply(self, K, xh):
+        """(Q A Q^T) x_hat: the operator in the scaled Gauss-point basis."""
+        return self.to_collocation(self.apply(K, self.from_collocation(xh)))
+
+    def collocation_diagonal(self, K):
+        """diag(Q A Q^T) from the assembled diagonal cell blocks A_cc (small
+        meshes only): the Jacobi diagonal of the operator in that basis."""
+        Q = self.collocation_matrix()
+        blocks = cell_blocks(self.assemble(K), self.n3)
+        return np.einsum("qm,cmk,qk->cq", Q, blocks, Q).reshape(-1)
 
     # -- coefficient gradient ---------------------------------------------------
     def face_form_unit(self, u, v):
