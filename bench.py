@@ -59,11 +59,13 @@ NOMINAL_FP64_TFLOPS = 1.25   # GB300 FP64 rate: 152 SMs x 2 DFMA/clk x 2 flop x 
 # on 32^3 and 40^3 launches, which fit (per cell, per interior face side)
 # exactly (profiles/apply_fp64_q3_executed_flops.md).  Set an entry to None
 # when its kernel changes until it is counted again.
-EXEC_FP64_Q3 = {"k_trace": (1792.0, 0.0), "k_cell_lo": (3440.0, 64.0)}
+EXEC_FP64_Q3 = {"k_trace": (1792.0, 0.0), "k_cell_lo": (3440.0, 64.0),
+                "k_trace_nd": (1344.0, 0.0), "k_cell_nd": (3008.0, 64.0)}
 # The same counters as FP64 instructions (DFMA, DADD and DMUL one each: every
 # one takes an issue slot of the FP64 pipe, whatever its flops), per cell and
 # per interior face side, exact at both sizes
-EXEC_FP64_INSTR_Q3 = {"k_trace": (1136.0, 0.0), "k_cell_lo": (1984.0, 48.0)}
+EXEC_FP64_INSTR_Q3 = {"k_trace": (1136.0, 0.0), "k_cell_lo": (1984.0, 48.0),
+                      "k_trace_nd": (768.0, 0.0), "k_cell_nd": (1536.0, 48.0)}
 
 
 def executed_fp64_per_dof(kernel: str, N: int, n: int, table=None):
@@ -263,14 +265,16 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def time_applies(m, x, y, steps, warmup, world, per_step=APPLIES_PER_STEP):
+def time_applies(m, x, y, steps, warmup, world, per_step=APPLIES_PER_STEP, nodal=False):
     """`steps` timed sweeps of `per_step` FP64 applies after `warmup` untimed
     sweeps; CUDA events on the launching stream, per-pass events inside the
-    library (dg_timing_enable) for the roofline."""
+    library (dg_timing_enable) for the roofline.  nodal: the operator in the
+    scaled Gauss-point basis (dg_apply_nodal) instead of dg_apply."""
     import torch
+    op = m.apply_nodal if nodal else m.apply
     for _ in range(warmup):
         for _ in range(per_step):
-            m.apply(x, y)
+            op(x, y)
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
@@ -280,7 +284,7 @@ def time_applies(m, x, y, steps, warmup, world, per_step=APPLIES_PER_STEP):
     e0.record(s)
     for _ in range(steps):
         for _ in range(per_step):
-            m.apply(x, y)
+            op(x, y)
     e1.record(s)
     torch.cuda.synchronize()
     barrier(world)
@@ -365,10 +369,14 @@ def run_cg(world, modes=None):
                       ("mixed_ir_restart_jacobi",
                        dg.DG_CG_MIXED_IR_RESTART | dg.DG_CG_PRECOND_JACOBI),
                       ("mixed_ir_kron", dg.DG_CG_MIXED_IR | dg.DG_CG_PRECOND_KRON),
-                      ("fp64_kron", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_KRON))
+                      ("fp64_kron", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_KRON),
+                      ("fp64_nodal", dg.DG_CG_FP64 | dg.DG_CG_NODAL),
+                      ("fp64_nodal_jacobi",
+                       dg.DG_CG_FP64 | dg.DG_CG_NODAL | dg.DG_CG_PRECOND_JACOBI))
     for name, mode in modes:
-        if mode & (dg.DG_CG_PRECOND_JACOBI | dg.DG_CG_PRECOND_KRON):
-            m.set_coefficient(Kd)  # drops the cached preconditioner: the solve forms it
+        if mode & (dg.DG_CG_PRECOND_JACOBI | dg.DG_CG_PRECOND_KRON | dg.DG_CG_NODAL):
+            # drops the cached preconditioner and basis data: the solve forms them
+            m.set_coefficient(Kd)
         x = torch.zeros_like(b)
         torch.cuda.synchronize()
         barrier(world)
@@ -380,6 +388,8 @@ def run_cg(world, modes=None):
     if out["fp64_jacobi"]["status"] == 0 and out["mixed_ir_jacobi"]["status"] == 0:
         out["speedup_mixed_vs_fp64_jacobi"] = (out["fp64_jacobi"]["seconds"]
                                                / out["mixed_ir_jacobi"]["seconds"])
+    if out.get("fp64_nodal", {}).get("status") == 0 and out["fp64"]["status"] == 0:
+        out["speedup_fp64_nodal_vs_fp64"] = out["fp64"]["seconds"] / out["fp64_nodal"]["seconds"]
     if "mixed_ir_kron" in out and out["mixed_ir_kron"]["status"] == 0:
         out["speedup_mixed_kron_vs_fp64_jacobi"] = (out["fp64_jacobi"]["seconds"]
                                                     / out["mixed_ir_kron"]["seconds"])
@@ -687,6 +697,35 @@ def run_fp32_apply(m, xd, world, steps=8):
             "pass_ms": {"pass1": ms1 / max(napp, 1), "pass2": ms2 / max(napp, 1)}}
 
 
+def run_nodal_apply(m, xd, world, peak_fp64=None, steps=8):
+    """The operator of the benchmark workload in the scaled Gauss-point basis
+    (dg_apply_nodal, the apply inside DG_CG_NODAL solves), timed like `value`,
+    with per-pass times, executed FP64 rates from the ncu counts and its
+    one-time setup (the basis's line operators)."""
+    import torch
+    xh = m.to_nodal(xd)
+    yh = torch.empty_like(xh)
+    ms, napp, ms1, ms2 = time_applies(m, xh, yh, steps, 2, world, nodal=True)
+    ms = max_over_ranks(ms, world)
+    nd, n = m.n_dofs, m.n
+    t1, t2 = ms1 / max(napp, 1), ms2 / max(napp, 1)
+    out = {"workload": "the benchmark workload, x mapped to the scaled Gauss-point basis",
+           "apply_gdof_s": world * nd * steps * APPLIES_PER_STEP / (ms * 1e-3) / 1e9,
+           "pass_ms": {"k_trace_nd": t1, "k_cell_nd": t2}}
+    if peak_fp64:
+        for name, t in (("k_trace_nd", t1), ("k_cell_nd", t2)):
+            epd = executed_fp64_per_dof(name, WORKLOAD["n_cells"], n)
+            ipd = executed_fp64_per_dof(name, WORKLOAD["n_cells"], n, EXEC_FP64_INSTR_Q3)
+            if epd is not None and t > 0:
+                a = epd * nd / (t * 1e-3) / 1e12
+                rate = ipd * nd / (t * 1e-3) / 1e12
+                out.setdefault("roofline", {})[name] = {
+                    "executed_flops_per_dof": epd, "achieved_tflops": a, "peak": peak_fp64,
+                    "frac": a / peak_fp64, "fp64_instructions_per_dof": ipd,
+                    "issue_frac": rate / (peak_fp64 / 2)}
+    return out
+
+
 def perturbed_vertices(N, seed=7):
     """Vertices of the N^3 unit-cube mesh with every interior vertex moved by
     up to 0.2 h in each direction (uniform, seeded): a multilinear mesh."""
@@ -928,12 +967,40 @@ def run_cg_probe(iters: int, n_cells: int = 0):
                        ("mixed_ir_jacobi", dg.DG_CG_MIXED_IR | dg.DG_CG_PRECOND_JACOBI),
                        ("fp64_jacobi", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_JACOBI),
                        ("mixed_ir_kron", dg.DG_CG_MIXED_IR | dg.DG_CG_PRECOND_KRON),
-                       ("fp64_kron", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_KRON)):
+                       ("fp64_kron", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_KRON),
+                       ("fp64_nodal", dg.DG_CG_FP64 | dg.DG_CG_NODAL),
+                       ("fp64_nodal_jacobi",
+                        dg.DG_CG_FP64 | dg.DG_CG_NODAL | dg.DG_CG_PRECOND_JACOBI)):
         x = torch.zeros_like(b)
         _, st = m.cg_solve(b, x, rtol=1e-12, maxit=iters, mode=mode, raise_on_error=False)
         print(json.dumps({"mode": name, "iterations": st["iterations"],
                           "ms_per_iteration": 1e3 * st["seconds"] / max(st["iterations"], 1)}),
               flush=True)
+
+
+def run_nodal_probe(n_cells: int, applies: int = 4):
+    """The N^3 Q3 operator (lognormal K seed 2) applied `applies` times in the
+    scaled Gauss-point basis, then `applies` times in the Legendre basis; prints
+    the per-pass times of each.  For ncu captures of the nodal kernels."""
+    import torch
+    import paper_1911_01492_gb300 as dg
+    from paper_1911_01492_gb300 import inputs
+    N, k = n_cells, 3
+    m = dg.Mesh(N, k)
+    m.set_coefficient(torch.from_numpy(inputs.lognormal_coefficient(N, k, seed=2)).cuda())
+    x = torch.from_numpy(inputs.uniform_vector(N, k, 3)).cuda()
+    xh = m.to_nodal(x)
+    y = torch.empty_like(x)
+    for nodal in (True, False):
+        m.timing_enable(applies)
+        for _ in range(applies):
+            (m.apply_nodal if nodal else m.apply)(xh if nodal else x, y)
+        torch.cuda.synchronize()
+        napp, ms1, ms2 = m.timing_read()
+        print(json.dumps({"basis": "nodal" if nodal else "legendre", "n_cells": N,
+                          "pass1_ms": ms1 / max(napp, 1), "pass2_ms": ms2 / max(napp, 1)}),
+              flush=True)
+    m.close()
 
 
 def roofline_entry(N, n, nd, napp, ms1, ms2, ms_step, peak_fp64):
@@ -1027,6 +1094,9 @@ def main(argv=None):
     ap.add_argument("--geometry-probe", type=int, default=0, metavar="N",
                     help="only run a few applies on the affine and multilinear N^3 Q3 "
                          "meshes (for kernel profiles) and exit")
+    ap.add_argument("--nodal-probe", type=int, default=0, metavar="N",
+                    help="apply the N^3 Q3 operator in the scaled Gauss-point basis and in the "
+                         "Legendre basis 4 times each (for kernel profiles)")
     ap.add_argument("--batched-full", action="store_true",
                     help="with --batched: also solve the whole 256-sample batch (minutes)")
     ap.add_argument("--n-cells", type=int, default=WORKLOAD["n_cells"],
@@ -1046,6 +1116,9 @@ def main(argv=None):
         return
     if args.cg_probe:
         run_cg_probe(args.cg_probe, args.cg_probe_cells)
+        return
+    if args.nodal_probe:
+        run_nodal_probe(args.nodal_probe)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -1086,9 +1159,10 @@ def main(argv=None):
                "steps": e2e_steps}
         del xh, yh
 
-    fp32 = None
+    fp32 = nodal = None
     if not args.no_extra:
         fp32 = _leg(run_fp32_apply, m, xd, world)
+        nodal = _leg(run_nodal_apply, m, xd, world, peak_fp64)
     cg2 = cg = K48 = None
     if not args.no_cg:
         cg2 = _leg(run_config2_cg, m, world)
@@ -1137,7 +1211,7 @@ def main(argv=None):
                 "clocks": clk.summary(), "cpu_baseline": cpu, "cg": cg,
                 "config2_cg": cg2, "config1": cfg1, "config4": cfg4,
                 "batched_cg": batched, "mlmc": mlmc_r, "affine": affine, "resilience": resil,
-                "fp32_apply": fp32,
+                "fp32_apply": fp32, "nodal_apply": nodal,
                 "oracle_legs": legs,
                 "bench_wall_s": time.perf_counter() - t_start}
         print(json.dumps(line), flush=True)

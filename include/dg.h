@@ -50,6 +50,7 @@ enum { DG_CG_FP64 = 0, DG_CG_MIXED_IR = 1, DG_CG_MIXED_IR_RESTART = 2 };  /* dg_
 enum { DG_CG_PRECOND_JACOBI = 256 };  /* OR into a mode: PCG with M = diag(A) */
 enum { DG_CG_PRECOND_BLOCK = 512 };   /* OR into DG_CG_FP64: PCG with M = the cell blocks of A */
 enum { DG_CG_PRECOND_KRON = 1024 };   /* OR into DG_CG_FP64 or DG_CG_MIXED_IR: Kronecker cell blocks */
+enum { DG_CG_NODAL = 2048 };          /* OR into DG_CG_FP64: iterate in the scaled Gauss-point basis */
 /* Boundary conditions (dg_set_boundary): bit f set = boundary side f is Dirichlet,
  * sides in the order x-, x+, y-, y+, z-, z+; the other sides carry zero flux. */
 enum { DG_BC_DIRICHLET = 0x3F, DG_BC_FLOW_X = 0x03 };
@@ -209,6 +210,19 @@ int dg_coeff_grad(const dg_mesh* mesh, const double* u, const double* v, double*
  *   first such solve after dg_set_coefficient (any degree); BREAKDOWN if a 1D
  *   factor has a negative eigenvalue (a direction with only zero-flux faces,
  *   one cell across, has a singular factor, which is allowed).
+ * DG_CG_FP64 | DG_CG_NODAL (with or without DG_CG_PRECOND_JACOBI): the same
+ *   FP64 CG run on (Q A Q^T) x_hat = Q b in the scaled Gauss-point basis of
+ *   dg_to_nodal.  Q is orthogonal, so without a preconditioner the iterates
+ *   are Q times those of the Legendre-basis CG (in exact arithmetic); each
+ *   operator application skips the six 1D basis transforms per cell.  With
+ *   DG_CG_PRECOND_JACOBI the diagonal is that of Q A Q^T (a different
+ *   preconditioner from diag(A)).  b and x are mapped once into the basis and
+ *   x back once; the returned residual is recomputed in the Legendre basis,
+ *   and if the mapping's rounding left it above rtol, plain FP64 CG iterations
+ *   from x finish the solve (counted in iterations).  Formed on the first such
+ *   solve after dg_set_coefficient: the line operators of Q A Q^T (as many
+ *   values as dg_set_coefficient's, ~7.5 doubles per DOF at degree 3) and two
+ *   solve vectors.  Cube meshes only.
  * Stops when ||b - A x|| <= rtol ||b|| recomputed in FP64.  Blocking.
  * Returns NOT_CONVERGED at maxit (x holds the last iterate), BREAKDOWN on
  * <p, Ap> <= 0 or non-finite scalars, TIMEOUT if a bounded wait of the mixed
@@ -352,6 +366,24 @@ int dg_boundary_flux(const dg_mesh* mesh, const double* u, int side, double g, d
  * Benchmarks divide the executed operation rate of the operator kernels by it.
  * Blocks; allocates and frees 64 bytes.  Errors: INVALID_ARG, CUDA. */
 int dg_peak_probe(int kind, double* tflops, void* stream);
+
+/* The scaled Gauss-point (collocation) basis.  No counterpart in the paper: a
+ * change to another orthonormal basis of the Section 4.1 discrete space, in
+ * which the Section 3.3 sum-factorised operator needs no basis transforms.
+ * Per cell, x_hat = Q x with Q = W^{1/2} (B (x) B (x) B): x_hat(a,b,e) =
+ * sqrt(w_a w_b w_e) u_h(xi_a, xi_b, xi_e) at the n^3 Gauss points, point
+ * index a + n(b + n e) (a along x), the layout of the coefficients.  Q is
+ * orthogonal (the Gauss rule integrates L_i L_j exactly), so dg_to_modal
+ * (x = Q^T x_hat) is its inverse and both preserve inner products.  FP64
+ * device vectors of n_dofs values, caller-owned, not aliased; asynchronous on
+ * `stream`; INVALID_ARG on NULL, aliased vectors or an affine or multilinear
+ * mesh.  dg_apply_nodal: y_hat = (Q A(K) Q^T) x_hat in FP64 (two kernels:
+ * face traces by Lagrange end values, then per-line operators and neighbour
+ * face terms); its first call after dg_set_coefficient forms the line
+ * operators of Q A Q^T (allocated once per mesh). */
+int dg_to_nodal(const dg_mesh* mesh, const double* x, double* xhat, void* stream);
+int dg_to_modal(const dg_mesh* mesh, const double* xhat, double* x, void* stream);
+int dg_apply_nodal(const dg_mesh* mesh, const double* xhat, double* yhat, void* stream);
 
 /* y = A(K) x in FP64, for callers that cannot allocate device memory.  The
  * paper has no counterpart; this is a deployment variant of dg_apply (Section

@@ -29,6 +29,7 @@ DG_CG_MIXED_IR_RESTART = 2
 DG_CG_PRECOND_JACOBI = 256
 DG_CG_PRECOND_BLOCK = 512
 DG_CG_PRECOND_KRON = 1024
+DG_CG_NODAL = 2048
 DG_BC_DIRICHLET = 0x3F
 DG_BC_FLOW_X = 0x03
 DG_BACKUP_NONE = 0
@@ -75,6 +76,9 @@ _SIGS = {
                                                 ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                                 _VP, _VP]),
     "dg_apply_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP]),
+    "dg_to_nodal": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "dg_to_modal": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "dg_apply_nodal": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "dg_diagonal": (ctypes.c_int, [_VP, _VP, _VP]),
     "dg_load_vector": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "dg_set_boundary": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -265,6 +269,38 @@ class Mesh:
                "dg_apply_adjoint" if adjoint else "dg_apply")
         return y
 
+    # -- scaled Gauss-point (collocation) basis ------------------------------------
+    def to_nodal(self, x, xhat=None, stream=None):
+        """x_hat = Q x: per cell the values at the Gauss points scaled by
+        sqrt(w_a w_b w_e) (an orthogonal change of basis; float64)."""
+        import torch
+        if xhat is None:
+            xhat = torch.empty_like(x)
+        _check(library().dg_to_nodal(self._h, _ptr(x, _f64(), self.n_dofs, "x"),
+                                     _ptr(xhat, _f64(), self.n_dofs, "xhat"), _stream(stream)),
+               "dg_to_nodal")
+        return xhat
+
+    def to_modal(self, xhat, x=None, stream=None):
+        """x = Q^T x_hat, the inverse of to_nodal (float64)."""
+        import torch
+        if x is None:
+            x = torch.empty_like(xhat)
+        _check(library().dg_to_modal(self._h, _ptr(xhat, _f64(), self.n_dofs, "xhat"),
+                                     _ptr(x, _f64(), self.n_dofs, "x"), _stream(stream)),
+               "dg_to_modal")
+        return x
+
+    def apply_nodal(self, xhat, yhat=None, stream=None):
+        """y_hat = (Q A Q^T) x_hat, the operator in the scaled Gauss-point basis (float64)."""
+        import torch
+        if yhat is None:
+            yhat = torch.empty_like(xhat)
+        _check(library().dg_apply_nodal(self._h, _ptr(xhat, _f64(), self.n_dofs, "xhat"),
+                                        _ptr(yhat, _f64(), self.n_dofs, "yhat"),
+                                        _stream(stream)), "dg_apply_nodal")
+        return yhat
+
     def apply_adjoint(self, ybar, xbar=None, stream=None):
         return self.apply(ybar, xbar, stream, adjoint=True)
 
@@ -347,11 +383,13 @@ class Mesh:
     # -- solvers ---------------------------------------------------------------
     def cg_solve(self, b, x=None, rtol: float = 1e-10, maxit: int = 100000,
                  mode: int = DG_CG_FP64, stream=None, raise_on_error: bool = True,
-                 precond: str | None = None):
+                 precond: str | None = None, nodal: bool = False):
         """Solve A x = b (blocking).  precond: None, "jacobi" (PCG with
         M = diag(A); same as OR-ing DG_CG_PRECOND_JACOBI into mode), "block"
         (M = the inverted cell blocks of A; FP64 mode, degree <= 4) or "kron"
         (M = the Kronecker cell blocks, fast diagonalisation; FP64 or mixed).
+        nodal: iterate in the scaled Gauss-point basis (same as OR-ing
+        DG_CG_NODAL into mode; FP64 mode, M = I or Jacobi).
         Returns (x, stats dict)."""
         import torch
         if precond not in (None, "jacobi", "block", "kron"):
@@ -362,6 +400,8 @@ class Mesh:
             mode |= DG_CG_PRECOND_BLOCK
         elif precond == "kron":
             mode |= DG_CG_PRECOND_KRON
+        if nodal:
+            mode |= DG_CG_NODAL
         if x is None:
             x = torch.zeros_like(b)
         st = CGStats()

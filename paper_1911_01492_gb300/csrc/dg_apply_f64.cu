@@ -3,6 +3,8 @@
 
 int dg_launch_apply_f64(const dg_mesh* m, const double* x, double* y, const int* skip,
                         cudaStream_t s) {
+  // inside a solve in the scaled Gauss-point basis (DG_CG_NODAL): Q A Q^T
+  if (m != nullptr && m->nodal_op) return dg_launch_apply_nodal_f64(m, x, y, skip, s);
   if (m != nullptr && m->multilinear) return dg_launch_apply_multilinear(m, x, y, skip, s);
   if (m != nullptr && m->affine) return dg_launch_apply_affine(m, x, y, skip, s);
   cudaError_t e = dgk::dispatch_n<double, dgk::ApplyF>(m->n, m, x, y, m->U64, m->X64, m->TR64,

@@ -840,10 +840,15 @@ k_cell_lo(const T* __restrict__ U, const T* __restrict__ Xm, const T* __restrict
 // plus the own-side part of the flux at the line's two face points, so that
 // pass 2 only adds the neighbour part of interior faces (FaceNbr).
 // Stored as lineop[((c*3 + dir)*n^2 + line)*n(n+1)/2 + packed(i, j)].
-template <int N>
+// NODAL: the line operators of Q A Q^T in the scaled Gauss-point basis
+// (dg_nodal.cu): x-lines in the collocation form like y and z, every entry
+// (i, j) of the line (s, t) multiplied by isw_i isw_j / (w_s w_t), which
+// removes the tangential weights of Kt and of the face weight.
+template <int N, bool NODAL = false>
 __global__ void k_line_ops(const double* __restrict__ kt, const double* __restrict__ gh,
                            double* __restrict__ lineop, long long ncells, int Nc,
-                           const __grid_constant__ DGTab<double> tab) {
+                           const __grid_constant__ DGTab<double> tab,
+                           const __grid_constant__ DGTabN<double> tn) {
   constexpr int N2 = N * N, N3 = N * N * N, NP = N * (N + 1) / 2;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ncells * 3 * N2) return;
@@ -866,7 +871,8 @@ __global__ void k_line_ops(const double* __restrict__ kt, const double* __restri
 #pragma unroll
   for (int i = 0; i < N; ++i) {
 #pragma unroll
-    for (int f = 0; f < N; ++f) gk[i][f] = (dir == 0 ? tab.Bd[f][i] : tab.D[f][i]) * k[f];
+    for (int f = 0; f < N; ++f)
+      gk[i][f] = (dir == 0 && !NODAL ? tab.Bd[f][i] : tab.D[f][i]) * k[f];
   }
   // Own-side face terms of the line's two faces (both trial and test function
   // on this cell's side).  At the face point of this line, with v the test
@@ -885,10 +891,11 @@ __global__ void k_line_ops(const double* __restrict__ kt, const double* __restri
   double v0[N], d0[N], v1[N], d1[N], P0[N], Q0[N], P1[N], Q1[N];
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    v0[j] = dir == 0 ? tab.a0[j] : tab.l0[j];
-    d0[j] = dir == 0 ? tab.d0[j] : tab.dl0[j];
-    v1[j] = dir == 0 ? tab.a1[j] : tab.l1[j];
-    d1[j] = dir == 0 ? tab.d1[j] : tab.dl1[j];
+    const bool modal = dir == 0 && !NODAL;
+    v0[j] = modal ? tab.a0[j] : tab.l0[j];
+    d0[j] = modal ? tab.d0[j] : tab.dl0[j];
+    v1[j] = modal ? tab.a1[j] : tab.l1[j];
+    d1[j] = modal ? tab.d1[j] : tab.dl1[j];
     P0[j] = fma(whl * S2, v0[j], cl * d0[j]);
     Q0[j] = cl * v0[j];
     P1[j] = fma(whu * S2, v1[j], -cu * d1[j]);
@@ -901,11 +908,12 @@ __global__ void k_line_ops(const double* __restrict__ kt, const double* __restri
       double acc = 0.0;
 #pragma unroll
       for (int f = 0; f < N; ++f)
-        acc = fma(gk[i][f], dir == 0 ? tab.Bd[f][j] : tab.D[f][j], acc);
+        acc = fma(gk[i][f], dir == 0 && !NODAL ? tab.Bd[f][j] : tab.D[f][j], acc);
       acc = fma(v0[i], P0[j], acc);
       acc = fma(d0[i], Q0[j], acc);
       acc = fma(v1[i], P1[j], acc);
       acc = fma(d1[i], Q1[j], acc);
+      if (NODAL) acc *= (tn.isw[i] * tn.isw[j]) / w2;
       M[packed<N>(i, j)] = acc;
     }
   }
@@ -1060,7 +1068,7 @@ struct LineOpsF {
                          int Nc, const DGTab<double>* tab, cudaStream_t s) {
     const long long threads = ncells * 3 * N * N;
     k_line_ops<N><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(kt, gh, lineop, ncells, Nc,
-                                                                    *tab);
+                                                                    *tab, DGTabN<double>{});
     return cudaGetLastError();
   }
 };

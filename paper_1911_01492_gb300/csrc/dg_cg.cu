@@ -741,7 +741,7 @@ int zero_solution(dg_mesh* m, double* x, dg_cg_stats* st, cudaStream_t s) {
 
 int cg_fp64(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_cg_stats* st,
             bool jacobi, cudaStream_t s, bool block = false, bool kron = false) {
-  const double* dinv = jacobi ? m->dinv64 : nullptr;
+  const double* dinv = jacobi ? (m->nodal_op ? m->dinvN64 : m->dinv64) : nullptr;
   const int max_restarts = 5;
   int iters = 0, restarts = 0;
   double res2 = 0, b2 = 0;
@@ -1225,6 +1225,67 @@ int cg_fp64_resilient(dg_mesh* m, const double* b, double* x, double rtol, int m
   return rc;
 }
 
+// Marks a solve in the scaled Gauss-point basis: while it lives, the internal
+// FP64 apply launcher applies Q A Q^T and the Jacobi diagonal is diag(Q A Q^T).
+struct NodalScope {
+  dg_mesh* m;
+  explicit NodalScope(dg_mesh* mm) : m(mm) { m->nodal_op = true; }
+  ~NodalScope() { m->nodal_op = false; }
+};
+
+// CG in the scaled Gauss-point basis (DG_CG_NODAL): b_hat = Q b, x_hat = Q x,
+// the FP64 CG of cg_fp64 on Q A Q^T, x = Q^T x_hat, then the residual in the
+// Legendre basis.  The solve's own stopping test is on ||b_hat - Q A Q^T
+// x_hat|| = ||b - A x|| (Q orthogonal); the mapping back rounds x, so if the
+// Legendre-basis residual is still above rtol, FP64 CG iterations (M = I)
+// continue from x.
+int cg_nodal(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_cg_stats* st,
+             bool jacobi, cudaStream_t s) {
+  int rc = jacobi ? dg_ensure_nodal_diag(m, s) : dg_ensure_nodal(m, s);
+  if (rc) return rc;
+  rc = dg_launch_collocation(m, b, m->bN64, true, s);
+  if (rc == DG_OK) rc = dg_launch_collocation(m, x, m->xN64, true, s);
+  if (rc) return rc;
+  dg_cg_stats sn{};
+  {
+    NodalScope scope(m);
+    rc = cg_fp64(m, m->bN64, m->xN64, rtol, maxit, &sn, jacobi, s);
+  }
+  // x holds the last iterate also when the solve stopped early
+  int rc2 = dg_launch_collocation(m, m->xN64, x, false, s);
+  if (rc2) return rc2;
+  if (rc != DG_OK && rc != DG_ERR_NOT_CONVERGED) return rc;
+  double res2 = 0.0, b2 = 0.0;
+  rc2 = true_residual(m, b, x, s, &res2, &b2);
+  if (rc2) return rc2;
+  const double rel = b2 > 0.0 ? std::sqrt(res2 / b2) : 0.0;
+  if (st) {
+    *st = sn;
+    st->rel_residual = rel;
+  }
+  if (rc != DG_OK || rel <= rtol) {
+    if (rc != DG_OK)  // the message of cg_fp64, with the Legendre-basis residual
+      return dg_fail(DG_ERR_NOT_CONVERGED,
+                     "dg_cg_solve(nodal): relative residual %.3e > rtol %.3e after %d "
+                     "iterations", rel, rtol, sn.iterations);
+    return DG_OK;
+  }
+  dg_cg_stats sp{};
+  const int left = maxit - sn.iterations;
+  if (left < 1)
+    return dg_fail(DG_ERR_NOT_CONVERGED,
+                   "dg_cg_solve(nodal): relative residual %.3e > rtol %.3e after %d iterations",
+                   rel, rtol, sn.iterations);
+  rc = cg_fp64(m, b, x, rtol, left, &sp, false, s);
+  if (st) {
+    st->iterations = sn.iterations + sp.iterations;
+    st->outer_iterations = sn.outer_iterations + 1 + sp.outer_iterations;
+    st->rel_residual = sp.rel_residual;
+    st->rel_residual_rec = sp.rel_residual_rec;
+  }
+  return rc;
+}
+
 }  // namespace
 
 extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double rtol, int maxit,
@@ -1239,9 +1300,15 @@ extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double
   const bool jacobi = (mode & DG_CG_PRECOND_JACOBI) != 0;
   const bool block = (mode & DG_CG_PRECOND_BLOCK) != 0;
   const bool kron = (mode & DG_CG_PRECOND_KRON) != 0;
-  const int base = mode & ~(DG_CG_PRECOND_JACOBI | DG_CG_PRECOND_BLOCK | DG_CG_PRECOND_KRON);
+  const bool nodal = (mode & DG_CG_NODAL) != 0;
+  const int base = mode & ~(DG_CG_PRECOND_JACOBI | DG_CG_PRECOND_BLOCK | DG_CG_PRECOND_KRON |
+                            DG_CG_NODAL);
   if (base != DG_CG_FP64 && base != DG_CG_MIXED_IR && base != DG_CG_MIXED_IR_RESTART)
     return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: unknown mode %d", mode);
+  if (nodal && (block || kron || base != DG_CG_FP64))
+    return dg_fail(DG_ERR_INVALID_ARG,
+                   "dg_cg_solve: DG_CG_NODAL goes with DG_CG_FP64, with or without "
+                   "DG_CG_PRECOND_JACOBI");
   if (block && (jacobi || kron || base != DG_CG_FP64))
     return dg_fail(DG_ERR_INVALID_ARG,
                    "dg_cg_solve: DG_CG_PRECOND_BLOCK goes with DG_CG_FP64 only");
@@ -1262,11 +1329,13 @@ extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double
   DG_CUDA(cudaStreamWaitEvent(m->solve_stream, m->ev, 0));
   if (st) *st = dg_cg_stats{};
   cudaStream_t s = m->solve_stream;
-  if (jacobi) rc = dg_ensure_diagonal(m, s);
+  if (jacobi && !nodal) rc = dg_ensure_diagonal(m, s);
   if (block) rc = dg_ensure_block(m, s);
   if (kron) rc = dg_ensure_kron(m, s);
   if (rc == DG_OK) {
-    if (base == DG_CG_FP64)
+    if (nodal)
+      rc = cg_nodal(m, b, x, rtol, maxit, st, jacobi, s);
+    else if (base == DG_CG_FP64)
       rc = cg_fp64(m, b, x, rtol, maxit, st, jacobi, s, block, kron);
     else if (base == DG_CG_MIXED_IR)
       rc = cg_mixed(m, b, x, rtol, maxit, st, jacobi, s, kron);

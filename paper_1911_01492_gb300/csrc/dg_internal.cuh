@@ -26,6 +26,19 @@ struct DGTab {
   T sigma;                        // penalty factor 2(k+1)^2 (dimensionless)
 };
 
+// 1D data of the scaled Gauss-point basis (dg_nodal.cu): a cell's values
+// u_hat(a,b,e) = sqrt(w_a w_b w_e) u_h(xi_a, xi_b, xi_e).  Face traces of u_h
+// and the test functions' face values in that basis carry 1 / sqrt(w) per
+// point along the line; the tangential factors cancel against the face weight.
+template <typename T>
+struct DGTabN {
+  T sw[DG_MAXN];                  // sqrt(w_a)
+  T isw[DG_MAXN];                 // 1 / sqrt(w_a)
+  T l0[DG_MAXN], l1[DG_MAXN];     // l_a(0) / sqrt(w_a), l_a(1) / sqrt(w_a)
+  T hdl0[DG_MAXN], hdl1[DG_MAXN]; // l_a'(0) / (2 sqrt(w_a)), l_a'(1) / (2 sqrt(w_a))
+  T Dh[DG_MAXN][DG_MAXN];         // sqrt(w_f) D[f][i] / sqrt(w_i)
+};
+
 // Host-side construction of the FP64 tables (dg_tables.cpp) and rounding to FP32.
 void dg_build_tables(int n, double sigma, DGTab<double>* t64, DGTab<float>* t32);
 // the n Gauss-Legendre points and weights on [0,1] of those tables
@@ -109,6 +122,18 @@ struct dg_mesh {
   double* kron64;
   float* kron32;
   bool has_kron;
+  // scaled Gauss-point basis (DG_CG_NODAL, dg_nodal.cu): its 1D tables, the
+  // line operators and Jacobi diagonal of Q A Q^T (formed on first use after
+  // the coefficient is set) and the solve's b and x in that basis
+  DGTabN<double> tabN64;
+  DGTabN<float> tabN32;
+  bool has_nodal, has_nodal_diag;
+  bool nodal_op;      // set while a solve runs in that basis: the internal
+                      // FP64 apply launcher then applies Q A Q^T
+  double* lineopN64;  // [c][3][n^2][n(n+1)/2]
+  double* dinvN64;
+  float* dinvN32;
+  double *bN64, *xN64;
   double* kbar;     // Kbar_c                          [c]
   int* dflag;       // device-side error flag of the setup kernels
 
@@ -205,6 +230,17 @@ int dg_prepare_mixed32(dg_mesh* m);
 int dg_prepare_apply_f64(int n);
 int dg_prepare_apply_f32(int n);
 int dg_prepare_grad(int n);
+
+// scaled Gauss-point basis (dg_nodal.cu): tables (at mesh creation), the
+// line operators of Q A Q^T and solve vectors (formed if needed), its Jacobi
+// diagonal, the FP64 apply of Q A Q^T, and x_hat = Q x / x = Q^T x_hat
+void dg_build_nodal_tables(const DGTab<double>& t, int n, DGTabN<double>* d, DGTabN<float>* f);
+int dg_ensure_nodal(dg_mesh* m, cudaStream_t s);
+int dg_ensure_nodal_diag(dg_mesh* m, cudaStream_t s);
+int dg_launch_apply_nodal_f64(const dg_mesh* m, const double* x, double* y, const int* skip,
+                              cudaStream_t s);
+int dg_launch_collocation(const dg_mesh* m, const double* in, double* out, bool to_nodal,
+                          cudaStream_t s);
 
 // 1 / diag(A) for the Jacobi preconditioner (dg_precond.cu); forms it if needed
 int dg_ensure_diagonal(dg_mesh* m, cudaStream_t s);

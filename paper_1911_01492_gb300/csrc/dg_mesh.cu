@@ -102,7 +102,7 @@ static cudaError_t dmalloc(P** p, size_t count) {
 }
 
 static void free_all(dg_mesh* m) {
-  void* ptrs[] = {m->kt64, m->kt32, m->gh64, m->gh32, m->dgam, m->kbar, m->dflag, m->fw64, m->fw32, m->lineop64, m->diag64, m->dinv64, m->dinv32, m->binv64, m->kron64, m->kron32, m->geo_vol, m->geo_det, m->geo_face, m->geo_pen,
+  void* ptrs[] = {m->kt64, m->kt32, m->gh64, m->gh32, m->dgam, m->kbar, m->dflag, m->fw64, m->fw32, m->lineop64, m->diag64, m->dinv64, m->dinv32, m->binv64, m->kron64, m->kron32, m->lineopN64, m->dinvN64, m->dinvN32, m->bN64, m->xN64, m->geo_vol, m->geo_det, m->geo_face, m->geo_pen,
                   m->U64,  m->X64,  m->TR64, m->U32,  m->X32,  m->TR32, m->U64b,
                   m->X64b, m->TR64b, m->hx_dev, m->hy_dev, m->r64, m->p64, m->q64,
                   m->t64,  m->s64, m->d32,  m->r32, m->p32, m->q32, m->partials, m->state,
@@ -149,6 +149,7 @@ extern "C" int dg_create_mesh(int n_cells, int degree, dg_mesh** out) {
     m->geomKappa[i] = 1.0;
   }
   dg_build_tables(m->n, m->sigma, &m->tab64, &m->tab32);
+  dg_build_nodal_tables(m->tab64, m->n, &m->tabN64, &m->tabN32);
   cudaError_t e = cudaGetDevice(&m->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, m->device);
   const size_t nd = (size_t)m->ndofs, nc = (size_t)m->ncells, ntr = (size_t)(12 * n2) * nc;
@@ -221,6 +222,8 @@ extern "C" int dg_set_boundary(dg_mesh* m, int dirichlet_mask) {
   m->has_diag = false;
   m->has_block = false;
   m->has_kron = false;
+  m->has_nodal = false;
+  m->has_nodal_diag = false;
   return DG_OK;
 }
 
@@ -276,6 +279,8 @@ extern "C" int dg_set_coefficient(dg_mesh* m, const double* K, void* stream) {
   m->has_diag = false;
   m->has_block = false;
   m->has_kron = false;
+  m->has_nodal = false;
+  m->has_nodal_diag = false;
   DG_CUDA(cudaMemsetAsync(m->dflag, 0, sizeof(int), s));
   {
     const long long threads = m->ncells * 32;

@@ -1,0 +1,468 @@
+// The operator in the scaled Gauss-point (collocation) basis, for CG.
+//
+// Per cell, Q = W^{1/2} (B (x) B (x) B) maps the Legendre coefficients x to the
+// values of u_h at the n^3 Gauss points scaled by sqrt(w_a w_b w_e).  The
+// n-point Gauss rule integrates L_i L_j exactly, so B^T diag(w) B = I and Q is
+// orthogonal.  The operator of the Section 4.1 form is A = T^T A_pt T, with T
+// the modal-to-point map and A_pt acting on point values (collocation
+// derivatives, the coefficient at the points, face traces by Lagrange end
+// values); hence Q A Q^T = W^{-1/2} A_pt W^{-1/2}.  CG (Section 2.4, M = I) on
+// (Q A Q^T) x_hat = Q b produces exactly Q times the iterates of CG on
+// A x = b, since Q preserves every inner product.
+//
+// Why: in the Legendre basis every application of A spends its FP64
+// instructions on six 1D basis transforms per cell (three forward, three
+// back), about a quarter of the FP64 work at Q3.  In the scaled point basis
+// those transforms vanish: pass 1 only forms face traces (Lagrange end values
+// of each line), pass 2 only applies the per-line operators (the volume term
+// and the own-side face terms) and the neighbours' face terms.  A solve maps b
+// and x into the basis once and x back once.
+//
+// In that basis the scaling is folded into the data: the line operators of
+// Q A Q^T are those of A_pt times isw_i isw_j / (w_s w_t) (k_line_ops<N,
+// true>); the Lagrange end values carry isw_a = 1/sqrt(w_a); the face weight
+// h gamma w_s w_t / 2 of a face point loses its tangential weights against
+// the two isw factors of the traces, so every point of a face has the weight
+// h gamma / 2 and no per-point face-weight array is read.
+#include "dg_apply_impl.cuh"
+
+namespace dgk {
+
+// ---------------------------------------------------------------------------
+// x_hat = Q x (TO_NODAL) or x = Q^T x_hat, per cell by three 1D contractions
+// (the parity-split B and B^T of the operator kernels) and the point scaling.
+// One thread per line of each of the block's CPB cells, lines exchanged
+// through shared memory.
+// ---------------------------------------------------------------------------
+template <int N, bool TO_NODAL>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+k_collocation(const double* __restrict__ in, double* __restrict__ out, long long ncells,
+              const __grid_constant__ DGTab<double> tab,
+              const __grid_constant__ DGTabN<double> tn) {
+  constexpr int C = Cfg<N>::CPB, N2 = N * N, N3 = N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* s = reinterpret_cast<double*>(smem_raw);
+  const long long c0 = (long long)blockIdx.x * C;
+  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
+  const int lc = threadIdx.x / N2;
+  const int t2 = threadIdx.x - lc * N2;
+  const int p = t2 % N, q = t2 / N;
+  const bool active = lc < nblk;
+  const long long c = c0 + lc;
+  double* sc = s + lc * N3;
+  const double* src = in + c * N3;
+  double* dst = out + c * N3;
+  if (TO_NODAL) {
+    if (active) {  // z-lines (i = p, j = q): modes along z -> points
+      double v[N], u[N];
+#pragma unroll
+      for (int l = 0; l < N; ++l) v[l] = src[l * N2 + q * N + p];
+      b_fwd<N>(tab, v, u);
+#pragma unroll
+      for (int e = 0; e < N; ++e) sc[e * N2 + q * N + p] = u[e];
+    }
+    __syncthreads();
+    if (active) {  // y-lines (i = p, e = q)
+      double v[N], u[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = sc[q * N2 + j * N + p];
+      b_fwd<N>(tab, v, u);
+#pragma unroll
+      for (int b = 0; b < N; ++b) sc[q * N2 + b * N + p] = u[b];
+    }
+    __syncthreads();
+    if (active) {  // x-lines (b = p, e = q), then the scaling sqrt(w_a w_b w_e)
+      double v[N], u[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) v[i] = sc[q * N2 + p * N + i];
+      b_fwd<N>(tab, v, u);
+      const double f = tn.sw[p] * tn.sw[q];
+#pragma unroll
+      for (int a = 0; a < N; ++a) dst[q * N2 + p * N + a] = u[a] * (tn.sw[a] * f);
+    }
+  } else {
+    if (active) {  // x-lines (b = p, e = q): the scaling, then B^T along x
+      double v[N], R[N];
+      const double f = tn.sw[p] * tn.sw[q];
+#pragma unroll
+      for (int a = 0; a < N; ++a) v[a] = src[q * N2 + p * N + a] * (tn.sw[a] * f);
+      b_bwd<N>(tab, v, R);
+#pragma unroll
+      for (int i = 0; i < N; ++i) sc[q * N2 + p * N + i] = R[i];
+    }
+    __syncthreads();
+    if (active) {  // y-lines (i = p, e = q)
+      double v[N], R[N];
+#pragma unroll
+      for (int b = 0; b < N; ++b) v[b] = sc[q * N2 + b * N + p];
+      b_bwd<N>(tab, v, R);
+#pragma unroll
+      for (int j = 0; j < N; ++j) sc[q * N2 + j * N + p] = R[j];
+    }
+    __syncthreads();
+    if (active) {  // z-lines (i = p, j = q): points along z -> modes
+      double v[N], R[N];
+#pragma unroll
+      for (int e = 0; e < N; ++e) v[e] = sc[e * N2 + q * N + p];
+      b_bwd<N>(tab, v, R);
+#pragma unroll
+      for (int l = 0; l < N; ++l) dst[l * N2 + q * N + p] = R[l];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1 in the point basis: the value and half the reference normal
+// derivative of u_h on the six faces, TR[c][2f + {0, 1}][n^2] (the layout of
+// the Legendre-basis pass), from each line's scaled point values with the
+// scaled Lagrange end values.  The stored traces lack the tangential factor
+// isw_s isw_t, which the face weight absorbs in pass 2; the factor 1/2 is the
+// average's (pass 2 then multiplies by h gamma instead of h gamma / 2).
+// ---------------------------------------------------------------------------
+template <int N, typename T>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+k_trace_nd(const T* __restrict__ x, T* __restrict__ TR, long long ncells, const int* skip,
+           const __grid_constant__ DGTabN<T> tn) {
+  constexpr int C = Cfg<N>::CPB, N2 = N * N, N3 = N * N * N;
+  if (skip != nullptr && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  const long long c0 = (long long)blockIdx.x * C;
+  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
+  {
+    const T* xb = x + c0 * N3;
+    for (int t = threadIdx.x; t < nblk * N3; t += blockDim.x) s[t] = xb[t];
+  }
+  __syncthreads();
+  const int lc = threadIdx.x / N2;
+  if (lc >= nblk) return;
+  const int t2 = threadIdx.x - lc * N2;
+  const int p = t2 % N, q = t2 / N, pt = t2;
+  const T* sc = s + lc * N3;
+  T* tr = TR + (c0 + lc) * (12 * N2);
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir) {
+    // x-line (b = p, e = q), y-line (a = p, e = q), z-line (a = p, b = q)
+    const int base = dir == 0 ? q * N2 + p * N : dir == 1 ? q * N2 + p : q * N + p;
+    const int step = dir == 0 ? 1 : dir == 1 ? N : N2;
+    T u[N];
+#pragma unroll
+    for (int e = 0; e < N; ++e) u[e] = sc[base + e * step];
+    T vm = tn.l0[0] * u[0], vp = tn.l1[0] * u[0];
+    T gm = tn.hdl0[0] * u[0], gp = tn.hdl1[0] * u[0];
+#pragma unroll
+    for (int e = 1; e < N; ++e) {
+      vm = fma(tn.l0[e], u[e], vm);
+      vp = fma(tn.l1[e], u[e], vp);
+      gm = fma(tn.hdl0[e], u[e], gm);
+      gp = fma(tn.hdl1[e], u[e], gp);
+    }
+    tr[(4 * dir + 0) * N2 + pt] = vm;  // lower face: value, derivative / 2
+    tr[(4 * dir + 1) * N2 + pt] = gm;
+    tr[(4 * dir + 2) * N2 + pt] = vp;  // upper face
+    tr[(4 * dir + 3) * N2 + pt] = gp;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2 in the point basis (FP64): per line r = M u with the precomputed
+// symmetric line operator of Q A Q^T (volume term and own-side face terms),
+// plus the neighbour part of the line's two interior faces, summed over the
+// z-, y- and x-lines through every point.  The z-line threads read their lines
+// from global memory and publish them in shared memory for the other two
+// directions; the partial sums stay in shared memory; the x-line threads
+// write y.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+k_cell_nd(const double* __restrict__ x, const double* __restrict__ TR,
+          const double* __restrict__ lineop, const double* __restrict__ gh,
+          double* __restrict__ y, long long ncells, int Nc, const int* skip,
+          const __grid_constant__ DGTabN<double> tn) {
+  constexpr int C = Cfg<N>::CPB, N2 = N * N, N3 = N * N * N, NP = N * (N + 1) / 2;
+  constexpr double S2 = 4.0 * N * N;  // 2 sigma, sigma = 2 (k+1)^2
+  if (skip != nullptr && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* su = reinterpret_cast<double*>(smem_raw);
+  double* sr = su + C * N3;
+  __shared__ int sbase[3];
+  const long long c0 = (long long)blockIdx.x * C;
+  const int nblk = (int)((ncells - c0) < C ? (ncells - c0) : C);
+  const int lc = threadIdx.x / N2;
+  const int t2 = threadIdx.x - lc * N2;
+  const int p = t2 % N, q = t2 / N, pt = t2;
+  const bool active = lc < nblk;
+  const long long c = c0 + lc;
+  const int o = lc * N3;
+  if (threadIdx.x == 0) {
+    const unsigned cu = (unsigned)c0, n = (unsigned)Nc;
+    sbase[0] = (int)(cu % n);
+    sbase[1] = (int)((cu / n) % n);
+    sbase[2] = (int)(cu / n / n);
+  }
+  // z-lines (a = p, b = q) from global memory
+  double u[N];
+  if (active) {
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+      u[e] = x[c * N3 + e * N2 + q * N + p];
+      su[o + e * N2 + q * N + p] = u[e];
+    }
+  }
+  __syncthreads();
+  int crd[3] = {sbase[0] + lc, sbase[1], sbase[2]};
+  while (crd[0] >= Nc) {
+    crd[0] -= Nc;
+    if (++crd[1] == Nc) {
+      crd[1] = 0;
+      ++crd[2];
+    }
+  }
+  const long long stride[3] = {1, Nc, (long long)Nc * Nc};
+  // r = r0 + M u + the neighbour terms of the line's faces 2 dir (lower) and
+  // 2 dir + 1 (upper); r0: the partial sums of the directions already done
+  // (none for the first).  The neighbour's trace (un, gn/2) comes with the
+  // derivative halved (pass 1), and g = h gamma is the face weight h gamma / 2
+  // times 2, so with l, dl the scaled end values:
+  //   upper face (this cell the (-) side):
+  //     r += -l1 g (sigma un + gn/2) + (dl1/2) g un,
+  //   lower face (this cell the (+) side):
+  //     r += l0 g (gn/2 - sigma un) - (dl0/2) g un.
+  auto line = [&](int dir, const double* r0, double (&r)[N]) {
+    const double* Mp = lineop + ((c * 3 + dir) * N2 + pt) * NP;
+    double Mv[NP];
+#pragma unroll
+    for (int t = 0; t < NP; ++t) Mv[t] = Mp[t];
+    double cv1 = 0.0, cd1 = 0.0, cv0 = 0.0, cd0 = 0.0;
+    if (crd[dir] < Nc - 1) {  // upper face: this cell is the (-) side
+      double un, gn;
+      load_trace<N>(TR, c + stride[dir], 2 * dir, pt, un, gn);
+      const double g = gh[c * 6 + 2 * dir + 1];
+      cv1 = g * fma(0.5 * S2, un, gn);  // enters with -l1
+      cd1 = g * un;                     // enters with +dl1 / 2
+    }
+    if (crd[dir] > 0) {  // lower face: this cell is the (+) side
+      double un, gn;
+      load_trace<N>(TR, c - stride[dir], 2 * dir + 1, pt, un, gn);
+      const double g = gh[c * 6 + 2 * dir];
+      cv0 = g * fma(-0.5 * S2, un, gn);  // enters with +l0
+      cd0 = g * un;                      // enters with -dl0 / 2
+    }
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+      double acc = r0 != nullptr ? fma(-tn.l1[e], cv1, r0[e]) : -tn.l1[e] * cv1;
+      acc = fma(tn.hdl1[e], cd1, acc);
+      acc = fma(tn.l0[e], cv0, acc);
+      acc = fma(-tn.hdl0[e], cd0, acc);
+#pragma unroll
+      for (int f = 0; f < N; ++f) acc = fma(Mv[packed<N>(e, f)], u[f], acc);
+      r[e] = acc;
+    }
+  };
+  if (active) {  // z-lines
+    double r[N];
+    line(2, nullptr, r);
+#pragma unroll
+    for (int e = 0; e < N; ++e) sr[o + e * N2 + q * N + p] = r[e];
+  }
+  __syncthreads();
+  if (active) {  // y-lines (a = p, e = q), continuing the z-lines' sums
+    double r0[N], r[N];
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+      u[b] = su[o + q * N2 + b * N + p];
+      r0[b] = sr[o + q * N2 + b * N + p];
+    }
+    line(1, r0, r);
+#pragma unroll
+    for (int b = 0; b < N; ++b) sr[o + q * N2 + b * N + p] = r[b];
+  }
+  __syncthreads();
+  if (active) {  // x-lines (b = p, e = q): the sum of all three directions
+    double r0[N], r[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      u[a] = su[o + q * N2 + p * N + a];
+      r0[a] = sr[o + q * N2 + p * N + a];
+    }
+    line(0, r0, r);
+#pragma unroll
+    for (int a = 0; a < N; ++a) y[c * N3 + q * N2 + p * N + a] = r[a];
+  }
+}
+
+// 1 / diag(Q A Q^T): at point (a, b, e) the sum of the diagonal entries of the
+// x-, y- and z-line operators through it (the neighbour terms couple other
+// cells only).  One thread per DOF.
+template <int N>
+__global__ void k_diag_nd(const double* __restrict__ lineop, double* __restrict__ dinv64,
+                          float* __restrict__ dinv32, long long ndofs) {
+  constexpr int N2 = N * N, N3 = N * N * N, NP = N * (N + 1) / 2;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ndofs) return;
+  const long long c = t / N3;
+  const int qi = (int)(t - c * N3);
+  const int a = qi % N, b = (qi / N) % N, e = qi / N2;
+  const double* L = lineop + c * 3 * N2 * NP;
+  const double d = L[(0 * N2 + b + N * e) * NP + packed<N>(a, a)] +
+                   L[(1 * N2 + a + N * e) * NP + packed<N>(b, b)] +
+                   L[(2 * N2 + a + N * b) * NP + packed<N>(e, e)];
+  const double di = 1.0 / d;
+  dinv64[t] = di;
+  dinv32[t] = (float)di;
+}
+
+template <int N>
+struct NodalF {
+  template <typename T>
+  static cudaError_t apply(const dg_mesh* m, const double* x, double* y, const int* skip,
+                           cudaStream_t s) {
+    const unsigned blocks = (unsigned)((m->ncells + Cfg<N>::CPB - 1) / Cfg<N>::CPB);
+    const size_t s1 = sizeof(double) * Cfg<N>::CPB * N * N * N;
+    dg_timing_mark(m, 0, s);
+    k_trace_nd<N, double><<<blocks, Cfg<N>::THREADS, s1, s>>>(x, m->TR64, m->ncells, skip,
+                                                             m->tabN64);
+    dg_timing_mark(m, 1, s);
+    k_cell_nd<N><<<blocks, Cfg<N>::THREADS, 2 * s1, s>>>(x, m->TR64, m->lineopN64, m->gh64, y,
+                                                        m->ncells, m->N, skip, m->tabN64);
+    dg_timing_mark(m, 2, s);
+    return cudaGetLastError();
+  }
+  template <typename T>
+  static cudaError_t run(int what, const dg_mesh* m, const double* x, double* y,
+                         const int* skip, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((m->ncells + Cfg<N>::CPB - 1) / Cfg<N>::CPB);
+    const size_t s1 = sizeof(double) * Cfg<N>::CPB * N * N * N;
+    switch (what) {
+      case 0: return apply<T>(m, x, y, skip, s);
+      case 1:
+        k_collocation<N, true><<<blocks, Cfg<N>::THREADS, s1, s>>>(x, y, m->ncells, m->tab64,
+                                                                   m->tabN64);
+        return cudaGetLastError();
+      case 2:
+        k_collocation<N, false><<<blocks, Cfg<N>::THREADS, s1, s>>>(x, y, m->ncells, m->tab64,
+                                                                    m->tabN64);
+        return cudaGetLastError();
+      case 3: {
+        const long long threads = m->ncells * 3 * N * N;
+        k_line_ops<N, true><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+            m->kt64, m->gh64, m->lineopN64, m->ncells, m->N, m->tab64, m->tabN64);
+        return cudaGetLastError();
+      }
+      case 4:
+        k_diag_nd<N><<<(unsigned)((m->ndofs + 255) / 256), 256, 0, s>>>(
+            m->lineopN64, m->dinvN64, m->dinvN32, m->ndofs);
+        return cudaGetLastError();
+      default: return cudaErrorInvalidValue;
+    }
+  }
+};
+
+}  // namespace dgk
+
+void dg_build_nodal_tables(const DGTab<double>& t, int n, DGTabN<double>* d, DGTabN<float>* f) {
+  *d = DGTabN<double>{};
+  *f = DGTabN<float>{};
+  for (int a = 0; a < n; ++a) {
+    const double sw = std::sqrt(t.w[a]), isw = 1.0 / sw;
+    d->sw[a] = sw;
+    d->isw[a] = isw;
+    d->l0[a] = t.l0[a] * isw;
+    d->l1[a] = t.l1[a] * isw;
+    d->hdl0[a] = 0.5 * t.dl0[a] * isw;
+    d->hdl1[a] = 0.5 * t.dl1[a] * isw;
+  }
+  for (int fq = 0; fq < n; ++fq)
+    for (int i = 0; i < n; ++i) d->Dh[fq][i] = d->sw[fq] * t.D[fq][i] * d->isw[i];
+  for (int a = 0; a < n; ++a) {
+    f->sw[a] = (float)d->sw[a];
+    f->isw[a] = (float)d->isw[a];
+    f->l0[a] = (float)d->l0[a];
+    f->l1[a] = (float)d->l1[a];
+    f->hdl0[a] = (float)d->hdl0[a];
+    f->hdl1[a] = (float)d->hdl1[a];
+    for (int i = 0; i < n; ++i) f->Dh[a][i] = (float)d->Dh[a][i];
+  }
+}
+
+namespace {
+int run_nodal(int what, const dg_mesh* m, const double* x, double* y, const int* skip,
+              cudaStream_t s, const char* who) {
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (m->n) {
+    case 2: e = dgk::NodalF<2>::run<double>(what, m, x, y, skip, s); break;
+    case 3: e = dgk::NodalF<3>::run<double>(what, m, x, y, skip, s); break;
+    case 4: e = dgk::NodalF<4>::run<double>(what, m, x, y, skip, s); break;
+    case 5: e = dgk::NodalF<5>::run<double>(what, m, x, y, skip, s); break;
+    case 6: e = dgk::NodalF<6>::run<double>(what, m, x, y, skip, s); break;
+    case 7: e = dgk::NodalF<7>::run<double>(what, m, x, y, skip, s); break;
+    case 8: e = dgk::NodalF<8>::run<double>(what, m, x, y, skip, s); break;
+    case 9: e = dgk::NodalF<9>::run<double>(what, m, x, y, skip, s); break;
+    default: break;
+  }
+  if (e != cudaSuccess) return dg_cuda_fail(e, who);
+  return DG_OK;
+}
+}  // namespace
+
+int dg_ensure_nodal(dg_mesh* m, cudaStream_t s) {
+  if (m->has_nodal) return DG_OK;
+  if (int rc = dg_require_cube(m, "the scaled Gauss-point basis")) return rc;
+  const size_t nd = (size_t)m->ndofs;
+  const size_t nlo = (size_t)3 * m->n * m->n * (size_t)(m->n * (m->n + 1) / 2) * (size_t)m->ncells;
+  if (m->lineopN64 == nullptr) DG_CUDA(cudaMalloc((void**)&m->lineopN64, nlo * sizeof(double)));
+  if (m->bN64 == nullptr) DG_CUDA(cudaMalloc((void**)&m->bN64, nd * sizeof(double)));
+  if (m->xN64 == nullptr) DG_CUDA(cudaMalloc((void**)&m->xN64, nd * sizeof(double)));
+  int rc = run_nodal(3, m, nullptr, nullptr, nullptr, s, "nodal line operators");
+  if (rc) return rc;
+  m->has_nodal = true;
+  return DG_OK;
+}
+
+int dg_ensure_nodal_diag(dg_mesh* m, cudaStream_t s) {
+  int rc = dg_ensure_nodal(m, s);
+  if (rc || m->has_nodal_diag) return rc;
+  const size_t nd = (size_t)m->ndofs;
+  if (m->dinvN64 == nullptr) DG_CUDA(cudaMalloc((void**)&m->dinvN64, nd * sizeof(double)));
+  if (m->dinvN32 == nullptr) DG_CUDA(cudaMalloc((void**)&m->dinvN32, nd * sizeof(float)));
+  rc = run_nodal(4, m, nullptr, nullptr, nullptr, s, "nodal Jacobi diagonal");
+  if (rc) return rc;
+  m->has_nodal_diag = true;
+  return DG_OK;
+}
+
+int dg_launch_apply_nodal_f64(const dg_mesh* m, const double* x, double* y, const int* skip,
+                              cudaStream_t s) {
+  return run_nodal(0, m, x, y, skip, s, "apply in the point basis (fp64) launch");
+}
+
+int dg_launch_collocation(const dg_mesh* m, const double* in, double* out, bool to_nodal,
+                          cudaStream_t s) {
+  return run_nodal(to_nodal ? 1 : 2, m, in, out, nullptr, s, "basis transform launch");
+}
+
+static int check_nodal_args(const dg_mesh* m, const void* a, const void* b, const char* who) {
+  if (m == nullptr) return dg_fail(DG_ERR_INVALID_ARG, "%s: mesh is NULL", who);
+  if (a == nullptr || b == nullptr) return dg_fail(DG_ERR_INVALID_ARG, "%s: NULL vector", who);
+  if (a == b) return dg_fail(DG_ERR_INVALID_ARG, "%s: input and output alias", who);
+  return dg_require_cube(m, who);
+}
+
+extern "C" int dg_to_nodal(const dg_mesh* m, const double* x, double* xhat, void* stream) {
+  if (int rc = check_nodal_args(m, x, xhat, "dg_to_nodal")) return rc;
+  return dg_launch_collocation(m, x, xhat, true, (cudaStream_t)stream);
+}
+
+extern "C" int dg_to_modal(const dg_mesh* m, const double* xhat, double* x, void* stream) {
+  if (int rc = check_nodal_args(m, xhat, x, "dg_to_modal")) return rc;
+  return dg_launch_collocation(m, xhat, x, false, (cudaStream_t)stream);
+}
+
+extern "C" int dg_apply_nodal(const dg_mesh* mc, const double* xhat, double* yhat, void* stream) {
+  if (int rc = check_nodal_args(mc, xhat, yhat, "dg_apply_nodal")) return rc;
+  if (!mc->has_coef) return dg_fail(DG_ERR_INVALID_ARG, "dg_apply_nodal: coefficient not set");
+  dg_mesh* m = const_cast<dg_mesh*>(mc);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int rc = dg_ensure_nodal(m, s)) return rc;
+  return dg_launch_apply_nodal_f64(m, xhat, yhat, nullptr, s);
+}

@@ -1,0 +1,199 @@
+"""The scaled Gauss-point (collocation) basis on the GPU against the oracle.
+
+dg_to_nodal / dg_to_modal against the oracle's Q and Q^T; dg_apply_nodal
+against the oracle's Q A Q^T element by element (1e-12, degrees 1-8, odd and
+one-cell meshes, both boundary conditions, and sampled cells of the 64^3 Q3
+benchmark mesh); the CG in that basis (DG_CG_NODAL) by its first iterates
+against the oracle's recurrence (M = I: the Legendre-basis iterates, since Q is
+orthogonal; Jacobi: the oracle's PCG on Q A Q^T with its diagonal) and by
+residuals that the oracle recomputes in the Legendre basis.
+"""
+import numpy as np
+import pytest
+
+from oracle import SIPG, cg
+from paper_1911_01492_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def dg(cuda_device):
+    import paper_1911_01492_gb300 as dg
+    dg.library()
+    return dg
+
+
+def relmax(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def field(N, k, seed):
+    # the per-cell statistics of the 64^3 workload (correlation length in cells)
+    return inputs.lognormal_coefficient(N, k, seed=seed, corr_len=0.1 * 64 / N)
+
+
+def mesh(dg, N, k, K, bc="dirichlet"):
+    import torch
+    m = dg.Mesh(N, k)
+    if bc != "dirichlet":
+        m.set_boundary(bc)
+    m.set_coefficient(torch.from_numpy(K).cuda())
+    return m
+
+
+@pytest.mark.parametrize("N,k", [(3, 1), (3, 2), (2, 3), (3, 4), (2, 5), (1, 6), (2, 7), (1, 8)])
+def test_transforms_match_oracle_and_invert(dg, N, k):
+    import torch
+    D = SIPG(N, k)
+    x = inputs.uniform_vector(N, k, 31)
+    m = dg.Mesh(N, k)
+    xh = m.to_nodal(torch.from_numpy(x).cuda())
+    assert relmax(xh.cpu().numpy(), D.to_collocation(x)) <= TOL64
+    back = m.to_modal(xh).cpu().numpy()
+    assert relmax(back, x) <= TOL64
+    xh2 = inputs.uniform_vector(N, k, 32)
+    got = m.to_modal(torch.from_numpy(xh2).cuda()).cpu().numpy()
+    assert relmax(got, D.from_collocation(xh2)) <= TOL64
+
+
+@pytest.mark.parametrize("N,k,seed,bc", [
+    (1, 1, 3, "dirichlet"), (4, 1, 4, "dirichlet"), (3, 2, 5, "dirichlet"), (5, 2, 6, "flow_x"),
+    (4, 3, 7, "dirichlet"), (3, 3, 8, "flow_x"), (3, 4, 9, "dirichlet"), (2, 5, 10, "dirichlet"),
+    (2, 6, 11, "flow_x"), (2, 7, 12, "dirichlet"), (1, 8, 13, "dirichlet"), (2, 8, 14, "dirichlet")])
+def test_apply_nodal_matches_oracle(dg, N, k, seed, bc):
+    import torch
+    D = SIPG(N, k, bc=bc)
+    K = field(N, k, seed)
+    m = mesh(dg, N, k, K, bc)
+    xh = inputs.uniform_vector(N, k, 100 + seed)
+    y = m.apply_nodal(torch.from_numpy(xh).cuda()).cpu().numpy()
+    assert relmax(y, D.collocation_apply(K, xh)) <= TOL64
+    # the same operator through the Legendre basis: Q^T (Q A Q^T) Q x = A x
+    x = inputs.uniform_vector(N, k, 200 + seed)
+    yx = m.to_modal(m.apply_nodal(m.to_nodal(torch.from_numpy(x).cuda()))).cpu().numpy()
+    assert relmax(yx, D.apply(K, x)) <= TOL64
+
+
+def test_apply_nodal_is_symmetric_and_follows_a_new_coefficient(dg):
+    import torch
+    N, k = 4, 3
+    K = field(N, k, 15)
+    m = mesh(dg, N, k, K)
+    u = torch.from_numpy(inputs.uniform_vector(N, k, 16)).cuda()
+    v = torch.from_numpy(inputs.uniform_vector(N, k, 17)).cuda()
+    a = float(v @ m.apply_nodal(u))
+    b = float(u @ m.apply_nodal(v))
+    assert abs(a - b) <= 1e-12 * abs(a)
+    # set_coefficient drops the basis's line operators: the next call uses the new K
+    K2 = field(N, k, 18)
+    m.set_coefficient(torch.from_numpy(K2).cuda())
+    D = SIPG(N, k)
+    y = m.apply_nodal(u).cpu().numpy()
+    assert relmax(y, D.collocation_apply(K2, u.cpu().numpy())) <= TOL64
+
+
+def test_apply_nodal_full_size_64cubed_q3_sampled_cells(dg):
+    """The benchmark mesh (64^3 Q3, lognormal K seed 2): every DOF of 24 random
+    cells (boundary, edge and interior cells included) against the oracle,
+    which applies A to Q^T x_hat on those cells only."""
+    import torch
+    N, k = 64, 3
+    K = inputs.lognormal_coefficient(N, k, seed=2)
+    D = SIPG(N, k)
+    m = mesh(dg, N, k, K)
+    xh = inputs.uniform_vector(N, k, 33)
+    y = m.apply_nodal(torch.from_numpy(xh).cuda()).cpu().numpy().reshape(N ** 3, -1)
+    rng = np.random.default_rng(34)
+    cells = np.concatenate([[0, N - 1, N * N * N - 1, N * N * (N // 2) + N * (N // 2)],
+                            rng.choice(N ** 3, 20, replace=False)])
+    x = D.from_collocation(xh)
+    ya = D.apply(K, x, cells=cells)
+    Q = D.collocation_matrix()
+    ref = ya.reshape(len(cells), -1) @ Q.T
+    assert relmax(y[cells], ref) <= TOL64
+
+
+@pytest.mark.parametrize("N,k", [(4, 3), (3, 2), (3, 4), (2, 6)])
+@pytest.mark.parametrize("precond", [None, "jacobi"])
+def test_nodal_cg_first_iterates_match_oracle_recurrence(dg, N, k, precond):
+    """Three CG iterations from x = 0.  M = I: Q is orthogonal, so x_3 equals
+    the Legendre-basis CG iterate.  Jacobi: the oracle's PCG on Q A Q^T with
+    M = diag(Q A Q^T), mapped back with Q^T."""
+    import torch
+    D = SIPG(N, k)
+    K = field(N, k, 41)
+    b = inputs.uniform_vector(N, k, 42)
+    if precond is None:
+        xref, _, _, _ = cg(lambda v: D.apply(K, v), b, rtol=1e-14, maxit=3)
+    else:
+        xh, _, _, _ = cg(lambda v: D.collocation_apply(K, v), D.to_collocation(b), rtol=1e-14,
+                         maxit=3, minv=1.0 / D.collocation_diagonal(K))
+        xref = D.from_collocation(xh)
+    m = mesh(dg, N, k, K)
+    x, st = m.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-14, maxit=3, precond=precond,
+                       nodal=True, raise_on_error=False)
+    assert st["iterations"] == 3, st
+    assert st["status"] == dg.DG_ERR_NOT_CONVERGED
+    assert relmax(x.cpu().numpy(), xref) <= 1e-10
+
+
+@pytest.mark.parametrize("N,k,seed,bc", [(4, 3, 5, "dirichlet"), (5, 2, 6, "dirichlet"),
+                                         (3, 4, 4, "dirichlet"), (4, 2, 7, "flow_x")])
+@pytest.mark.parametrize("precond", [None, "jacobi"])
+def test_nodal_cg_residual_checked_by_oracle(dg, N, k, seed, bc, precond):
+    import torch
+    D = SIPG(N, k, bc=bc)
+    K = field(N, k, seed)
+    b = inputs.constant_load_vector(N, k)
+    m = mesh(dg, N, k, K, bc)
+    x, st = m.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-10, precond=precond, nodal=True)
+    x = x.cpu().numpy()
+    assert st["status"] == 0
+    assert st["rel_residual"] <= 1e-10
+    rel = np.linalg.norm(b - D.apply(K, x)) / np.linalg.norm(b)
+    assert rel <= 1.05e-10
+    # same solution as the Legendre-basis solve within the conditioning bound
+    xm, _ = m.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-12, precond=precond)
+    xm = xm.cpu().numpy()
+    assert np.linalg.norm(x - xm) <= 1e-5 * np.linalg.norm(xm)
+
+
+def test_nodal_cg_initial_guess_zero_rhs_and_rejected_modes(dg):
+    import torch
+    N, k = 3, 3
+    D = SIPG(N, k)
+    K = field(N, k, 9)
+    m = mesh(dg, N, k, K)
+    b = inputs.uniform_vector(N, k, 10)
+    x0 = torch.from_numpy(inputs.uniform_vector(N, k, 11)).cuda()
+    x, st = m.cg_solve(torch.from_numpy(b).cuda(), x=x0, rtol=1e-11, nodal=True)
+    rel = np.linalg.norm(b - D.apply(K, x.cpu().numpy())) / np.linalg.norm(b)
+    assert rel <= 1.05e-11
+    z = torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda")
+    x, st = m.cg_solve(z.clone(), x=torch.ones_like(z), rtol=1e-10, nodal=True)
+    assert st["status"] == 0 and torch.count_nonzero(x).item() == 0
+    for mode in (dg.DG_CG_MIXED_IR, dg.DG_CG_MIXED_IR_RESTART):
+        with pytest.raises(dg.DGError, match="INVALID_ARG"):
+            m.cg_solve(torch.from_numpy(b).cuda(), mode=mode, nodal=True)
+    with pytest.raises(dg.DGError, match="INVALID_ARG"):
+        m.cg_solve(torch.from_numpy(b).cuda(), precond="kron", nodal=True)
+
+
+def test_nodal_cg_first_iterates_full_size_48cubed_q4(dg):
+    """The CG workload (48^3 Q4, lognormal K seed 4) in the benchmark's
+    configuration: three iterations in the point basis, every DOF against the
+    oracle's Legendre-basis recurrence."""
+    import torch
+    N, k = 48, 4
+    K = inputs.lognormal_coefficient(N, k, seed=4)
+    b = inputs.uniform_vector(N, k, 23)
+    D = SIPG(N, k)
+    xref, _, _, _ = cg(lambda v: D.apply(K, v), b, rtol=1e-14, maxit=3)
+    m = mesh(dg, N, k, K)
+    x, st = m.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-14, maxit=3, nodal=True,
+                       raise_on_error=False)
+    assert st["iterations"] == 3, st
+    assert relmax(x.cpu().numpy(), xref) <= 1e-10
