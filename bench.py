@@ -371,8 +371,7 @@ def run_cg(world, modes=None):
                       ("mixed_ir_kron", dg.DG_CG_MIXED_IR | dg.DG_CG_PRECOND_KRON),
                       ("fp64_kron", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_KRON),
                       ("fp64_nodal", dg.DG_CG_FP64 | dg.DG_CG_NODAL),
-                      ("fp64_nodal_jacobi",
-                       dg.DG_CG_FP64 | dg.DG_CG_NODAL | dg.DG_CG_PRECOND_JACOBI))
+                      ("mixed_ir_nodal", dg.DG_CG_MIXED_IR | dg.DG_CG_NODAL))
     for name, mode in modes:
         if mode & (dg.DG_CG_PRECOND_JACOBI | dg.DG_CG_PRECOND_KRON | dg.DG_CG_NODAL):
             # drops the cached preconditioner and basis data: the solve forms them
@@ -970,7 +969,8 @@ def run_cg_probe(iters: int, n_cells: int = 0):
                        ("fp64_kron", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_KRON),
                        ("fp64_nodal", dg.DG_CG_FP64 | dg.DG_CG_NODAL),
                        ("fp64_nodal_jacobi",
-                        dg.DG_CG_FP64 | dg.DG_CG_NODAL | dg.DG_CG_PRECOND_JACOBI)):
+                        dg.DG_CG_FP64 | dg.DG_CG_NODAL | dg.DG_CG_PRECOND_JACOBI),
+                       ("mixed_ir_nodal", dg.DG_CG_MIXED_IR | dg.DG_CG_NODAL)):
         x = torch.zeros_like(b)
         _, st = m.cg_solve(b, x, rtol=1e-12, maxit=iters, mode=mode, raise_on_error=False)
         print(json.dumps({"mode": name, "iterations": st["iterations"],

@@ -50,7 +50,7 @@ enum { DG_CG_FP64 = 0, DG_CG_MIXED_IR = 1, DG_CG_MIXED_IR_RESTART = 2 };  /* dg_
 enum { DG_CG_PRECOND_JACOBI = 256 };  /* OR into a mode: PCG with M = diag(A) */
 enum { DG_CG_PRECOND_BLOCK = 512 };   /* OR into DG_CG_FP64: PCG with M = the cell blocks of A */
 enum { DG_CG_PRECOND_KRON = 1024 };   /* OR into DG_CG_FP64 or DG_CG_MIXED_IR: Kronecker cell blocks */
-enum { DG_CG_NODAL = 2048 };          /* OR into DG_CG_FP64: iterate in the scaled Gauss-point basis */
+enum { DG_CG_NODAL = 2048 };          /* OR into DG_CG_FP64 or DG_CG_MIXED_IR: iterate in the scaled Gauss-point basis */
 /* Boundary conditions (dg_set_boundary): bit f set = boundary side f is Dirichlet,
  * sides in the order x-, x+, y-, y+, z-, z+; the other sides carry zero flux. */
 enum { DG_BC_DIRICHLET = 0x3F, DG_BC_FLOW_X = 0x03 };
@@ -210,19 +210,22 @@ int dg_coeff_grad(const dg_mesh* mesh, const double* u, const double* v, double*
  *   first such solve after dg_set_coefficient (any degree); BREAKDOWN if a 1D
  *   factor has a negative eigenvalue (a direction with only zero-flux faces,
  *   one cell across, has a singular factor, which is allowed).
- * DG_CG_FP64 | DG_CG_NODAL (with or without DG_CG_PRECOND_JACOBI): the same
- *   FP64 CG run on (Q A Q^T) x_hat = Q b in the scaled Gauss-point basis of
- *   dg_to_nodal.  Q is orthogonal, so without a preconditioner the iterates
- *   are Q times those of the Legendre-basis CG (in exact arithmetic); each
- *   operator application skips the six 1D basis transforms per cell.  With
+ * DG_CG_FP64 or DG_CG_MIXED_IR | DG_CG_NODAL (with or without
+ *   DG_CG_PRECOND_JACOBI): the same CG run on (Q A Q^T) x_hat = Q b in the
+ *   scaled Gauss-point basis of dg_to_nodal, the FP32 operator of the mixed
+ *   mode and its FP64 refinements included.  Q is orthogonal, so without a
+ *   preconditioner the iterates are Q times those of the Legendre-basis CG
+ *   (in exact arithmetic); each operator application skips the six 1D basis
+ *   transforms per cell.  With
  *   DG_CG_PRECOND_JACOBI the diagonal is that of Q A Q^T (a different
  *   preconditioner from diag(A)).  b and x are mapped once into the basis and
  *   x back once; the returned residual is recomputed in the Legendre basis,
  *   and if the mapping's rounding left it above rtol, plain FP64 CG iterations
  *   from x finish the solve (counted in iterations).  Formed on the first such
  *   solve after dg_set_coefficient: the line operators of Q A Q^T (as many
- *   values as dg_set_coefficient's, ~7.5 doubles per DOF at degree 3) and two
- *   solve vectors.  Cube meshes only.
+ *   values as dg_set_coefficient's, ~7.5 doubles per DOF at degree 3), two
+ *   solve vectors and, for the mixed mode, h K at the points in FP32.  Cube
+ *   meshes only.
  * Stops when ||b - A x|| <= rtol ||b|| recomputed in FP64.  Blocking.
  * Returns NOT_CONVERGED at maxit (x holds the last iterate), BREAKDOWN on
  * <p, Ap> <= 0 or non-finite scalars, TIMEOUT if a bounded wait of the mixed

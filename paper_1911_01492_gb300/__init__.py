@@ -389,7 +389,7 @@ class Mesh:
         (M = the inverted cell blocks of A; FP64 mode, degree <= 4) or "kron"
         (M = the Kronecker cell blocks, fast diagonalisation; FP64 or mixed).
         nodal: iterate in the scaled Gauss-point basis (same as OR-ing
-        DG_CG_NODAL into mode; FP64 mode, M = I or Jacobi).
+        DG_CG_NODAL into mode; FP64 or mixed mode, M = I or Jacobi).
         Returns (x, stats dict)."""
         import torch
         if precond not in (None, "jacobi", "block", "kron"):

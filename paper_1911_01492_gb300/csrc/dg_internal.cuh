@@ -35,7 +35,8 @@ struct DGTabN {
   T sw[DG_MAXN];                  // sqrt(w_a)
   T isw[DG_MAXN];                 // 1 / sqrt(w_a)
   T l0[DG_MAXN], l1[DG_MAXN];     // l_a(0) / sqrt(w_a), l_a(1) / sqrt(w_a)
-  T hdl0[DG_MAXN], hdl1[DG_MAXN]; // l_a'(0) / (2 sqrt(w_a)), l_a'(1) / (2 sqrt(w_a))
+  T dl0[DG_MAXN], dl1[DG_MAXN];   // l_a'(0) / sqrt(w_a), l_a'(1) / sqrt(w_a)
+  T hdl0[DG_MAXN], hdl1[DG_MAXN]; // the same halved
   T Dh[DG_MAXN][DG_MAXN];         // sqrt(w_f) D[f][i] / sqrt(w_i)
 };
 
@@ -134,6 +135,8 @@ struct dg_mesh {
   double* dinvN64;
   float* dinvN32;
   double *bN64, *xN64;
+  float* hk32;        // h K at the volume points (FP32 operator in that basis) [c][q]
+  bool has_nodal32;
   double* kbar;     // Kbar_c                          [c]
   int* dflag;       // device-side error flag of the setup kernels
 
@@ -237,6 +240,7 @@ int dg_prepare_grad(int n);
 void dg_build_nodal_tables(const DGTab<double>& t, int n, DGTabN<double>* d, DGTabN<float>* f);
 int dg_ensure_nodal(dg_mesh* m, cudaStream_t s);
 int dg_ensure_nodal_diag(dg_mesh* m, cudaStream_t s);
+int dg_ensure_nodal32(dg_mesh* m, cudaStream_t s);  // h K in FP32 for the mixed CG
 int dg_launch_apply_nodal_f64(const dg_mesh* m, const double* x, double* y, const int* skip,
                               cudaStream_t s);
 int dg_launch_collocation(const dg_mesh* m, const double* in, double* out, bool to_nodal,

@@ -127,6 +127,58 @@ struct ZDirUpdate {
   }
 };
 
+// Pass 1 in the scaled Gauss-point basis (DG_CG_NODAL solves) on a group of
+// cells staged in shared memory (s, n^3 values per cell): the z-line threads
+// produce their lines with the loader (the direction update), keep them in
+// shared memory for the y- and x-lines and form the z-face traces at once;
+// after one barrier the same threads form the y- and x-face traces.  Traces
+// (value, full reference derivative) by the scaled Lagrange end values, layout
+// TR[c][2f + {0, 1}][n^2] as in the Legendre basis.
+template <int N, typename T, typename ZL>
+__device__ __forceinline__ void trace_core_nd(T* __restrict__ TR, long long c0, int nblk,
+                                              const DGTabN<T>& tn, T* s, const ZL& zload) {
+  constexpr int N2 = N * N, N3 = N * N * N;
+  const int lc = threadIdx.x / N2;
+  const int t2 = threadIdx.x - lc * N2;
+  const int p = t2 % N, q = t2 / N;
+  const bool active = lc < nblk;
+  T* sc = s + lc * N3;
+  T* tr = TR + (c0 + lc) * (12 * N2) + t2;
+  auto ends = [&](const T (&u)[N], T* trf) {
+    using ::fma;  // the scalar one (dgk::fma is the packed pair's)
+    T vm = tn.l0[0] * u[0], vp = tn.l1[0] * u[0];
+    T gm = tn.dl0[0] * u[0], gp = tn.dl1[0] * u[0];
+#pragma unroll
+    for (int e = 1; e < N; ++e) {
+      vm = fma(tn.l0[e], u[e], vm);
+      vp = fma(tn.l1[e], u[e], vp);
+      gm = fma(tn.dl0[e], u[e], gm);
+      gp = fma(tn.dl1[e], u[e], gp);
+    }
+    trf[0] = vm;
+    trf[N2] = gm;
+    trf[2 * N2] = vp;
+    trf[3 * N2] = gp;
+  };
+  if (active) {  // z-line (a = p, b = q)
+    T v[N];
+    zload.template operator()<N, T>(sc, lc, p, q, v);
+#pragma unroll
+    for (int e = 0; e < N; ++e) sc[e * N2 + q * N + p] = v[e];
+    ends(v, tr + 8 * N2);
+  }
+  __syncthreads();
+  if (active) {
+    T u[N];
+#pragma unroll
+    for (int b = 0; b < N; ++b) u[b] = sc[q * N2 + b * N + p];  // y-line (a = p, e = q)
+    ends(u, tr + 4 * N2);
+#pragma unroll
+    for (int a = 0; a < N; ++a) u[a] = sc[q * N2 + p * N + a];  // x-line (b = p, e = q)
+    ends(u, tr);
+  }
+}
+
 // Direction kernel with the block's inputs staged by bulk copies,
 // double-buffered.  The cells are cut into groups of G = 4 CPB cells: G n^3
 // floats are a multiple of 16 bytes for every n, so each group of r, p (and
@@ -153,11 +205,13 @@ struct Dir32Bulk {
   static_assert(GROUP_BYTES % 16 == 0, "bulk copies need 16-byte multiples");
 };
 
-template <int N, bool PC>
+// ND: the scaled Gauss-point basis (point values in, trace_core_nd).
+template <int N, bool PC, bool ND = false>
 __global__ void __launch_bounds__(Dir32Bulk<N, PC>::THREADS)
 k_dir32_bulk(const float* __restrict__ r, float* __restrict__ p, float* __restrict__ TR,
              const float* __restrict__ dinv, long long ncells, DGCGState* st,
-             long long limit, int stall_test, const __grid_constant__ DGTab<float> tab) {
+             long long limit, int stall_test, const __grid_constant__ DGTab<float> tab,
+             const __grid_constant__ DGTabN<float> tn) {
   using B = Dir32Bulk<N, PC>;
   constexpr int N3 = B::N3, G = B::G, NT = B::THREADS;
   // nothing to do once done, at the cap, or with an FP64 refinement pending
@@ -227,7 +281,10 @@ k_dir32_bulk(const float* __restrict__ r, float* __restrict__ p, float* __restri
       const int nblk = (int)((ncells - cg0) < G ? (ncells - cg0) : G);
       // p = z + beta p by the z-line threads, then pass 1 of p (traces only)
       const ZDirUpdate<PC> zl{br(b), bd(b), p + cg0 * N3, beta};
-      trace_core<N, float, 2>(nullptr, nullptr, TR, cg0, nblk, tab, bp(b), nullptr, zl);
+      if constexpr (ND)
+        trace_core_nd<N, float>(TR, cg0, nblk, tn, bp(b), zl);
+      else
+        trace_core<N, float, 2>(nullptr, nullptr, TR, cg0, nblk, tab, bp(b), nullptr, zl);
       __syncthreads();
     }
   }
@@ -566,6 +623,242 @@ k_cell32x2(const float* __restrict__ pg, const float* __restrict__ TR,
   }
 }
 
+// ---------------------------------------------------------------------------
+// k_cell32x2_nd: the FP32 operator pass of the mixed iteration in the scaled
+// Gauss-point basis (DG_CG_NODAL), on pairs of consecutive cells in packed
+// FP32 like k_cell32x2.  Per line of each direction (z, then y, then x):
+// r += Dh^T (h K . Dh u) with Dh = sqrt(w) D / sqrt(w) (the collocation
+// derivative of the scaled point values), plus the own and neighbour face
+// terms with the scaled Lagrange end values and the face weight h gamma / 2.
+// No basis transforms: the z-line threads load p from global memory, the
+// partial sums of q stay in shared memory, the x-line threads finish q, store
+// it and fold <p, q> (exact products, compensated float-float sums) as the
+// Legendre-basis kernel does.  Three block barriers instead of eight.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS, N <= 5 ? 8 : 1)
+k_cell32x2_nd(const float* __restrict__ pg, const float* __restrict__ TR,
+              const float* __restrict__ hk, const float* __restrict__ gh, float* __restrict__ qg,
+              long long ncells, int Nc, double* __restrict__ partials, DGCGState* st,
+              const __grid_constant__ DGTabN<float> tn) {
+  constexpr int C = Cfg<N>::CPB, N2 = N * N, N3 = N * N * N, NT = Cfg<N>::THREADS;
+  constexpr float S2 = 4.0f * N * N;  // 2 sigma, sigma = 2 (k+1)^2
+  if (st->done || st->iters >= st->maxit || st->ru_skip == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  F2* su = reinterpret_cast<F2*>(smem_raw);
+  F2* sr = su + C * N3;
+  F2* sk = sr + C * N3;
+  __shared__ float rh[NT], rl[NT];
+  __shared__ bool is_last;
+  __shared__ int sbase[3];
+  const long long c0 = (long long)blockIdx.x * (2 * C);
+  const int lc = threadIdx.x / N2;
+  const int t2 = threadIdx.x - lc * N2;
+  const int p = t2 % N, q = t2 / N;
+  const long long ca = c0 + 2 * lc, cb = ca + 1;
+  const bool va = ca < ncells, vb = cb < ncells;
+  const int o = lc * N3;
+  if (threadIdx.x == 0) {
+    const unsigned cu = (unsigned)c0, n = (unsigned)Nc;
+    sbase[0] = (int)(cu % n);
+    sbase[1] = (int)((cu / n) % n);
+    sbase[2] = (int)(cu / n / n);
+  }
+  // h K of the block's cell pairs and the thread's z-line of p (a = p, b = q)
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int t = threadIdx.x + k * NT;  // < C N3 = N NT
+    const int pr = t / N3, pos = t - pr * N3;
+    const long long c = c0 + 2 * pr;
+    sk[t] = F2(c < ncells ? hk[c * N3 + pos] : 0.0f, c + 1 < ncells ? hk[(c + 1) * N3 + pos] : 0.0f);
+  }
+  F2 u[N];
+#pragma unroll
+  for (int e = 0; e < N; ++e) {
+    const int idx = e * N2 + q * N + p;
+    u[e] = F2(va ? pg[ca * N3 + idx] : 0.0f, vb ? pg[cb * N3 + idx] : 0.0f);
+    su[o + idx] = u[e];
+  }
+  __syncthreads();
+  int cxa = sbase[0] + 2 * lc, cya = sbase[1], cza = sbase[2];
+  while (cxa >= Nc) {
+    cxa -= Nc;
+    if (++cya == Nc) {
+      cya = 0;
+      ++cza;
+    }
+  }
+  int cxb = cxa + 1, cyb = cya, czb = cza;
+  if (cxb == Nc) {
+    cxb = 0;
+    if (++cyb == Nc) {
+      cyb = 0;
+      ++czb;
+    }
+  }
+  const long long sy = Nc, sz = (long long)Nc * Nc;
+  const int pt = t2;
+  // face f's neighbour trace, weight h gamma / 2 and boundary factor e for
+  // both lanes (zero trace on a boundary lane; a lane without a cell loads
+  // nothing and keeps finite zeros)
+  auto face = [&](int f, bool ina, bool inb, long long cna, long long cnb, F2& un, F2& gn,
+                  F2& wh, F2& e) {
+    float ua = 0.f, ga = 0.f, ub = 0.f, gb = 0.f;
+    if (ina) load_trace<N>(TR, cna, f ^ 1, pt, ua, ga);
+    if (inb) load_trace<N>(TR, cnb, f ^ 1, pt, ub, gb);
+    un = F2(ua, ub);
+    gn = F2(ga, gb);
+    wh = F2(va ? 0.5f * gh[ca * 6 + f] : 0.0f, vb ? 0.5f * gh[cb * 6 + f] : 0.0f);
+    e = F2(ina ? 1.0f : 2.0f, inb ? 1.0f : 2.0f);
+  };
+  auto flux = [&](bool upper, F2 uo, F2 go, F2 unf, F2 gnf, F2 whf, F2 ef, F2& cv, F2& cd) {
+    const F2 J = upper ? uo - unf : unf - uo;
+    const F2 G = fma(ef, go, gnf);
+    const F2 tt = upper ? fma(S2, J, -G) : fma(-S2, J, G);
+    cv = whf * tt;
+    cd = (whf * ef) * J;
+  };
+  // one line: r = r + Dh^T (hK . Dh u) + the line's two faces (slots sl, su_)
+  auto line = [&](int base, int step, const F2 (&un)[2], const F2 (&gn)[2], const F2 (&wh)[2],
+                  const F2 (&ee)[2], F2 (&r)[N]) {
+    F2 kg[N];
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+      F2 g = tn.Dh[e][0] * u[0];
+#pragma unroll
+      for (int f = 1; f < N; ++f) g = fma(tn.Dh[e][f], u[f], g);
+      kg[e] = sk[o + base + e * step] * g;
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+      for (int e = 0; e < N; ++e) r[i] = fma(tn.Dh[e][i], kg[e], r[i]);
+    }
+    F2 vm = tn.l0[0] * u[0], vp = tn.l1[0] * u[0];
+    F2 gm = tn.dl0[0] * u[0], gp = tn.dl1[0] * u[0];
+#pragma unroll
+    for (int e = 1; e < N; ++e) {
+      vm = fma(tn.l0[e], u[e], vm);
+      vp = fma(tn.l1[e], u[e], vp);
+      gm = fma(tn.dl0[e], u[e], gm);
+      gp = fma(tn.dl1[e], u[e], gp);
+    }
+    F2 cv1, cd1, cv0, cd0;
+    flux(true, vp, gp, un[1], gn[1], wh[1], ee[1], cv1, cd1);
+    flux(false, vm, gm, un[0], gn[0], wh[0], ee[0], cv0, cd0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      F2 acc = fma(tn.l1[i], cv1, r[i]);
+      acc = fma(-tn.dl1[i], cd1, acc);
+      acc = fma(tn.l0[i], cv0, acc);
+      r[i] = fma(-tn.dl0[i], cd0, acc);
+    }
+  };
+  F2 un[2], gn[2], wh[2], ee[2];
+  {  // z-lines (a = p, b = q): the first partial sums of q
+    face(4, va && cza > 0, vb && czb > 0, ca - sz, cb - sz, un[0], gn[0], wh[0], ee[0]);
+    face(5, va && cza < Nc - 1, vb && czb < Nc - 1, ca + sz, cb + sz, un[1], gn[1], wh[1], ee[1]);
+    const int base = q * N + p;
+    F2 r[N];
+#pragma unroll
+    for (int e = 0; e < N; ++e) r[e] = F2(0.0f);
+    line(base, N2, un, gn, wh, ee, r);
+#pragma unroll
+    for (int e = 0; e < N; ++e) sr[o + base + e * N2] = r[e];
+  }
+  __syncthreads();
+  {  // y-lines (a = p, e = q)
+    face(2, va && cya > 0, vb && cyb > 0, ca - sy, cb - sy, un[0], gn[0], wh[0], ee[0]);
+    face(3, va && cya < Nc - 1, vb && cyb < Nc - 1, ca + sy, cb + sy, un[1], gn[1], wh[1], ee[1]);
+    const int base = q * N2 + p;
+    F2 r[N];
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+      u[b] = su[o + base + b * N];
+      r[b] = sr[o + base + b * N];
+    }
+    line(base, N, un, gn, wh, ee, r);
+#pragma unroll
+    for (int b = 0; b < N; ++b) sr[o + base + b * N] = r[b];
+  }
+  __syncthreads();
+  // x-lines (b = p, e = q): finish q, store it and fold <p, q> over the line
+  F2 hi = F2(0.0f), lo = F2(0.0f);
+  {
+    face(0, va && cxa > 0, vb && cxb > 0, ca - 1, cb - 1, un[0], gn[0], wh[0], ee[0]);
+    face(1, va && cxa < Nc - 1, vb && cxb < Nc - 1, ca + 1, cb + 1, un[1], gn[1], wh[1], ee[1]);
+    const int base = q * N2 + p * N;
+    F2 r[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      u[a] = su[o + base + a];
+      r[a] = sr[o + base + a];
+    }
+    line(base, 1, un, gn, wh, ee, r);
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      if (va) qg[ca * N3 + base + a] = r[a].v.x;
+      if (vb) qg[cb * N3 + base + a] = r[a].v.y;
+      const F2 pr = u[a] * r[a];
+      const F2 er = fma(u[a], r[a], -pr);  // u r = pr + er exactly
+      const F2 s1 = hi + pr;
+      const F2 bb = s1 - hi;
+      const F2 t1 = (hi - (s1 - bb)) + (pr - bb);
+      hi = s1;
+      lo = lo + (t1 + er);
+    }
+  }
+  {  // combine the lanes
+    float s1, t1;
+    two_sum_f(hi.v.x, hi.v.y, s1, t1);
+    rh[threadIdx.x] = s1;
+    rl[threadIdx.x] = (lo.v.x + lo.v.y) + t1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float h = rh[threadIdx.x], l = rl[threadIdx.x];
+    for (int i = threadIdx.x + 32; i < NT; i += 32) {
+      float s1, t1;
+      two_sum_f(h, rh[i], s1, t1);
+      h = s1;
+      l += t1 + rl[i];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h, off);
+      const float ol = __shfl_xor_sync(0xffffffffu, l, off);
+      float s1, t1;
+      two_sum_f(h, oh, s1, t1);
+      h = s1;
+      l += ol + t1;
+    }
+    if (threadIdx.x == 0) {
+      partials[blockIdx.x] = (double)h + (double)l;
+      __threadfence();
+      is_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  __shared__ double rd[NT];
+  const double tot = last_block_total<NT>(partials, (int)gridDim.x, rd);
+  if (threadIdx.x == 0) {
+    st->pq = tot;
+    if (!(tot > 0.0) || !isfinite(tot)) {
+      st->breakdown = 1;
+      st->done = 1;
+      st->ru_skip = 1;
+    } else {
+      const double rho = st->rho_new;  // k_dir32_bulk has used beta; commit the new rho
+      st->rho = rho;
+      st->restart = 0;
+      st->alpha = rho / tot;
+    }
+    st->ticket = 0u;
+  }
+}
+
 template <int N>
 struct Mixed32F {
   template <typename T>
@@ -579,15 +872,30 @@ struct Mixed32F {
     const long long limit = stall_now ? (1LL << 12) : (1LL << 22);
     const int pc = dinv != nullptr;
     const unsigned gb = (unsigned)m->dir_bulk_grid[pc];
+    const unsigned blocks2 = (unsigned)((m->ncells + 2 * C - 1) / (2 * C));
+    if (m->nodal_op) {  // the scaled Gauss-point basis (DG_CG_NODAL)
+      if (pc)
+        k_dir32_bulk<N, true, true><<<gb, Dir32Bulk<N, true>::THREADS, Dir32Bulk<N, true>::SMEM,
+                                      s>>>(rin, m->p32, m->TR32, dinv, m->ncells, m->state, limit,
+                                           stall_now ? 1 : 0, m->tab32, m->tabN32);
+      else
+        k_dir32_bulk<N, false, true><<<gb, Dir32Bulk<N, false>::THREADS,
+                                       Dir32Bulk<N, false>::SMEM, s>>>(
+            rin, m->p32, m->TR32, dinv, m->ncells, m->state, limit, stall_now ? 1 : 0, m->tab32,
+            m->tabN32);
+      k_cell32x2_nd<N><<<blocks2, Cfg<N>::THREADS, sizeof(F2) * 3 * C * N3, s>>>(
+          m->p32, m->TR32, m->hk32, m->gh32, m->q32, m->ncells, m->N, m->partials_cells,
+          m->state, m->tabN32);
+      return cudaGetLastError();
+    }
     if (pc)
       k_dir32_bulk<N, true><<<gb, Dir32Bulk<N, true>::THREADS, Dir32Bulk<N, true>::SMEM, s>>>(
           rin, m->p32, m->TR32, dinv, m->ncells, m->state, limit, stall_now ? 1 : 0,
-          m->tab32);
+          m->tab32, m->tabN32);
     else
       k_dir32_bulk<N, false><<<gb, Dir32Bulk<N, false>::THREADS, Dir32Bulk<N, false>::SMEM, s>>>(
           rin, m->p32, m->TR32, dinv, m->ncells, m->state, limit, stall_now ? 1 : 0,
-          m->tab32);
-    const unsigned blocks2 = (unsigned)((m->ncells + 2 * C - 1) / (2 * C));
+          m->tab32, m->tabN32);
     k_cell32x2<N><<<blocks2, Cfg<N>::THREADS, sizeof(F2) * 4 * C * N3, s>>>(
         m->p32, m->TR32, m->kt32, m->gh32, m->q32, m->ncells, m->N, m->partials_cells,
         m->state, m->tab32);
@@ -606,13 +914,20 @@ struct PrepareMixed32F {
       cudaError_t e = cudaFuncSetAttribute(k_cell32x2<N>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(sizeof(F2) * 4 * Cfg<N>::CPB * N * N * N));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cell32x2_nd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(F2) * 3 * Cfg<N>::CPB * N * N * N));
       if (e != cudaSuccess) return e;
     }
     for (int pc = 0; pc < 2; ++pc) {
       const void* fn = pc ? (const void*)k_dir32_bulk<N, true> : (const void*)k_dir32_bulk<N, false>;
+      const void* fnd = pc ? (const void*)k_dir32_bulk<N, true, true>
+                           : (const void*)k_dir32_bulk<N, false, true>;
       const size_t smem = pc ? Dir32Bulk<N, true>::SMEM : Dir32Bulk<N, false>::SMEM;
       cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fnd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       int occ = 0;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, Dir32Bulk<N, false>::THREADS,

@@ -312,6 +312,17 @@ __global__ void k_diag_nd(const double* __restrict__ lineop, double* __restrict_
   dinv32[t] = (float)di;
 }
 
+// h K at the volume points in FP32 from h w_q K (the FP32 cell kernel of the
+// point basis scales its collocation derivatives by sqrt(w) instead).
+__global__ void k_hk32(const double* __restrict__ kt, float* __restrict__ hk, long long ndofs,
+                       int n, const __grid_constant__ DGTab<double> tab) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ndofs) return;
+  const int qi = (int)(t % ((long long)n * n * n));
+  const int a = qi % n, b = (qi / n) % n, e = qi / (n * n);
+  hk[t] = (float)(kt[t] / (tab.w[a] * tab.w[b] * tab.w[e]));
+}
+
 template <int N>
 struct NodalF {
   template <typename T>
@@ -369,6 +380,8 @@ void dg_build_nodal_tables(const DGTab<double>& t, int n, DGTabN<double>* d, DGT
     d->isw[a] = isw;
     d->l0[a] = t.l0[a] * isw;
     d->l1[a] = t.l1[a] * isw;
+    d->dl0[a] = t.dl0[a] * isw;
+    d->dl1[a] = t.dl1[a] * isw;
     d->hdl0[a] = 0.5 * t.dl0[a] * isw;
     d->hdl1[a] = 0.5 * t.dl1[a] * isw;
   }
@@ -379,6 +392,8 @@ void dg_build_nodal_tables(const DGTab<double>& t, int n, DGTabN<double>* d, DGT
     f->isw[a] = (float)d->isw[a];
     f->l0[a] = (float)d->l0[a];
     f->l1[a] = (float)d->l1[a];
+    f->dl0[a] = (float)d->dl0[a];
+    f->dl1[a] = (float)d->dl1[a];
     f->hdl0[a] = (float)d->hdl0[a];
     f->hdl1[a] = (float)d->hdl1[a];
     for (int i = 0; i < n; ++i) f->Dh[a][i] = (float)d->Dh[a][i];
@@ -428,6 +443,17 @@ int dg_ensure_nodal_diag(dg_mesh* m, cudaStream_t s) {
   rc = run_nodal(4, m, nullptr, nullptr, nullptr, s, "nodal Jacobi diagonal");
   if (rc) return rc;
   m->has_nodal_diag = true;
+  return DG_OK;
+}
+
+int dg_ensure_nodal32(dg_mesh* m, cudaStream_t s) {
+  int rc = dg_ensure_nodal(m, s);
+  if (rc || m->has_nodal32) return rc;
+  if (m->hk32 == nullptr) DG_CUDA(cudaMalloc((void**)&m->hk32, (size_t)m->ndofs * sizeof(float)));
+  dgk::k_hk32<<<(unsigned)((m->ndofs + 255) / 256), 256, 0, s>>>(m->kt64, m->hk32, m->ndofs, m->n,
+                                                                 m->tab64);
+  DG_CUDA(cudaGetLastError());
+  m->has_nodal32 = true;
   return DG_OK;
 }
 

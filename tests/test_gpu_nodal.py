@@ -3,7 +3,7 @@
 dg_to_nodal / dg_to_modal against the oracle's Q and Q^T; dg_apply_nodal
 against the oracle's Q A Q^T element by element (1e-12, degrees 1-8, odd and
 one-cell meshes, both boundary conditions, and sampled cells of the 64^3 Q3
-benchmark mesh); the CG in that basis (DG_CG_NODAL) by its first iterates
+benchmark mesh); the CG in that basis (DG_CG_NODAL, FP64 and mixed) by its first iterates
 against the oracle's recurrence (M = I: the Legendre-basis iterates, since Q is
 orthogonal; Jacobi: the oracle's PCG on Q A Q^T with its diagonal) and by
 residuals that the oracle recomputes in the Legendre basis.
@@ -116,12 +116,15 @@ def test_apply_nodal_full_size_64cubed_q3_sampled_cells(dg):
     assert relmax(y[cells], ref) <= TOL64
 
 
-@pytest.mark.parametrize("N,k", [(4, 3), (3, 2), (3, 4), (2, 6)])
+@pytest.mark.parametrize("N,k", [(4, 3), (3, 2), (3, 4), (2, 6), (3, 1), (2, 8)])
 @pytest.mark.parametrize("precond", [None, "jacobi"])
-def test_nodal_cg_first_iterates_match_oracle_recurrence(dg, N, k, precond):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_nodal_cg_first_iterates_match_oracle_recurrence(dg, N, k, precond, mode):
     """Three CG iterations from x = 0.  M = I: Q is orthogonal, so x_3 equals
     the Legendre-basis CG iterate.  Jacobi: the oracle's PCG on Q A Q^T with
-    M = diag(Q A Q^T), mapped back with Q^T."""
+    M = diag(Q A Q^T), mapped back with Q^T.  The mixed mode runs the FP32
+    point-basis kernels (tolerance 1e-4 from FP32 rounding), the FP64 mode the
+    FP64 ones (1e-10)."""
     import torch
     D = SIPG(N, k)
     K = field(N, k, 41)
@@ -134,22 +137,24 @@ def test_nodal_cg_first_iterates_match_oracle_recurrence(dg, N, k, precond):
         xref = D.from_collocation(xh)
     m = mesh(dg, N, k, K)
     x, st = m.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-14, maxit=3, precond=precond,
-                       nodal=True, raise_on_error=False)
+                       mode=mode, nodal=True, raise_on_error=False)
     assert st["iterations"] == 3, st
     assert st["status"] == dg.DG_ERR_NOT_CONVERGED
-    assert relmax(x.cpu().numpy(), xref) <= 1e-10
+    assert relmax(x.cpu().numpy(), xref) <= (1e-10 if mode == 0 else 1e-4)
 
 
 @pytest.mark.parametrize("N,k,seed,bc", [(4, 3, 5, "dirichlet"), (5, 2, 6, "dirichlet"),
                                          (3, 4, 4, "dirichlet"), (4, 2, 7, "flow_x")])
 @pytest.mark.parametrize("precond", [None, "jacobi"])
-def test_nodal_cg_residual_checked_by_oracle(dg, N, k, seed, bc, precond):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_nodal_cg_residual_checked_by_oracle(dg, N, k, seed, bc, precond, mode):
     import torch
     D = SIPG(N, k, bc=bc)
     K = field(N, k, seed)
     b = inputs.constant_load_vector(N, k)
     m = mesh(dg, N, k, K, bc)
-    x, st = m.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-10, precond=precond, nodal=True)
+    x, st = m.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-10, precond=precond, mode=mode,
+                       nodal=True)
     x = x.cpu().numpy()
     assert st["status"] == 0
     assert st["rel_residual"] <= 1e-10
@@ -175,17 +180,18 @@ def test_nodal_cg_initial_guess_zero_rhs_and_rejected_modes(dg):
     z = torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda")
     x, st = m.cg_solve(z.clone(), x=torch.ones_like(z), rtol=1e-10, nodal=True)
     assert st["status"] == 0 and torch.count_nonzero(x).item() == 0
-    for mode in (dg.DG_CG_MIXED_IR, dg.DG_CG_MIXED_IR_RESTART):
-        with pytest.raises(dg.DGError, match="INVALID_ARG"):
-            m.cg_solve(torch.from_numpy(b).cuda(), mode=mode, nodal=True)
     with pytest.raises(dg.DGError, match="INVALID_ARG"):
-        m.cg_solve(torch.from_numpy(b).cuda(), precond="kron", nodal=True)
+        m.cg_solve(torch.from_numpy(b).cuda(), mode=dg.DG_CG_MIXED_IR_RESTART, nodal=True)
+    with pytest.raises(dg.DGError, match="INVALID_ARG"):
+        m.cg_solve(torch.from_numpy(b).cuda(), precond="block", nodal=True)
 
 
 def test_nodal_cg_first_iterates_full_size_48cubed_q4(dg):
     """The CG workload (48^3 Q4, lognormal K seed 4) in the benchmark's
-    configuration: three iterations in the point basis, every DOF against the
-    oracle's Legendre-basis recurrence."""
+    configuration: three iterations in the point basis, FP64 and mixed (the
+    FP32 point-basis kernels at full size, bulk-copy direction kernel in its
+    persistent grid), every DOF against the oracle's Legendre-basis
+    recurrence."""
     import torch
     N, k = 48, 4
     K = inputs.lognormal_coefficient(N, k, seed=4)
@@ -193,7 +199,8 @@ def test_nodal_cg_first_iterates_full_size_48cubed_q4(dg):
     D = SIPG(N, k)
     xref, _, _, _ = cg(lambda v: D.apply(K, v), b, rtol=1e-14, maxit=3)
     m = mesh(dg, N, k, K)
-    x, st = m.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-14, maxit=3, nodal=True,
-                       raise_on_error=False)
-    assert st["iterations"] == 3, st
-    assert relmax(x.cpu().numpy(), xref) <= 1e-10
+    for mode, tol in ((0, 1e-10), (1, 1e-4)):
+        x, st = m.cg_solve(torch.from_numpy(b).cuda(), rtol=1e-14, maxit=3, mode=mode,
+                           nodal=True, raise_on_error=False)
+        assert st["iterations"] == 3, st
+        assert relmax(x.cpu().numpy(), xref) <= tol
