@@ -315,8 +315,13 @@ int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, const double* c
 /* dg_cg_solve_batched with a mode: DG_CG_FP64 (the same as
  * dg_cg_solve_batched) or DG_CG_FP64 | DG_CG_PRECOND_JACOBI, every sample then
  * running Section 2.4's PCG with M = diag(A_s) (formed per mesh as by
- * dg_diagonal, cached until its next dg_set_coefficient).  Other modes:
- * INVALID_ARG.  Everything else as dg_cg_solve_batched. */
+ * dg_diagonal, cached until its next dg_set_coefficient), or
+ * DG_CG_FP64 | DG_CG_NODAL: every sample's CG (M = I) in the scaled
+ * Gauss-point basis of dg_to_nodal (b and x mapped per sample, the persistent
+ * kernel on the transform-free passes, x mapped back, the residual recomputed
+ * in the Legendre basis and a sample left above rtol by the mapping's
+ * rounding finished by dg_cg_solve).  Other modes: INVALID_ARG.  Everything
+ * else as dg_cg_solve_batched. */
 int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count, const double* const* b,
                              double* const* x, double rtol, int maxit, int mode,
                              dg_cg_stats* st, void* stream);

@@ -451,12 +451,16 @@ class Mesh:
 
 
 def cg_solve_batched(meshes, bs, xs, rtol: float = 1e-8, maxit: int = 100000, stream=None,
-                     raise_on_error: bool = True, precond: str | None = None):
+                     raise_on_error: bool = True, precond: str | None = None,
+                     nodal: bool = False):
     """Solve meshes[s] x[s] = b[s] for all s in one lock-step batched solve
-    (FP64).  precond: None or "jacobi" (PCG with M = diag(A_s))."""
+    (FP64).  precond: None or "jacobi" (PCG with M = diag(A_s)).  nodal:
+    iterate in the scaled Gauss-point basis (M = I only)."""
     if precond not in (None, "jacobi"):
         raise ValueError(f"unknown preconditioner {precond!r}")
     mode = DG_CG_FP64 | (DG_CG_PRECOND_JACOBI if precond == "jacobi" else 0)
+    if nodal:
+        mode |= DG_CG_NODAL
     count = len(meshes)
     if not (len(bs) == len(xs) == count):
         raise ValueError("meshes, bs and xs must have the same length")

@@ -49,7 +49,7 @@
 #include <string>
 #include <vector>
 
-#include "dg_apply_impl.cuh"
+#include "dg_nodal_impl.cuh"
 
 namespace {
 
@@ -59,6 +59,7 @@ constexpr double LAUNCH_SECONDS = 2.0;   // work per production launch (estimate
 constexpr double EST_DOF_RATE = 7.0e9;   // DOF-iterations per second for that estimate
 
 __constant__ DGTab<double> c_btab[DG_MAXN - 1];  // tables for n = 2..9
+__constant__ DGTabN<double> c_btabN[DG_MAXN - 1];  // scaled Gauss-point basis, n = 2..9
 
 struct SampleDev {
   const double* b;
@@ -67,7 +68,8 @@ struct SampleDev {
   double *U, *X, *TR;
   const double* kt;      // h w K (not read: the line operators hold the volume term)
   const double* fw;
-  const double* lineop;
+  const double* lineop;  // line operators of A, or of Q A Q^T in the scaled Gauss-point basis
+  const double* gh;      // h gamma per face side (the point basis's face weights)
   const double* dinv;  // 1 / diag(A) for M = diag(A); nullptr for M = I
   long long ncells;
   int Nc;          // cells per direction
@@ -141,54 +143,62 @@ __host__ __device__ constexpr int group_cells(int n) {
        : n == 8 ? dgk::Cfg<8>::CPB : dgk::Cfg<9>::CPB;
 }
 
-template <int N>
+// ND: the samples' vectors are in the scaled Gauss-point basis (DG_CG_NODAL)
+// and the passes are the transform-free ones of dg_nodal_impl.cuh.
+template <int N, bool ND>
 __device__ __forceinline__ void group_pass1(const SampleDev& S, long long c0, int nblk,
                                             double* smem) {
-  dgk::trace_cells<N, double>(S.u, S.U, S.X, S.TR, c0, nblk, c_btab[N - 2], smem);
+  if constexpr (ND)
+    dgk::trace_cells_nd<N, double>(S.u, S.TR, c0, nblk, c_btabN[N - 2], smem);
+  else
+    dgk::trace_cells<N, double>(S.u, S.U, S.X, S.TR, c0, nblk, c_btab[N - 2], smem);
 }
-template <int N>
+template <int N, bool ND>
 __device__ __forceinline__ void group_pass2(const SampleDev& S, long long c0, int nblk,
                                             double* smem) {
-  dgk::cell_cells<N, double, true>(S.U, S.X, S.TR, S.kt, S.fw, S.w, c0, nblk, S.Nc,
-                                   c_btab[N - 2], smem, S.lineop);
+  if constexpr (ND)
+    dgk::cell_cells_nd<N>(S.u, S.TR, S.lineop, S.gh, S.w, c0, nblk, S.Nc, c_btabN[N - 2], smem);
+  else
+    dgk::cell_cells<N, double, true>(S.U, S.X, S.TR, S.kt, S.fw, S.w, c0, nblk, S.Nc,
+                                     c_btab[N - 2], smem, S.lineop);
 }
 
-template <int MAXN>
+template <int MAXN, bool ND>
 __device__ __forceinline__ void pass1_dispatch(const SampleDev& sd, long long c, int nblk,
                                                double* smem) {
   switch (sd.n) {
-    case 2: group_pass1<2>(sd, c, nblk, smem); break;
-    case 3: group_pass1<3>(sd, c, nblk, smem); break;
-    case 4: group_pass1<4>(sd, c, nblk, smem); break;
-    case 5: group_pass1<5>(sd, c, nblk, smem); break;
+    case 2: group_pass1<2, ND>(sd, c, nblk, smem); break;
+    case 3: group_pass1<3, ND>(sd, c, nblk, smem); break;
+    case 4: group_pass1<4, ND>(sd, c, nblk, smem); break;
+    case 5: group_pass1<5, ND>(sd, c, nblk, smem); break;
     default:
       if constexpr (MAXN > 5) {
         switch (sd.n) {
-          case 6: group_pass1<6>(sd, c, nblk, smem); break;
-          case 7: group_pass1<7>(sd, c, nblk, smem); break;
-          case 8: group_pass1<8>(sd, c, nblk, smem); break;
-          default: group_pass1<9>(sd, c, nblk, smem); break;
+          case 6: group_pass1<6, ND>(sd, c, nblk, smem); break;
+          case 7: group_pass1<7, ND>(sd, c, nblk, smem); break;
+          case 8: group_pass1<8, ND>(sd, c, nblk, smem); break;
+          default: group_pass1<9, ND>(sd, c, nblk, smem); break;
         }
       }
       break;
   }
 }
 
-template <int MAXN>
+template <int MAXN, bool ND>
 __device__ __forceinline__ void pass2_dispatch(const SampleDev& sd, long long c, int nblk,
                                                double* smem) {
   switch (sd.n) {
-    case 2: group_pass2<2>(sd, c, nblk, smem); break;
-    case 3: group_pass2<3>(sd, c, nblk, smem); break;
-    case 4: group_pass2<4>(sd, c, nblk, smem); break;
-    case 5: group_pass2<5>(sd, c, nblk, smem); break;
+    case 2: group_pass2<2, ND>(sd, c, nblk, smem); break;
+    case 3: group_pass2<3, ND>(sd, c, nblk, smem); break;
+    case 4: group_pass2<4, ND>(sd, c, nblk, smem); break;
+    case 5: group_pass2<5, ND>(sd, c, nblk, smem); break;
     default:
       if constexpr (MAXN > 5) {
         switch (sd.n) {
-          case 6: group_pass2<6>(sd, c, nblk, smem); break;
-          case 7: group_pass2<7>(sd, c, nblk, smem); break;
-          case 8: group_pass2<8>(sd, c, nblk, smem); break;
-          default: group_pass2<9>(sd, c, nblk, smem); break;
+          case 6: group_pass2<6, ND>(sd, c, nblk, smem); break;
+          case 7: group_pass2<7, ND>(sd, c, nblk, smem); break;
+          case 8: group_pass2<8, ND>(sd, c, nblk, smem); break;
+          default: group_pass2<9, ND>(sd, c, nblk, smem); break;
         }
       }
       break;
@@ -197,7 +207,7 @@ __device__ __forceinline__ void pass2_dispatch(const SampleDev& sd, long long c,
 
 // One persistent launch of up to `iters` lock-step iterations over every
 // unfinished sample.  `tile`: cell groups per work unit.
-template <int BT, int MAXN>
+template <int BT, int MAXN, bool ND>
 __global__ void __launch_bounds__(BT, BT == 128 ? 6 : 3)
 kb_persistent(const SampleDev* __restrict__ S, const int2* __restrict__ units, int nu, int tile,
               BState* st, double* part, unsigned* tickets, BCtl* ctl, int iters, long long limit,
@@ -245,7 +255,7 @@ kb_persistent(const SampleDev* __restrict__ S, const int2* __restrict__ units, i
       __syncthreads();
       for (long long c = c0; c < c1; c += cpb) {
         const int nblk = (int)((c1 - c) < cpb ? (c1 - c) : cpb);
-        pass1_dispatch<MAXN>(sd, c, nblk, smem);
+        pass1_dispatch<MAXN, ND>(sd, c, nblk, smem);
         __syncthreads();
       }
     }
@@ -261,7 +271,7 @@ kb_persistent(const SampleDev* __restrict__ S, const int2* __restrict__ units, i
                                                                     : sd.ncells;
       for (long long c = c0; c < c1; c += cpb) {
         const int nblk = (int)((c1 - c) < cpb ? (c1 - c) : cpb);
-        pass2_dispatch<MAXN>(sd, c, nblk, smem);
+        pass2_dispatch<MAXN, ND>(sd, c, nblk, smem);
         __syncthreads();
       }
       const long long n3 = (long long)sd.n * sd.n * sd.n;
@@ -450,8 +460,22 @@ kb_residual(const double* __restrict__ b, const double* __restrict__ q, long lon
   }
 }
 
-template <int MAXN>
+template <int MAXN, bool ND>
 size_t persistent_smem() {
+  if constexpr (ND) {  // the point basis's passes need half the shared memory
+    size_t m = 0;
+    m = std::max(m, dgk::cell_smem_nd<2>());
+    m = std::max(m, dgk::cell_smem_nd<3>());
+    m = std::max(m, dgk::cell_smem_nd<4>());
+    m = std::max(m, dgk::cell_smem_nd<5>());
+    if (MAXN > 5) {
+      m = std::max(m, dgk::cell_smem_nd<6>());
+      m = std::max(m, dgk::cell_smem_nd<7>());
+      m = std::max(m, dgk::cell_smem_nd<8>());
+      m = std::max(m, dgk::cell_smem_nd<9>());
+    }
+    return m;
+  }
   size_t m = 0;
   m = std::max(m, dgk::cell_smem<2, double>());
   m = std::max(m, dgk::cell_smem<3, double>());
@@ -532,20 +556,20 @@ struct Batch {
   }
 };
 
-template <int BT, int MAXN>
+template <int BT, int MAXN, bool ND>
 int launch_persistent(Batch& B, int count, int tsel, int blocks, int iters, long long limit,
                       int stall, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(BT);
-  cfg.dynamicSmemBytes = persistent_smem<MAXN>();
+  cfg.dynamicSmemBytes = persistent_smem<MAXN, ND>();
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  DG_CUDA(cudaLaunchKernelEx(&cfg, kb_persistent<BT, MAXN>,
+  DG_CUDA(cudaLaunchKernelEx(&cfg, kb_persistent<BT, MAXN, ND>,
                              (const SampleDev*)(B.d_samples + (size_t)tsel * count),
                              (const int2*)(B.d_units + B.unit_off[tsel]), B.nunits[tsel],
                              TILES[tsel], B.d_state, B.d_part, B.d_tickets, B.d_ctl, iters,
@@ -569,7 +593,7 @@ int start_sample(Batch& B, const SampleDev& d, dg_mesh* m, const double* b, cons
   return DG_OK;
 }
 
-template <int BT, int MAXN>
+template <int BT, int MAXN, bool ND>
 int solve_batched(const dg_mesh* const* meshes, int count, const double* const* b,
                   double* const* x, double rtol, int maxit, bool jacobi, int mode,
                   dg_cg_stats* st, void* stream) {
@@ -599,7 +623,8 @@ int solve_batched(const dg_mesh* const* meshes, int count, const double* const* 
     d.TR = m->TR64;
     d.kt = m->kt64;
     d.fw = m->fw64;
-    d.lineop = m->lineop64;
+    d.lineop = ND ? m->lineopN64 : m->lineop64;
+    d.gh = m->gh64;
     d.dinv = nullptr;
     if (jacobi) {
       rc = dg_ensure_diagonal(m, m->solve_stream);
@@ -653,12 +678,18 @@ int solve_batched(const dg_mesh* const* meshes, int count, const double* const* 
     DGTab<float> t32;
     for (int n = 2; n <= DG_MAXN; ++n) dg_build_tables(n, 2.0 * n * n, &t64[n - 2], &t32);
     DG_CUDA(cudaMemcpyToSymbolAsync(c_btab, t64, sizeof(t64), 0, cudaMemcpyHostToDevice, s));
+    if (ND) {
+      DGTabN<double> tn64[DG_MAXN - 1];
+      DGTabN<float> tn32;
+      for (int n = 2; n <= DG_MAXN; ++n) dg_build_nodal_tables(t64[n - 2], n, &tn64[n - 2], &tn32);
+      DG_CUDA(cudaMemcpyToSymbolAsync(c_btabN, tn64, sizeof(tn64), 0, cudaMemcpyHostToDevice, s));
+    }
   }
-  const size_t smem = persistent_smem<MAXN>();
-  DG_CUDA(cudaFuncSetAttribute(kb_persistent<BT, MAXN>,
+  const size_t smem = persistent_smem<MAXN, ND>();
+  DG_CUDA(cudaFuncSetAttribute(kb_persistent<BT, MAXN, ND>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int max_bpsm = 0;
-  DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_bpsm, kb_persistent<BT, MAXN>, BT,
+  DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_bpsm, kb_persistent<BT, MAXN, ND>, BT,
                                                         smem));
   if (max_bpsm < 1)
     return dg_fail(DG_ERR_CUDA, "dg_cg_solve_batched: persistent kernel cannot be resident");
@@ -746,7 +777,8 @@ int solve_batched(const dg_mesh* const* meshes, int count, const double* const* 
         cudaGraph_t g = nullptr;
         cudaGraphExec_t ex = nullptr;
         DG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        int rc = launch_persistent<BT, MAXN>(B, count, cands[ci].second, cands[ci].first * sms,
+        int rc = launch_persistent<BT, MAXN, ND>(B, count, cands[ci].second,
+                                                 cands[ci].first * sms,
                                              tune ? ITERS_TUNE : iters_launch, limit, stall, s);
         cudaError_t ec = cudaStreamEndCapture(s, &g);
         if (rc) {
@@ -864,15 +896,89 @@ int solve_batched(const dg_mesh* const* meshes, int count, const double* const* 
   return first_bad;
 }
 
+// The batch in the scaled Gauss-point basis (DG_CG_NODAL, M = I): every
+// sample's b and x mapped into the basis, the lock-step solve on Q A Q^T with
+// the transform-free passes, x mapped back, and the residual recomputed in the
+// Legendre basis; a sample that the mapping's rounding left above rtol is
+// finished by the one-sample FP64 CG from its x.
+int solve_batched_nodal(const dg_mesh* const* meshes, int count, const double* const* b,
+                        double* const* x, double rtol, int maxit, int maxn, int mode,
+                        dg_cg_stats* st, void* stream) {
+  cudaStream_t us = (cudaStream_t)stream;
+  std::vector<const double*> bn(count);
+  std::vector<double*> xn(count);
+  for (int i = 0; i < count; ++i) {
+    dg_mesh* m = const_cast<dg_mesh*>(meshes[i]);
+    int rc = dg_ensure_solver_ws(m);
+    if (rc == DG_OK) rc = dg_ensure_nodal(m, us);
+    if (rc == DG_OK) rc = dg_launch_collocation(m, b[i], m->bN64, true, us);
+    if (rc == DG_OK) rc = dg_launch_collocation(m, x[i], m->xN64, true, us);
+    if (rc) return rc;
+    bn[i] = m->bN64;
+    xn[i] = m->xN64;
+  }
+  std::vector<dg_cg_stats> local(st ? 0 : count);
+  dg_cg_stats* sts = st ? st : local.data();
+  int rc;
+  {
+    struct Scope {  // the internal FP64 launcher applies Q A Q^T while it lives
+      const dg_mesh* const* ms;
+      int n;
+      Scope(const dg_mesh* const* a, int c) : ms(a), n(c) {
+        for (int i = 0; i < n; ++i) const_cast<dg_mesh*>(ms[i])->nodal_op = true;
+      }
+      ~Scope() {
+        for (int i = 0; i < n; ++i) const_cast<dg_mesh*>(ms[i])->nodal_op = false;
+      }
+    } scope(meshes, count);
+    rc = maxn <= 5 ? solve_batched<128, 5, true>(meshes, count, bn.data(), xn.data(), rtol, maxit,
+                                                 false, mode, sts, stream)
+                   : solve_batched<256, DG_MAXN, true>(meshes, count, bn.data(), xn.data(), rtol,
+                                                       maxit, false, mode, sts, stream);
+  }
+  if (rc != DG_OK && rc != DG_ERR_NOT_CONVERGED && rc != DG_ERR_BREAKDOWN) return rc;
+  for (int i = 0; i < count; ++i) {
+    dg_mesh* m = const_cast<dg_mesh*>(meshes[i]);
+    int r2 = dg_launch_collocation(m, xn[i], x[i], false, us);
+    if (r2) return r2;
+    r2 = dg_launch_apply_f64(m, x[i], m->q64, nullptr, us);
+    if (r2) return r2;
+    kb_residual<<<1, 256, 0, us>>>(b[i], m->q64, m->ndofs, m->partials);
+    double out[2];
+    DG_CUDA(cudaMemcpyAsync(out, m->partials, sizeof(out), cudaMemcpyDeviceToHost, us));
+    DG_CUDA(cudaStreamSynchronize(us));
+    const double rel = out[1] > 0 ? std::sqrt(out[0] / out[1]) : 0.0;
+    sts[i].rel_residual = sts[i].rel_residual_rec = rel;
+    if (sts[i].status == DG_OK && rel > rtol) {
+      dg_cg_stats ps{};
+      const int left = maxit - sts[i].iterations;
+      const int prc = left >= 1 ? dg_cg_solve(m, b[i], x[i], rtol, left, DG_CG_FP64, &ps, stream)
+                                : DG_ERR_NOT_CONVERGED;
+      sts[i].iterations += ps.iterations;
+      sts[i].outer_iterations += 1;
+      if (left >= 1) sts[i].rel_residual = sts[i].rel_residual_rec = ps.rel_residual;
+      sts[i].status = prc;
+      if (prc != DG_OK && rc == DG_OK) {
+        rc = prc;
+        dg_fail(prc, "dg_cg_solve_batched: sample %d: not converged after the point-basis "
+                     "solve (relative residual %.3e)", i, sts[i].rel_residual);
+      }
+    }
+  }
+  return rc;
+}
+
 }  // namespace
 
 extern "C" int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count,
                                         const double* const* b, double* const* x, double rtol,
                                         int maxit, int mode, dg_cg_stats* st, void* stream) {
-  if (mode != DG_CG_FP64 && mode != (DG_CG_FP64 | DG_CG_PRECOND_JACOBI))
+  const bool nodal = (mode & DG_CG_NODAL) != 0;
+  if (mode != DG_CG_FP64 && mode != (DG_CG_FP64 | DG_CG_PRECOND_JACOBI) &&
+      mode != (DG_CG_FP64 | DG_CG_NODAL))
     return dg_fail(DG_ERR_INVALID_ARG,
-                   "dg_cg_solve_batched: mode %d; the batched solver runs DG_CG_FP64, with or "
-                   "without DG_CG_PRECOND_JACOBI", mode);
+                   "dg_cg_solve_batched: mode %d; the batched solver runs DG_CG_FP64, with "
+                   "DG_CG_PRECOND_JACOBI or with DG_CG_NODAL", mode);
   const bool jacobi = (mode & DG_CG_PRECOND_JACOBI) != 0;
   if (meshes == nullptr || b == nullptr || x == nullptr || count < 1)
     return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve_batched: NULL array or count < 1");
@@ -901,9 +1007,12 @@ extern "C" int dg_cg_solve_batched_mode(const dg_mesh* const* meshes, int count,
                        s);
     maxn = m->n > maxn ? m->n : maxn;
   }
+  if (nodal) return solve_batched_nodal(meshes, count, b, x, rtol, maxit, maxn, mode, st, stream);
   if (maxn <= 5)
-    return solve_batched<128, 5>(meshes, count, b, x, rtol, maxit, jacobi, mode, st, stream);
-  return solve_batched<256, DG_MAXN>(meshes, count, b, x, rtol, maxit, jacobi, mode, st, stream);
+    return solve_batched<128, 5, false>(meshes, count, b, x, rtol, maxit, jacobi, mode, st,
+                                        stream);
+  return solve_batched<256, DG_MAXN, false>(meshes, count, b, x, rtol, maxit, jacobi, mode, st,
+                                            stream);
 }
 
 extern "C" int dg_cg_solve_batched(const dg_mesh* const* meshes, int count, const double* const* b,

@@ -204,3 +204,53 @@ def test_nodal_cg_first_iterates_full_size_48cubed_q4(dg):
                            nodal=True, raise_on_error=False)
         assert st["iterations"] == 3, st
         assert relmax(x.cpu().numpy(), xref) <= tol
+
+
+# uneven levels: sizes and degrees differ inside one batch
+BATCH_LEVELS = [(4, 1), (4, 2), (3, 3), (3, 4), (5, 2), (2, 4)]
+
+
+def make_batch(dg, levels, seed0):
+    import torch
+    meshes, bs, xs, Ks = [], [], [], []
+    for s, (N, k) in enumerate(levels):
+        K = field(N, k, seed0 + s)
+        meshes.append(mesh(dg, N, k, K))
+        Ks.append(K)
+        bs.append(torch.from_numpy(inputs.uniform_vector(N, k, seed0 + 1000 + s)).cuda())
+        xs.append(torch.zeros(meshes[-1].n_dofs, dtype=torch.float64, device="cuda"))
+    return meshes, bs, xs, Ks
+
+
+@pytest.mark.parametrize("levels", [BATCH_LEVELS, [(3, 2), (2, 5), (2, 7)]])
+def test_batched_nodal_matches_oracle_and_single_sample_solves(dg, levels):
+    """The lock-step batched CG in the point basis (both kernel widths): every
+    sample's residual recomputed by the oracle in the Legendre basis, the
+    iteration count of a one-sample FP64 CG (the same iterates in exact
+    arithmetic) and the same solution."""
+    meshes, bs, xs, Ks = make_batch(dg, levels, 3000)
+    stats = dg.cg_solve_batched(meshes, bs, xs, rtol=1e-10, nodal=True)
+    for s, ((N, k), m, b, x, K, st) in enumerate(zip(levels, meshes, bs, xs, Ks, stats)):
+        assert st["status"] == 0, (s, st)
+        bn = b.cpu().numpy()
+        r = np.linalg.norm(bn - SIPG(N, k).apply(K, x.cpu().numpy())) / np.linalg.norm(bn)
+        assert r <= 1.05e-10, (s, r)
+        xseq, sst = m.cg_solve(b, rtol=1e-10)
+        assert abs(st["iterations"] - sst["iterations"]) <= max(3, sst["iterations"] // 20)
+        assert float((x - xseq).norm() / xseq.norm()) <= 1e-6
+
+
+def test_batched_nodal_zero_rhs_initial_guess_and_rejected_mode(dg):
+    import torch
+    meshes, bs, xs, Ks = make_batch(dg, [(3, 2), (2, 3)], 3100)
+    bs[1].zero_()
+    xs[1].fill_(1.0)
+    xs[0].copy_(torch.from_numpy(inputs.uniform_vector(3, 2, 3101)).cuda())
+    stats = dg.cg_solve_batched(meshes, bs, xs, rtol=1e-10, nodal=True)
+    assert all(st["status"] == 0 for st in stats)
+    assert torch.count_nonzero(xs[1]).item() == 0
+    bn = bs[0].cpu().numpy()
+    r = np.linalg.norm(bn - SIPG(3, 2).apply(Ks[0], xs[0].cpu().numpy())) / np.linalg.norm(bn)
+    assert r <= 1.05e-10
+    with pytest.raises(dg.DGError, match="INVALID_ARG"):
+        dg.cg_solve_batched(meshes, bs, xs, rtol=1e-10, nodal=True, precond="jacobi")
