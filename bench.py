@@ -371,7 +371,11 @@ def run_cg(world, modes=None):
                       ("mixed_ir_kron", dg.DG_CG_MIXED_IR | dg.DG_CG_PRECOND_KRON),
                       ("fp64_kron", dg.DG_CG_FP64 | dg.DG_CG_PRECOND_KRON),
                       ("fp64_nodal", dg.DG_CG_FP64 | dg.DG_CG_NODAL),
-                      ("mixed_ir_nodal", dg.DG_CG_MIXED_IR | dg.DG_CG_NODAL))
+                      ("mixed_ir_nodal", dg.DG_CG_MIXED_IR | dg.DG_CG_NODAL),
+                      ("fp64_nodal_kron",
+                       dg.DG_CG_FP64 | dg.DG_CG_NODAL | dg.DG_CG_PRECOND_KRON),
+                      ("mixed_ir_nodal_kron",
+                       dg.DG_CG_MIXED_IR | dg.DG_CG_NODAL | dg.DG_CG_PRECOND_KRON))
     for name, mode in modes:
         if mode & (dg.DG_CG_PRECOND_JACOBI | dg.DG_CG_PRECOND_KRON | dg.DG_CG_NODAL):
             # drops the cached preconditioner and basis data: the solve forms them

@@ -210,21 +210,24 @@ int dg_coeff_grad(const dg_mesh* mesh, const double* u, const double* v, double*
  *   first such solve after dg_set_coefficient (any degree); BREAKDOWN if a 1D
  *   factor has a negative eigenvalue (a direction with only zero-flux faces,
  *   one cell across, has a singular factor, which is allowed).
- * DG_CG_FP64 or DG_CG_MIXED_IR | DG_CG_NODAL (with or without
- *   DG_CG_PRECOND_JACOBI): the same CG run on (Q A Q^T) x_hat = Q b in the
+ * DG_CG_FP64 or DG_CG_MIXED_IR | DG_CG_NODAL (M = I, DG_CG_PRECOND_JACOBI or
+ *   DG_CG_PRECOND_KRON): the same CG run on (Q A Q^T) x_hat = Q b in the
  *   scaled Gauss-point basis of dg_to_nodal, the FP32 operator of the mixed
- *   mode and its FP64 refinements included.  Q is orthogonal, so without a
- *   preconditioner the iterates are Q times those of the Legendre-basis CG
- *   (in exact arithmetic); each operator application skips the six 1D basis
- *   transforms per cell.  With
- *   DG_CG_PRECOND_JACOBI the diagonal is that of Q A Q^T (a different
- *   preconditioner from diag(A)).  b and x are mapped once into the basis and
- *   x back once; the returned residual is recomputed in the Legendre basis,
- *   and if the mapping's rounding left it above rtol, plain FP64 CG iterations
- *   from x finish the solve (counted in iterations).  Formed on the first such
- *   solve after dg_set_coefficient: the line operators of Q A Q^T (as many
- *   values as dg_set_coefficient's, ~7.5 doubles per DOF at degree 3), two
- *   solve vectors and, for the mixed mode, h K at the points in FP32.  Cube
+ *   mode and its FP64 refinements included.  Q is orthogonal, so with M = I
+ *   the iterates are Q times those of the Legendre-basis CG (in exact
+ *   arithmetic), and so they are with the Kronecker cell blocks, whose
+ *   eigenbases are rotated into the basis (Q M Q^T); each operator
+ *   application skips the six 1D basis transforms per cell.  With
+ *   DG_CG_PRECOND_JACOBI the diagonal is that of Q A Q^T (a different, and
+ *   measured weaker, preconditioner than diag(A)).  b and x are mapped once
+ *   into the basis and x back once; the returned residual is recomputed in
+ *   the Legendre basis, and if the mapping's rounding left it above rtol, the
+ *   same solver (precision and preconditioner) continues from x in the
+ *   Legendre basis (its iterations counted in iterations, one more outer
+ *   iteration).  Formed on the first such solve after dg_set_coefficient: the
+ *   line operators of Q A Q^T (as many values as dg_set_coefficient's, ~7.5
+ *   doubles per DOF at degree 3), two solve vectors, for the mixed mode h K at
+ *   the points in FP32, for the Kronecker blocks the rotated factors.  Cube
  *   meshes only.
  * Stops when ||b - A x|| <= rtol ||b|| recomputed in FP64.  Blocking.
  * Returns NOT_CONVERGED at maxit (x holds the last iterate), BREAKDOWN on

@@ -1238,11 +1238,13 @@ struct NodalScope {
 // x = Q^T x_hat, then the residual in the Legendre basis.  The solve's own
 // stopping test is on ||b_hat - Q A Q^T x_hat|| = ||b - A x|| (Q orthogonal);
 // the mapping back rounds x, so if the Legendre-basis residual is still above
-// rtol, FP64 CG iterations (M = I) continue from x.
+// rtol, the same solver (precision and preconditioner) continues from x in the
+// Legendre basis.
 int cg_nodal(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_cg_stats* st,
-             bool jacobi, bool mixed, cudaStream_t s) {
+             bool jacobi, bool kron, bool mixed, cudaStream_t s) {
   int rc = jacobi ? dg_ensure_nodal_diag(m, s) : dg_ensure_nodal(m, s);
   if (rc == DG_OK && mixed) rc = dg_ensure_nodal32(m, s);
+  if (rc == DG_OK && kron) rc = dg_ensure_kron_nodal(m, s);
   if (rc) return rc;
   rc = dg_launch_collocation(m, b, m->bN64, true, s);
   if (rc == DG_OK) rc = dg_launch_collocation(m, x, m->xN64, true, s);
@@ -1250,8 +1252,8 @@ int cg_nodal(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_
   dg_cg_stats sn{};
   {
     NodalScope scope(m);
-    rc = mixed ? cg_mixed(m, m->bN64, m->xN64, rtol, maxit, &sn, jacobi, s)
-               : cg_fp64(m, m->bN64, m->xN64, rtol, maxit, &sn, jacobi, s);
+    rc = mixed ? cg_mixed(m, m->bN64, m->xN64, rtol, maxit, &sn, jacobi, s, kron)
+               : cg_fp64(m, m->bN64, m->xN64, rtol, maxit, &sn, jacobi, s, false, kron);
   }
   // x holds the last iterate also when the solve stopped early
   int rc2 = dg_launch_collocation(m, m->xN64, x, false, s);
@@ -1269,13 +1271,17 @@ int cg_nodal(dg_mesh* m, const double* b, double* x, double rtol, int maxit, dg_
   // up to the mapping's rounding) and x holds the last iterate
   if (rc != DG_OK) return rc;
   if (rel <= rtol) return DG_OK;
+  // finish in the Legendre basis with the same precision and preconditioner
+  // (a few iterations: only the mapping's rounding is left)
   dg_cg_stats sp{};
   const int left = maxit - sn.iterations;
   if (left < 1)
     return dg_fail(DG_ERR_NOT_CONVERGED,
                    "dg_cg_solve(nodal): relative residual %.3e > rtol %.3e after %d iterations",
                    rel, rtol, sn.iterations);
-  rc = cg_fp64(m, b, x, rtol, left, &sp, false, s);
+  if (jacobi && (rc = dg_ensure_diagonal(m, s))) return rc;
+  rc = mixed ? cg_mixed(m, b, x, rtol, left, &sp, jacobi, s, kron)
+             : cg_fp64(m, b, x, rtol, left, &sp, jacobi, s, false, kron);
   if (st) {
     st->iterations = sn.iterations + sp.iterations;
     st->outer_iterations = sn.outer_iterations + 1 + sp.outer_iterations;
@@ -1304,10 +1310,10 @@ extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double
                             DG_CG_NODAL);
   if (base != DG_CG_FP64 && base != DG_CG_MIXED_IR && base != DG_CG_MIXED_IR_RESTART)
     return dg_fail(DG_ERR_INVALID_ARG, "dg_cg_solve: unknown mode %d", mode);
-  if (nodal && (block || kron || base == DG_CG_MIXED_IR_RESTART))
+  if (nodal && (block || base == DG_CG_MIXED_IR_RESTART))
     return dg_fail(DG_ERR_INVALID_ARG,
-                   "dg_cg_solve: DG_CG_NODAL goes with DG_CG_FP64 or DG_CG_MIXED_IR, with or "
-                   "without DG_CG_PRECOND_JACOBI");
+                   "dg_cg_solve: DG_CG_NODAL goes with DG_CG_FP64 or DG_CG_MIXED_IR, with M = I, "
+                   "DG_CG_PRECOND_JACOBI or DG_CG_PRECOND_KRON");
   if (block && (jacobi || kron || base != DG_CG_FP64))
     return dg_fail(DG_ERR_INVALID_ARG,
                    "dg_cg_solve: DG_CG_PRECOND_BLOCK goes with DG_CG_FP64 only");
@@ -1333,7 +1339,7 @@ extern "C" int dg_cg_solve(const dg_mesh* mc, const double* b, double* x, double
   if (kron) rc = dg_ensure_kron(m, s);
   if (rc == DG_OK) {
     if (nodal)
-      rc = cg_nodal(m, b, x, rtol, maxit, st, jacobi, base == DG_CG_MIXED_IR, s);
+      rc = cg_nodal(m, b, x, rtol, maxit, st, jacobi, kron, base == DG_CG_MIXED_IR, s);
     else if (base == DG_CG_FP64)
       rc = cg_fp64(m, b, x, rtol, maxit, st, jacobi, s, block, kron);
     else if (base == DG_CG_MIXED_IR)

@@ -137,6 +137,11 @@ struct dg_mesh {
   double *bN64, *xN64;
   float* hk32;        // h K at the volume points (FP32 operator in that basis) [c][q]
   bool has_nodal32;
+  // the Kronecker cell blocks in that basis: eigenbases rotated by
+  // q = diag(sqrt(w)) B per direction, same layout as kron64 / kron32
+  double* kronN64;
+  float* kronN32;
+  bool has_kron_nodal;
   double* kbar;     // Kbar_c                          [c]
   int* dflag;       // device-side error flag of the setup kernels
 
@@ -256,6 +261,7 @@ int dg_ensure_block(dg_mesh* m, cudaStream_t s);
 // FP64 initialisation with p = z, FP32 mixed iteration)
 enum { DG_KRON_FP64 = 0, DG_KRON_FP64_INIT = 1, DG_KRON_FP32 = 2 };
 int dg_ensure_kron(dg_mesh* m, cudaStream_t s);
+int dg_ensure_kron_nodal(dg_mesh* m, cudaStream_t s);  // the same in the point basis
 int dg_launch_kron_apply(const dg_mesh* m, const void* r, void* z, void* p, int mode,
                          cudaStream_t s);
 int dg_launch_block_apply(const dg_mesh* m, const double* r, double* z, double* p, bool init,

@@ -317,6 +317,49 @@ k_kron_apply(const T* __restrict__ KD, const T* __restrict__ r, T* __restrict__ 
   kron_finish<NT, MODE>(part, partials, st, rd);
 }
 
+// The factors in the scaled Gauss-point basis: per cell and direction
+// Qhat = q Q with q[a][i] = sqrt(w_a) L_i(xi_a) (orthogonal), the eigenvalues
+// unchanged: Q M Q^T is again a Kronecker sum with these eigenbases.  One
+// thread per (cell, direction).
+template <int N>
+__global__ void k_kron_rotate(const double* __restrict__ K64, double* __restrict__ KN64,
+                              float* __restrict__ KN32, long long ncells,
+                              const __grid_constant__ DGTab<double> tab) {
+  constexpr int N2 = N * N, KS = 3 * N2 + 3 * N;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * ncells) return;
+  const long long c = t / 3;
+  const int d = (int)(t - 3 * c);
+  const double* Q = K64 + c * KS + d * N2;
+  double* Q64 = KN64 + c * KS + d * N2;
+  float* Q32 = KN32 + c * KS + d * N2;
+  for (int a = 0; a < N; ++a) {
+    const double sw = sqrt(tab.w[a]);
+    for (int j = 0; j < N; ++j) {
+      double acc = 0.0;
+      for (int i = 0; i < N; ++i) acc = fma(tab.B[a][i], Q[i * N + j], acc);
+      Q64[a * N + j] = sw * acc;
+      Q32[a * N + j] = (float)(sw * acc);
+    }
+  }
+  const double* L = K64 + c * KS + 3 * N2 + d * N;
+  for (int j = 0; j < N; ++j) {
+    KN64[c * KS + 3 * N2 + d * N + j] = L[j];
+    KN32[c * KS + 3 * N2 + d * N + j] = (float)L[j];
+  }
+}
+
+template <int N>
+struct KronRotateF {
+  template <typename T>
+  static cudaError_t run(dg_mesh* m, cudaStream_t s) {
+    const long long threads = 3 * m->ncells;
+    k_kron_rotate<N><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
+        m->kron64, m->kronN64, m->kronN32, m->ncells, m->tab64);
+    return cudaGetLastError();
+  }
+};
+
 template <int N>
 struct KronSetupF {
   template <typename T>
@@ -335,22 +378,25 @@ struct KronApplyF {
                          cudaStream_t s) {
     using K64 = KronCfg<N, double>;
     using K32 = KronCfg<N, float>;
+    // inside a solve in the scaled Gauss-point basis: the rotated factors
+    const double* f64 = m->nodal_op ? m->kronN64 : m->kron64;
+    const float* f32 = m->nodal_op ? m->kronN32 : m->kron32;
     const unsigned b64 = (unsigned)((m->ncells + K64::C - 1) / K64::C);
     const unsigned b32 = (unsigned)((m->ncells + K32::C - 1) / K32::C);
     switch (mode) {
       case DG_KRON_FP64:
         k_kron_apply<N, double, 0><<<b64, K64::THREADS, 0, s>>>(
-            m->kron64, (const double*)r, (double*)z, nullptr, m->ncells, m->partials_cells,
+            f64, (const double*)r, (double*)z, nullptr, m->ncells, m->partials_cells,
             m->state);
         break;
       case DG_KRON_FP64_INIT:
         k_kron_apply<N, double, 1><<<b64, K64::THREADS, 0, s>>>(
-            m->kron64, (const double*)r, (double*)z, (double*)p, m->ncells, m->partials_cells,
+            f64, (const double*)r, (double*)z, (double*)p, m->ncells, m->partials_cells,
             m->state);
         break;
       default:
         k_kron_apply<N, float, 2><<<b32, K32::THREADS, 0, s>>>(
-            m->kron32, (const float*)r, (float*)z, nullptr, m->ncells, m->partials_cells,
+            f32, (const float*)r, (float*)z, nullptr, m->ncells, m->partials_cells,
             m->state);
         break;
     }
@@ -380,6 +426,22 @@ int dg_ensure_kron(dg_mesh* m, cudaStream_t s) {
     return dg_fail(DG_ERR_BREAKDOWN,
                    "Kronecker cell blocks: a 1D factor has a negative eigenvalue");
   m->has_kron = true;
+  return DG_OK;
+}
+
+int dg_ensure_kron_nodal(dg_mesh* m, cudaStream_t s) {
+  int rc = dg_ensure_kron(m, s);
+  if (rc || m->has_kron_nodal) return rc;
+  const size_t KS = (size_t)(3 * m->n * m->n + 3 * m->n);
+  if (m->kronN64 == nullptr) {
+    cudaError_t e = cudaMalloc((void**)&m->kronN64, sizeof(double) * KS * (size_t)m->ncells);
+    if (e == cudaSuccess)
+      e = cudaMalloc((void**)&m->kronN32, sizeof(float) * KS * (size_t)m->ncells);
+    if (e != cudaSuccess) return dg_cuda_fail(e, "Kronecker cell blocks (point basis): storage");
+  }
+  cudaError_t e = dgk::dispatch_n<double, dgk::KronRotateF>(m->n, m, s);
+  if (e != cudaSuccess) return dg_cuda_fail(e, "Kronecker cell blocks (point basis): rotation");
+  m->has_kron_nodal = true;
   return DG_OK;
 }
 

@@ -102,7 +102,7 @@ static cudaError_t dmalloc(P** p, size_t count) {
 }
 
 static void free_all(dg_mesh* m) {
-  void* ptrs[] = {m->kt64, m->kt32, m->gh64, m->gh32, m->dgam, m->kbar, m->dflag, m->fw64, m->fw32, m->lineop64, m->diag64, m->dinv64, m->dinv32, m->binv64, m->kron64, m->kron32, m->lineopN64, m->dinvN64, m->dinvN32, m->bN64, m->xN64, m->hk32, m->geo_vol, m->geo_det, m->geo_face, m->geo_pen,
+  void* ptrs[] = {m->kt64, m->kt32, m->gh64, m->gh32, m->dgam, m->kbar, m->dflag, m->fw64, m->fw32, m->lineop64, m->diag64, m->dinv64, m->dinv32, m->binv64, m->kron64, m->kron32, m->lineopN64, m->dinvN64, m->dinvN32, m->bN64, m->xN64, m->hk32, m->kronN64, m->kronN32, m->geo_vol, m->geo_det, m->geo_face, m->geo_pen,
                   m->U64,  m->X64,  m->TR64, m->U32,  m->X32,  m->TR32, m->U64b,
                   m->X64b, m->TR64b, m->hx_dev, m->hy_dev, m->r64, m->p64, m->q64,
                   m->t64,  m->s64, m->d32,  m->r32, m->p32, m->q32, m->partials, m->state,
@@ -225,6 +225,7 @@ extern "C" int dg_set_boundary(dg_mesh* m, int dirichlet_mask) {
   m->has_nodal = false;
   m->has_nodal_diag = false;
   m->has_nodal32 = false;
+  m->has_kron_nodal = false;
   return DG_OK;
 }
 
@@ -283,6 +284,7 @@ extern "C" int dg_set_coefficient(dg_mesh* m, const double* K, void* stream) {
   m->has_nodal = false;
   m->has_nodal_diag = false;
   m->has_nodal32 = false;
+  m->has_kron_nodal = false;
   DG_CUDA(cudaMemsetAsync(m->dflag, 0, sizeof(int), s));
   {
     const long long threads = m->ncells * 32;

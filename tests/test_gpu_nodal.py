@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import SIPG, cg
+from oracle.dg_oracle import kron_block_inverse
 from paper_1911_01492_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -117,20 +118,24 @@ def test_apply_nodal_full_size_64cubed_q3_sampled_cells(dg):
 
 
 @pytest.mark.parametrize("N,k", [(4, 3), (3, 2), (3, 4), (2, 6), (3, 1), (2, 8)])
-@pytest.mark.parametrize("precond", [None, "jacobi"])
+@pytest.mark.parametrize("precond", [None, "jacobi", "kron"])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_nodal_cg_first_iterates_match_oracle_recurrence(dg, N, k, precond, mode):
-    """Three CG iterations from x = 0.  M = I: Q is orthogonal, so x_3 equals
-    the Legendre-basis CG iterate.  Jacobi: the oracle's PCG on Q A Q^T with
-    M = diag(Q A Q^T), mapped back with Q^T.  The mixed mode runs the FP32
-    point-basis kernels (tolerance 1e-4 from FP32 rounding), the FP64 mode the
-    FP64 ones (1e-10)."""
+    """Three CG iterations from x = 0.  M = I and the Kronecker cell blocks: Q
+    is orthogonal and Q M Q^T is the point basis's preconditioner, so x_3
+    equals the Legendre-basis (P)CG iterate.  Jacobi: the oracle's PCG on
+    Q A Q^T with M = diag(Q A Q^T), mapped back with Q^T.  The mixed mode runs
+    the FP32 point-basis kernels (tolerance 1e-4 from FP32 rounding), the FP64
+    mode the FP64 ones (1e-10)."""
     import torch
     D = SIPG(N, k)
     K = field(N, k, 41)
     b = inputs.uniform_vector(N, k, 42)
     if precond is None:
         xref, _, _, _ = cg(lambda v: D.apply(K, v), b, rtol=1e-14, maxit=3)
+    elif precond == "kron":
+        xref, _, _, _ = cg(lambda v: D.apply(K, v), b, rtol=1e-14, maxit=3,
+                           minv=kron_block_inverse(D, K))
     else:
         xh, _, _, _ = cg(lambda v: D.collocation_apply(K, v), D.to_collocation(b), rtol=1e-14,
                          maxit=3, minv=1.0 / D.collocation_diagonal(K))
@@ -145,7 +150,7 @@ def test_nodal_cg_first_iterates_match_oracle_recurrence(dg, N, k, precond, mode
 
 @pytest.mark.parametrize("N,k,seed,bc", [(4, 3, 5, "dirichlet"), (5, 2, 6, "dirichlet"),
                                          (3, 4, 4, "dirichlet"), (4, 2, 7, "flow_x")])
-@pytest.mark.parametrize("precond", [None, "jacobi"])
+@pytest.mark.parametrize("precond", [None, "jacobi", "kron"])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_nodal_cg_residual_checked_by_oracle(dg, N, k, seed, bc, precond, mode):
     import torch
