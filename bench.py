@@ -979,7 +979,11 @@ def run_cg_probe(iters: int, n_cells: int = 0):
                        ("fp64_nodal", dg.DG_CG_FP64 | dg.DG_CG_NODAL),
                        ("fp64_nodal_jacobi",
                         dg.DG_CG_FP64 | dg.DG_CG_NODAL | dg.DG_CG_PRECOND_JACOBI),
-                       ("mixed_ir_nodal", dg.DG_CG_MIXED_IR | dg.DG_CG_NODAL)):
+                       ("mixed_ir_nodal", dg.DG_CG_MIXED_IR | dg.DG_CG_NODAL),
+                       ("fp64_nodal_kron",
+                        dg.DG_CG_FP64 | dg.DG_CG_NODAL | dg.DG_CG_PRECOND_KRON),
+                       ("mixed_ir_nodal_kron",
+                        dg.DG_CG_MIXED_IR | dg.DG_CG_NODAL | dg.DG_CG_PRECOND_KRON)):
         x = torch.zeros_like(b)
         _, st = m.cg_solve(b, x, rtol=1e-12, maxit=iters, mode=mode, raise_on_error=False)
         print(json.dumps({"mode": name, "iterations": st["iterations"],
