@@ -50,6 +50,12 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert L.dg_create_mesh(4, 2, None) == dg.DG_ERR_INVALID_ARG
     assert L.dg_apply(None, None, None, 0, None) == dg.DG_ERR_INVALID_ARG
     assert L.dg_cg_solve(None, None, None, 1e-10, 10, 0, None, None) == dg.DG_ERR_INVALID_ARG
+    for fn in (L.dg_to_nodal, L.dg_to_modal, L.dg_apply_nodal):
+        assert fn(None, None, None, None) == dg.DG_ERR_INVALID_ARG
+        assert b"mesh is NULL" in L.dg_last_error()
+    assert L.dg_cg_solve_batched_mode(None, 1, None, None, 1e-10, 10,
+                                      dg.DG_CG_FP64 | dg.DG_CG_NODAL | dg.DG_CG_PRECOND_JACOBI,
+                                      None, None) == dg.DG_ERR_INVALID_ARG
     assert L.dg_destroy_mesh(None) == dg.DG_OK
 
 
