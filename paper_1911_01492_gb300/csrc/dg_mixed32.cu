@@ -416,16 +416,17 @@ k_cell32x2(const float* __restrict__ pg, const float* __restrict__ TR,
       ++czb;
     }
   }
+  const bool pairrow = vb && cxb != 0;  // both cells of the pair in one x-row
   const long long sy = Nc, sz = (long long)Nc * Nc;
   const int pt = p + N * q;
   const float hw2 = 0.5f * tab.w[pt % N] * tab.w[pt / N];
   // face f's neighbour trace (value, derivative) and weight W/2 for both lanes;
   // zero trace on a boundary lane
   auto face = [&](int f, bool ina, bool inb, long long cna, long long cnb, F2& un, F2& gn,
-                  F2& wh, F2& e) {
+                  F2& wh, F2& e, bool lda = true, bool ldb = true) {
     float ua = 0.f, ga = 0.f, ub = 0.f, gb = 0.f;
-    if (ina) load_trace<N>(TR, cna, f ^ 1, pt, ua, ga);
-    if (inb) load_trace<N>(TR, cnb, f ^ 1, pt, ub, gb);
+    if (ina && lda) load_trace<N>(TR, cna, f ^ 1, pt, ua, ga);
+    if (inb && ldb) load_trace<N>(TR, cnb, f ^ 1, pt, ub, gb);
     un = F2(ua, ub);
     gn = F2(ga, gb);
     wh = F2(va ? hw2 * gh[ca * 6 + f] : 0.0f, vb ? hw2 * gh[cb * 6 + f] : 0.0f);
@@ -494,9 +495,12 @@ k_cell32x2(const float* __restrict__ pg, const float* __restrict__ TR,
 #pragma unroll
     for (int e = 0; e < N; ++e) sr[o + base + e * step] = r[e];
     if (dir == 1) {  // the x-faces' data, in flight during the barrier
-      face(0, va && cxa > 0, vb && cxb > 0, ca - 1, cb - 1, un[0], gn[0], wh[0], ee[0]);
+      // b's x- neighbour and a's x+ neighbour are the pair's other cell when
+      // both sit in one x-row: their traces are formed in this thread below
+      face(0, va && cxa > 0, vb && cxb > 0, ca - 1, cb - 1, un[0], gn[0], wh[0], ee[0], true,
+           !pairrow);
       face(1, va && cxa < Nc - 1, vb && cxb < Nc - 1, ca + 1, cb + 1, un[1], gn[1], wh[1],
-           ee[1]);
+           ee[1], !pairrow, true);
     }
     __syncthreads();
   }
@@ -525,6 +529,13 @@ k_cell32x2(const float* __restrict__ pg, const float* __restrict__ TR,
       for (int i = 4; i < N; i += 2) De = fma(tab.d1[i], X[i], De);
     }
     F2 cv1, cd1, cv0, cd0;
+    if (pairrow) {  // the face between the pair's cells: each lane's neighbour is the other lane
+      const F2 xm = Se - So, xp = Se + So, dxm = Do - De, dxp = Do + De;
+      un[1].v.x = xm.v.y;
+      gn[1].v.x = dxm.v.y;
+      un[0].v.y = xp.v.x;
+      gn[0].v.y = dxp.v.x;
+    }
     flux(true, Se + So, Do + De, un[1], gn[1], wh[1], ee[1], cv1, cd1);
     flux(false, Se - So, Do - De, un[0], gn[0], wh[0], ee[0], cv0, cd0);
     const F2 spl = cv1 + cv0, smn = cv1 - cv0;
@@ -696,16 +707,17 @@ k_cell32x2_nd(const float* __restrict__ pg, const float* __restrict__ TR,
       ++czb;
     }
   }
+  const bool pairrow = vb && cxb != 0;  // both cells of the pair in one x-row
   const long long sy = Nc, sz = (long long)Nc * Nc;
   const int pt = t2;
   // face f's neighbour trace, weight h gamma / 2 and boundary factor e for
   // both lanes (zero trace on a boundary lane; a lane without a cell loads
   // nothing and keeps finite zeros)
   auto face = [&](int f, bool ina, bool inb, long long cna, long long cnb, F2& un, F2& gn,
-                  F2& wh, F2& e) {
+                  F2& wh, F2& e, bool lda = true, bool ldb = true) {
     float ua = 0.f, ga = 0.f, ub = 0.f, gb = 0.f;
-    if (ina) load_trace<N>(TR, cna, f ^ 1, pt, ua, ga);
-    if (inb) load_trace<N>(TR, cnb, f ^ 1, pt, ub, gb);
+    if (ina && lda) load_trace<N>(TR, cna, f ^ 1, pt, ua, ga);
+    if (inb && ldb) load_trace<N>(TR, cnb, f ^ 1, pt, ub, gb);
     un = F2(ua, ub);
     gn = F2(ga, gb);
     wh = F2(va ? 0.5f * gh[ca * 6 + f] : 0.0f, vb ? 0.5f * gh[cb * 6 + f] : 0.0f);
@@ -719,8 +731,10 @@ k_cell32x2_nd(const float* __restrict__ pg, const float* __restrict__ TR,
     cd = (whf * ef) * J;
   };
   // one line: r = r + Dh^T (hK . Dh u) + the line's two faces (slots sl, su_)
-  auto line = [&](int base, int step, const F2 (&un)[2], const F2 (&gn)[2], const F2 (&wh)[2],
-                  const F2 (&ee)[2], F2 (&r)[N]) {
+  // swap: the two faces are the x-faces and the pair shares one of them (the
+  // lanes' own traces there are each other's neighbour traces)
+  auto line = [&](int base, int step, F2 (&un)[2], F2 (&gn)[2], const F2 (&wh)[2],
+                  const F2 (&ee)[2], F2 (&r)[N], bool swap = false) {
     F2 kg[N];
 #pragma unroll
     for (int e = 0; e < N; ++e) {
@@ -742,6 +756,12 @@ k_cell32x2_nd(const float* __restrict__ pg, const float* __restrict__ TR,
       vp = fma(tn.l1[e], u[e], vp);
       gm = fma(tn.dl0[e], u[e], gm);
       gp = fma(tn.dl1[e], u[e], gp);
+    }
+    if (swap) {
+      un[1].v.x = vm.v.y;
+      gn[1].v.x = gm.v.y;
+      un[0].v.y = vp.v.x;
+      gn[0].v.y = gp.v.x;
     }
     F2 cv1, cd1, cv0, cd0;
     flux(true, vp, gp, un[1], gn[1], wh[1], ee[1], cv1, cd1);
@@ -785,8 +805,12 @@ k_cell32x2_nd(const float* __restrict__ pg, const float* __restrict__ TR,
   // x-lines (b = p, e = q): finish q, store it and fold <p, q> over the line
   F2 hi = F2(0.0f), lo = F2(0.0f);
   {
-    face(0, va && cxa > 0, vb && cxb > 0, ca - 1, cb - 1, un[0], gn[0], wh[0], ee[0]);
-    face(1, va && cxa < Nc - 1, vb && cxb < Nc - 1, ca + 1, cb + 1, un[1], gn[1], wh[1], ee[1]);
+    // b's x- and a's x+ neighbour: the pair's other cell when both sit in one
+    // x-row; their traces are formed in this thread (line(..., pairrow))
+    face(0, va && cxa > 0, vb && cxb > 0, ca - 1, cb - 1, un[0], gn[0], wh[0], ee[0], true,
+         !pairrow);
+    face(1, va && cxa < Nc - 1, vb && cxb < Nc - 1, ca + 1, cb + 1, un[1], gn[1], wh[1], ee[1],
+         !pairrow, true);
     const int base = q * N2 + p * N;
     F2 r[N];
 #pragma unroll
@@ -794,7 +818,7 @@ k_cell32x2_nd(const float* __restrict__ pg, const float* __restrict__ TR,
       u[a] = su[o + base + a];
       r[a] = sr[o + base + a];
     }
-    line(base, 1, un, gn, wh, ee, r);
+    line(base, 1, un, gn, wh, ee, r, pairrow);
 #pragma unroll
     for (int a = 0; a < N; ++a) {
       if (va) qg[ca * N3 + base + a] = r[a].v.x;
